@@ -1,0 +1,319 @@
+"""Benchmark: 3-D compressible Navier-Stokes cell-updates per second of one TVD-RK3 step.
+
+Workload (default): the compressible Taylor-Green vortex on a 128^3 periodic box, Ma 0.1, Re 1600,
+Pr 0.71, power-law viscosity, WENO5-Z + HLLC + fourth-order central dissipative fluxes, CFL 0.5,
+FP64 state and arithmetic.  Synthetic: the textbook closed-form initial condition.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fluid|reference] [--workload NAME]
+
+Prints one JSON line.  `value` = interior cells x steps x ranks / (max over ranks of the summed
+CUDA-event time of the K timed steps); L2 is flushed before every timed step.  With N > 1 (launched
+by torch.distributed.run) every rank advances its own independent replica of the workload.
+`--impl reference` times the CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_19494_gb300 import accounting, workloads  # noqa: E402
+
+METRIC = "3D NS cell-updates/s per RK3 step, FP64 vs mixed; adjoint/forward time ratio"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    "tgv128": lambda: workloads.tgv_case(128),
+    "tgv64": lambda: workloads.tgv_case(64),
+    "channel192": lambda: workloads.channel_case(192, 128, 128),
+    "channel256": lambda: workloads.channel_case(256, 128, 128),
+}
+
+
+def initial_prims(case, centres):
+    xc, yc, zc = centres
+    if case["name"].startswith("tgv"):
+        return workloads.tgv_prims(case, xc, yc, zc)
+    return workloads.channel_prims(case, xc, yc, zc, seed=0)
+
+
+def describe(name, case):
+    return {"workload": "%s: %s" % (name, {
+        "tgv": "compressible Taylor-Green vortex, periodic [0,2pi]^3, Ma 0.1, Re 1600, Pr 0.71, power-law mu",
+        "cha": "compressible channel, Ma_b 1.5, Re_b 3000, tanh(beta=2) walls, isothermal, body force"}[name[:3]]),
+        "grid": list(case["n"]), "scheme": "WENO5-%s + HLLC + 4th-order central viscous, TVD-RK3, CFL %.1f"
+        % (case["weno"].upper(), case["cfl"]), "precision": "fp64",
+        "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ------------------------------------------------------------------------------------------------
+def run_fluid(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_19494_gb300 import build, native
+    from paper_2406_19494_gb300.solver import Solver
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    case = WORKLOADS[args.workload]()
+    s = Solver(case)
+    cen = [s.grid(a)[0][3:-3] for a in range(3)]
+    W = np.pad(initial_prims(case, cen), [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    Wd = torch.from_numpy(W).cuda()
+    U0 = s.prim_to_cons(Wd)
+    del Wd
+    U = U0.clone()
+    ncell = case["n"][0] * case["n"][1] * case["n"][2]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        s.step(U, 1)
+    s.check()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, each bracketed by events, L2 flushed before each --------------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    s.profile_read(reset=True)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            s.step(U, 1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    s.check()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    launches = sum(n for _, n in prof.values())
+
+    # ---- end-to-end through the C ABI with host buffers ---------------------------------------
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    Ue = torch.empty_like(U0)
+    nbytes = Uh.numel() * 8
+    e_ms = []
+    for k in range(max(2, min(args.steps, 5)) + 1):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Ue.copy_(Uh, non_blocking=True)
+        s.step(Ue, 1)
+        Uout.copy_(Ue, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e_ms.append(a.elapsed_time(b))
+    e2e_ms = sum(e_ms) / len(e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+
+    # ---- roofline of the dominant kernel class (the face kernels) ------------------------------
+    face = {k: v for k, v in prof.items() if k.startswith("face_")}
+    face_ms = sum(v[0] for v in face.values())
+    face_n = sum(v[1] for v in face.values())
+    per_launch_flops = accounting.cell_axis_flops(3, case["weno"], case["visc"]) * ncell
+    achieved = per_launch_flops / (face_ms / face_n * 1e-3) / 1e12 if face_n else None
+    fp64_probe = ctypes_peak(s, 0)
+    # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz
+    peak = 152 * 2 * 2 * 2.07e9 / 1e12
+
+    value = ncell * args.steps * ws / (total_ms * 1e-3)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(describe(args.workload, case), parallelism="replicas x%d" % ws if ws > 1 else "1 GPU"),
+        "e2e": {"value": ncell * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_face (x, y, z)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                     "fp64_fma_probe_tflops": fp64_probe / 1e3 if fp64_probe else None,
+                     "flops_per_cell_axis": accounting.cell_axis_flops(3, case["weno"], case["visc"]),
+                     "flops_per_cell_update": accounting.cell_update_flops(3, case["weno"], case["visc"])},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "clocks": clk.summary(),
+        "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
+                  "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, case, samples=1)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def ctypes_peak(s, kind):
+    import ctypes
+    import torch
+    g = ctypes.c_double()
+    st = s.lib.fluid_measure_peak(kind, ctypes.byref(g), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return g.value if st == 0 else None
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm of this benchmark)
+# ------------------------------------------------------------------------------------------------
+SLAB = 8   # interior z-planes of the sample
+
+
+def _oracle_sample(case_dict):
+    from oracle import ns_fv as nf
+    case = nf.Case(case_dict)
+    grid = nf.Grid(case)
+    cen = [grid.axes[a].xc[3:-3] for a in range(3)]
+    W = np.pad(initial_prims(case_dict, cen), [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U = nf.fill_halos(nf.prim_to_cons(W, case), case, grid)
+    # a z-slab of SLAB interior planes with its halos, treated as an already filled block
+    sub = dict(case_dict, n=(case.n[0], case.n[1], SLAB))
+    sc = nf.Case(sub)
+    sg = nf.Grid(sc)
+    Us = np.ascontiguousarray(U[:, 0:SLAB + 6])
+    return nf, sc, sg, Us
+
+
+def cpu_baseline(args, case_dict, samples=1):
+    nf, sc, sg, Us = _oracle_sample(case_dict)
+    cells = sc.n[0] * sc.n[1] * sc.n[2]
+    t0 = time.perf_counter()
+    for _ in range(samples):
+        for _stage in range(3):
+            nf.rhs_filled(Us, sc, sg)
+    dt = (time.perf_counter() - t0) / samples
+    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the same "
+                      "state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2])}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    case = WORKLOADS[args.workload]()
+    nf, sc, sg, Us = _oracle_sample(case)
+    cells = sc.n[0] * sc.n[1] * sc.n[2]
+    for _ in range(args.warmup):
+        nf.rhs_filled(Us, sc, sg)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _stage in range(3):
+            nf.rhs_filled(Us, sc, sg)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = cells * args.steps / total
+    sample = ("each step: 3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the "
+              "%s state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2], args.workload))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": describe(args.workload, case), "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fluid", choices=("fluid", "reference"))
+    ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "fluid":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fluid(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * fluid.h -- C ABI of the GB300 finite-volume compressible Navier-Stokes solver.
+ *
+ * The library computes the semi-discrete right-hand side R = dU/dt of the compressible
+ * Navier-Stokes equations (paper Section 2.1, Eq. NSE and Eq. ODE) for a cell-averaged state on a
+ * structured Cartesian grid, uniform or tanh-stretched per axis, and advances it with an explicit
+ * TVD Runge-Kutta scheme (Section 2.1).  Convective face fluxes come from WENO5 reconstruction of
+ * the primitive variables and the HLLC Riemann solver (Section 2.1, Section 3.1); dissipative
+ * fluxes (Newtonian stress with the Stokes hypothesis, Fourier heat flux; Section 2.1) from
+ * fourth-order central differences.  Boundary conditions assign halo cells (Section 3.2):
+ * periodic, zero-gradient, isothermal or adiabatic no-slip wall, the disturbance ("porous") wall
+ * with one wall-normal transpiration parameter per wall cell, and a Dirichlet inflow profile.
+ *
+ * Conventions common to every entry point
+ *   - State arrays are device pointers to FP64 structure-of-arrays data U[5][pz][py][px] with
+ *     x fastest, variables (rho, rho u, rho v, rho w, E).  Every active axis a (a < ndim) carries
+ *     FLUID_HALO = 3 halo cells per side: p_a = n_a + 6; inactive axes have n_a = 1, p_a = 1.
+ *     The caller owns these buffers; they must be 8-byte aligned and must not alias unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  All work is
+ *     enqueued asynchronously on it; nothing synchronises unless the function says so.
+ *   - Every function returns a fluid_status.  Nothing throws across the ABI.  On failure the
+ *     message of fluid_last_error() says why.  A CUDA launch error is returned as FLUID_ECUDA by the
+ *     call that detects it (errors of asynchronous work surface at the next synchronising call).
+ *   - The solver object is not thread-safe: one host thread at a time per solver.
+ *   - The library allocates device memory only in fluid_create (scratch owned by the solver,
+ *     released by fluid_destroy).
+ */
+#ifndef FLUID_H
+#define FLUID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLUID_ABI_VERSION 1
+#define FLUID_HALO 3
+
+typedef enum fluid_status {
+  FLUID_OK = 0,
+  FLUID_EINVAL = 1,      /* invalid argument or configuration */
+  FLUID_ENOMEM = 2,      /* device allocation failed */
+  FLUID_ECUDA = 3,       /* a CUDA runtime call failed */
+  FLUID_ENONFINITE = 4,  /* a state value became NaN/Inf, or a wall ghost temperature <= 0 */
+  FLUID_ETIMEOUT = 5,    /* a bounded wait ran out */
+  FLUID_EBUSY = 6,       /* resource temporarily unavailable */
+  FLUID_EBUDGET = 7,     /* request exceeds the memory budget */
+  FLUID_ENOTSUP = 8      /* configuration recognised but not supported by this build */
+} fluid_status;
+
+/* boundary kinds (per axis and side) -- halo assignment of Section 3.2 */
+enum {
+  FLUID_BC_PERIODIC = 0,
+  FLUID_BC_ZERO_GRADIENT = 1, /* transmissive: halo = first interior cell */
+  FLUID_BC_WALL = 2,          /* isothermal no-slip: mirrored velocity, T_ghost = 2 T_w - T, same p */
+  FLUID_BC_ADIABATIC = 3,     /* adiabatic no-slip: mirrored velocity, same rho and p */
+  FLUID_BC_POROUS = 4,        /* isothermal no-slip with wall-normal transpiration v_w,i (below) */
+  FLUID_BC_INFLOW = 5         /* Dirichlet: fixed primitive profile (fluid_set_inflow) */
+};
+/* grid mapping per axis: face coordinate x(eta), eta = index / n */
+enum {
+  FLUID_STRETCH_UNIFORM = 0,
+  FLUID_STRETCH_TANH2 = 1,    /* x = lo + (hi-lo)/2 (1 + tanh(beta (2 eta - 1)) / tanh beta) */
+  FLUID_STRETCH_TANH1 = 2     /* x = lo + (hi-lo) (1 - tanh(beta (1 - eta)) / tanh beta) */
+};
+enum { FLUID_VISC_NONE = 0, FLUID_VISC_CONSTANT = 1, FLUID_VISC_POWER = 2, FLUID_VISC_SUTHERLAND = 3 };
+enum { FLUID_WENO_JS = 0, FLUID_WENO_Z = 1 };
+enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
+
+/*
+ * Configuration of one solve.  Versioned by struct_size (set it to sizeof(fluid_config)).
+ *   ndim           1, 2 or 3; axes a >= ndim are inactive (n[a] == 1)
+ *   n[a]           interior cells per axis (active axes: 3 .. 2^20, product of padded sizes < 2^31)
+ *   lo, hi         domain extent per axis (face coordinates of the boundaries), hi > lo
+ *   stretch, beta  grid mapping per axis (beta > 0 for the tanh mappings)
+ *   bc[a][side]    boundary kind for side 0 (low) and 1 (high); periodic must pair with periodic
+ *   t_wall[a][s]   wall temperature for FLUID_BC_WALL / FLUID_BC_POROUS faces
+ *   gamma, gas_R   ideal gas: p = (gamma - 1)(E - rho |u|^2 / 2), T = p / (rho R)
+ *   prandtl        lambda = mu c_p / Pr, c_p = gamma R / (gamma - 1)
+ *   visc_law       mu(T): constant mu_ref; power mu_ref (T/T_ref)^visc_exp;
+ *                  Sutherland mu_ref (T/T_ref)^1.5 (T_ref + suth_S) / (T + suth_S); NONE = Euler
+ *   weno, weno_eps WENO5-JS (eps default 1e-6) or WENO5-Z (q = 2, eps default 1e-40); eps <= 0
+ *                  selects the default
+ *   body_force     constant force per unit volume f; source S = (0, f, f . u)
+ *   cfl, dt_fixed  dt = cfl * min(dx/(|u|+c), dx^2/(2 max(4/3, gamma/Pr) mu/rho)) over cells and
+ *                  active axes, or dt_fixed when > 0
+ *   precision      FLUID_PREC_FP64 (all arithmetic in FP64)
+ *   porous_*       porous strip on face (porous_axis, porous_side), which must have kind
+ *                  FLUID_BC_POROUS: wall cells porous_begin .. porous_begin + porous_count - 1 along
+ *                  the first other active axis carry v_w,i = (A / phi0) phi_i sin(2 pi kappa x_i)
+ *                  (Section 3.2's disturbance v = A sin(2 pi kappa x) when phi_i = phi0)
+ */
+typedef struct fluid_config {
+  uint32_t struct_size;
+  int32_t ndim;
+  int32_t n[3];
+  int32_t stretch[3];
+  int32_t bc[3][2];
+  int32_t visc_law;
+  int32_t weno;
+  int32_t precision;
+  int32_t porous_axis, porous_side, porous_begin, porous_count;
+  double lo[3], hi[3], beta[3];
+  double t_wall[3][2];
+  double gamma, gas_R, prandtl;
+  double mu_ref, T_ref, visc_exp, suth_S;
+  double weno_eps;
+  double body_force[3];
+  double cfl, dt_fixed;
+  double porous_A, porous_kappa, porous_phi0;
+} fluid_config;
+
+typedef struct fluid_solver fluid_solver; /* opaque; owned by the library */
+
+/* Validate cfg and create a solver on the current CUDA device; allocates the solver's scratch
+ * (primitive and gradient fields, stage buffer, face-flux accumulator, grid metrics).
+ * Errors: FLUID_EINVAL (bad cfg, out == NULL), FLUID_ENOMEM, FLUID_ECUDA. */
+int fluid_create(const fluid_config* cfg, fluid_solver** out);
+
+/* Release the solver and its scratch (synchronises the device first).  NULL is a no-op. */
+void fluid_destroy(fluid_solver* s);
+
+/* Message of the last failure on s, or of the last failed fluid_create when s == NULL. */
+const char* fluid_last_error(const fluid_solver* s);
+
+/* Padded sizes p[0..2] (x, y, z) of the state arrays; cells = p0 p1 p2 per variable. */
+int fluid_padded_dims(const fluid_solver* s, int32_t p[3]);
+
+/* Copy the grid of axis a (0..2) to host arrays of length p[a]: cell centres xc and widths dx
+ * (face-coordinate differences).  Either pointer may be NULL. */
+int fluid_get_grid(const fluid_solver* s, int axis, double* xc, double* dx);
+
+/* Set the porous-wall parameters phi[0..n-1] (device pointer, n == porous_count) and recompute the
+ * wall transpiration velocities v_w on `stream`.  Until called, phi_i = phi0. */
+int fluid_set_wall_params(fluid_solver* s, const double* phi_dev, int n, void* stream);
+
+/* Set the Dirichlet inflow profile of face (axis, side) from device memory: primitives
+ * (rho, u, v, w, p) shaped [5][T2][T1], T1/T2 the padded sizes of the lower/higher other axis,
+ * count = 5 * T1 * T2 doubles; copied into solver storage on `stream`. */
+int fluid_set_inflow(fluid_solver* s, int axis, int side, const double* W_dev, size_t count,
+                     void* stream);
+
+/* Convert primitives W[5][pz][py][px] (rho, u, v, w, p) to conservative U over all padded cells:
+ * E = p / (gamma - 1) + rho |u|^2 / 2.  W and U may be the same buffer. */
+int fluid_prim_to_cons(fluid_solver* s, const double* W_dev, double* U_dev, void* stream);
+
+/* Right-hand side of Eq. ODE: R = -sum_d (F_{d,+} - F_{d,-}) / dx_d + S for every interior cell,
+ * with F = F^c - F^d the convective minus dissipative face flux and S the body-force source.  U
+ * is read only (its halos are not read or written: boundary values are built from the interior);
+ * R has U's padded shape and only its interior is written.  U and R must not alias. */
+int fluid_rhs(fluid_solver* s, const double* U_dev, double* R_dev, void* stream);
+
+/* CFL time step of the state U (see fluid_config.cfl), written to *dt_dev (one double, device). */
+int fluid_compute_dt(fluid_solver* s, const double* U_dev, double* dt_dev, void* stream);
+
+/* Advance U in place by nsteps steps of the third-order TVD (Shu-Osher) Runge-Kutta scheme:
+ *   U1 = Un + dt R(Un); U2 = 3/4 Un + 1/4 (U1 + dt R(U1)); Un+1 = 1/3 Un + 2/3 (U2 + dt R(U2)),
+ * dt from the CFL rule of each step's initial state (or dt_fixed) and clipped so that the solver
+ * time never passes t_end (t_end <= 0 means no limit; steps after t_end leave U unchanged).  The
+ * solver time and last dt live on the device.  Halos of U are left unspecified. */
+int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* stream);
+
+/* Synchronise `stream` and read the solver time and the last step's dt (either may be NULL). */
+int fluid_get_time(fluid_solver* s, double* t, double* last_dt, void* stream);
+
+/* Set the solver time (enqueued on `stream`). */
+int fluid_set_time(fluid_solver* s, double t, void* stream);
+
+/* Synchronise `stream`; return FLUID_ENONFINITE if any stage produced a non-finite value or a
+ * non-positive ghost temperature since the last check (and clear the flag), else FLUID_OK. */
+int fluid_check(fluid_solver* s, void* stream);
+
+/* Kernel classes reported by the profiler. */
+enum {
+  FLUID_KERNEL_PRIM_BC = 0,  /* primitives + boundary halos */
+  FLUID_KERNEL_GRAD = 1,     /* centre velocity gradients */
+  FLUID_KERNEL_FACE_X = 2,   /* WENO5 + HLLC + dissipative flux + divergence along x */
+  FLUID_KERNEL_FACE_Y = 3,
+  FLUID_KERNEL_FACE_Z = 4,
+  FLUID_KERNEL_STAGE = 5,    /* RK3 stage combination (+ source) */
+  FLUID_KERNEL_DT = 6,       /* CFL reduction */
+  FLUID_KERNEL_SOURCE = 7,   /* body-force source of fluid_rhs */
+  FLUID_KERNEL_COUNT = 8
+};
+
+/* Kernel timing.  While enabled, every kernel the solver launches is bracketed by a CUDA event
+ * pair recorded on the launch stream (the measured time is the kernel's device time plus event
+ * overhead of a few microseconds).  fluid_profile_read synchronises on the pending events, adds
+ * them to per-class totals and returns the total milliseconds and launch count of class `kind`;
+ * reset != 0 clears all totals after reading. */
+int fluid_profile_enable(fluid_solver* s, int enable);
+int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* launches, int reset);
+
+/* FMA-throughput probe (synchronises `stream`): kind 0 = FP64, 1 = FP32; writes achieved GFLOP/s
+ * (2 flops per FMA) of a kernel of independent FMA chains over every SM. */
+int fluid_measure_peak(int kind, double* gflops, void* stream);
+
+/* Library build information: ABI version, and sizeof(fluid_config) expected. */
+int fluid_abi_version(void);
+size_t fluid_config_size(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLUID_H */

@@ -1,0 +1,53 @@
+"""Algorithmic work per unit of the FP64 path (used for roofline fractions).
+
+Counts are floating-point operations of the discretisation itself, as the kernels evaluate it:
+add, sub, mul, div, sqrt, min/max and pow count one each; a fused multiply-add counts two.  They
+are not instruction counts (a division or square root expands into several FP64 instructions).
+
+Per face (one axis, one face, 3-D viscous WENO5-Z + HLLC):
+  WENO5-Z reconstruction    73 per variable and side (JS: 69); 10 per face
+  HLLC (one star branch)   115
+  dissipative flux          90 (power-law mu; Sutherland 94; 1-D / 2-D fewer tangential terms)
+Per cell and axis: one face + the flux difference (3 per variable) = face + 15.
+Per cell and stage: primitives 15, centre gradients 6 per component, stage combination about 20.
+Per cell and RK3 step: 3 stages + the CFL reduction (about 28).
+"""
+
+WENO = {"z": 73, "js": 69}
+HLLC = 115
+PRIM = 15
+STAGE = 20
+DT = 28
+
+
+def visc_face(ndim, visc):
+    if visc == "none":
+        return 0
+    tang = ndim - 1                       # tangential axes with derivative terms
+    mu = {"constant": 0, "power": 3, "sutherland": 7}[visc]
+    return 20 + 24 + 10 * tang + 2 + mu + 1 + 9 + 7 + 4
+
+
+def face_flops(ndim, weno, visc):
+    return 10 * WENO[weno] + HLLC + visc_face(ndim, visc)
+
+
+def cell_axis_flops(ndim, weno, visc):
+    """One face flux plus the flux difference of one cell along one axis (a face-kernel unit)."""
+    return face_flops(ndim, weno, visc) + 15
+
+
+def cell_stage_flops(ndim, weno, visc):
+    grad = 6 * 3 * ndim if visc != "none" else 0
+    return ndim * cell_axis_flops(ndim, weno, visc) + PRIM + grad + STAGE
+
+
+def cell_update_flops(ndim, weno, visc):
+    """Algorithmic FP64 flops of one cell over one TVD-RK3 step."""
+    return 3 * cell_stage_flops(ndim, weno, visc) + DT
+
+
+def cell_update_bytes(nvar=5, word=8):
+    """Compulsory HBM bytes of one cell over one RK3 step with a fully fused stage: stage 1 reads
+    Un and writes U1 (2 arrays), stages 2 and 3 read two arrays and write one (3 each)."""
+    return 8 * nvar * word

@@ -1,0 +1,572 @@
+// C ABI of the solver (declared in include/fluid.h): configuration checks, grid metrics, scratch
+// ownership and the launch sequences of the right-hand side and the TVD-RK3 step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fluid_internal.cuh"
+
+using fl::BC;
+using fl::Ctl;
+using fl::Geo;
+using fl::Phys;
+
+struct fluid_solver {
+  fluid_config cfg;
+  Geo geo;
+  Phys ph;
+  BC bc;
+  int device = 0;
+  double* metric = nullptr;        // 5 arrays x 3 axes, each of length p[a]
+  double* W = nullptr;             // primitives, NW * ncell
+  double* G = nullptr;             // velocity gradients, NG * ncell (viscous only)
+  double* A = nullptr;             // RK stage state, NV * ncell
+  double* R = nullptr;             // right-hand side accumulator, NV * ncell
+  double* partial = nullptr;       // dt partial minima
+  int nparts = 0;
+  Ctl* ctl = nullptr;
+  double* vw = nullptr;            // porous transpiration velocities
+  double* phi = nullptr;           // porous parameters
+  double* inflow[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  size_t inflow_count[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  std::vector<double> host_xc[3], host_dx[3];
+  std::string err;
+  // kernel timing (fluid_profile_*): event pairs bracketing each launch, resolved on read
+  struct ProfEvent {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<ProfEvent> prof_pending, prof_pool;
+  double prof_ms[FLUID_KERNEL_COUNT] = {0};
+  int64_t prof_n[FLUID_KERNEL_COUNT] = {0};
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(fluid_solver* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(fluid_solver* s, cudaError_t e, const char* what) {
+  return fail(s, e == cudaErrorMemoryAllocation ? FLUID_ENOMEM : FLUID_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FL_CUDA(s, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+  } while (0)
+
+// face coordinate x(eta) and dx/deta of the axis mapping
+void axis_map(int stretch, double beta, double lo, double hi, double eta, double* x, double* dxdeta) {
+  const double L = hi - lo;
+  if (stretch == FLUID_STRETCH_UNIFORM) {
+    *x = lo + L * eta;
+    *dxdeta = L;
+    return;
+  }
+  const double tb = std::tanh(beta);
+  if (stretch == FLUID_STRETCH_TANH2) {
+    const double t = std::tanh(beta * (2.0 * eta - 1.0));
+    *x = lo + 0.5 * L * (1.0 + t / tb);
+    *dxdeta = L * beta * (1.0 - t * t) / tb;
+  } else {
+    const double t = std::tanh(beta * (1.0 - eta));
+    *x = lo + L * (1.0 - t / tb);
+    *dxdeta = L * beta * (1.0 - t * t) / tb;
+  }
+}
+
+// host metric arrays of one axis: xc, dx, 1/dx, mc, mf over the padded range
+void axis_metrics(const fluid_config& c, int a, int h, std::vector<double> out[5]) {
+  const int n = c.n[a];
+  const int p = n + 2 * h;
+  for (int k = 0; k < 5; ++k) out[k].assign(p, 0.0);
+  if (c.stretch[a] == FLUID_STRETCH_UNIFORM) {
+    const double d = (c.hi[a] - c.lo[a]) / n;
+    for (int i = 0; i < p; ++i) {
+      const double ai = (double)(i - h);
+      out[0][i] = c.lo[a] + (ai + 0.5) * d;
+      out[1][i] = d;
+      out[2][i] = 1.0 / d;
+      out[3][i] = 1.0 / d;
+      out[4][i] = 1.0 / d;
+    }
+    return;
+  }
+  std::vector<double> xf(p + 1);
+  double dd;
+  for (int k = 0; k <= p; ++k)
+    axis_map(c.stretch[a], c.beta[a], c.lo[a], c.hi[a], (double)(k - h) / n, &xf[k], &dd);
+  for (int i = 0; i < p; ++i) {
+    const double ai = (double)(i - h);
+    double x, dc, df;
+    out[1][i] = xf[i + 1] - xf[i];
+    out[0][i] = 0.5 * (xf[i + 1] + xf[i]);
+    out[2][i] = 1.0 / out[1][i];
+    axis_map(c.stretch[a], c.beta[a], c.lo[a], c.hi[a], (ai + 0.5) / n, &x, &dc);
+    axis_map(c.stretch[a], c.beta[a], c.lo[a], c.hi[a], (ai + 1.0) / n, &x, &df);
+    out[3][i] = n / dc;
+    out[4][i] = n / df;
+  }
+}
+
+
+std::string validate(const fluid_config* c) {
+  if (!c) return "cfg is NULL";
+  if (c->struct_size != sizeof(fluid_config)) return "cfg->struct_size != sizeof(fluid_config)";
+  if (c->ndim < 1 || c->ndim > 3) return "ndim must be 1, 2 or 3";
+  long long cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    const bool act = a < c->ndim;
+    if (act && (c->n[a] < 3 || c->n[a] > (1 << 20))) return "active axes need 3 <= n <= 2^20 cells";
+    if (!act && c->n[a] != 1) return "inactive axes must have n == 1";
+    if (!(c->hi[a] > c->lo[a])) return "hi must exceed lo on every axis";
+    if (c->stretch[a] < 0 || c->stretch[a] > 2) return "unknown stretch kind";
+    if (c->stretch[a] != FLUID_STRETCH_UNIFORM && !(c->beta[a] > 0)) return "tanh stretching needs beta > 0";
+    if (!act && c->stretch[a] != FLUID_STRETCH_UNIFORM) return "inactive axes must be uniform";
+    cells *= c->n[a] + (act ? 2 * FLUID_HALO : 0);
+    if (!act) continue;
+    for (int s = 0; s < 2; ++s) {
+      const int k = c->bc[a][s];
+      if (k < 0 || k > FLUID_BC_INFLOW) return "unknown boundary kind";
+      if ((k == FLUID_BC_WALL || k == FLUID_BC_POROUS) && !(c->t_wall[a][s] > 0))
+        return "isothermal walls need t_wall > 0";
+    }
+    if ((c->bc[a][0] == FLUID_BC_PERIODIC) != (c->bc[a][1] == FLUID_BC_PERIODIC))
+      return "periodic boundaries must pair";
+  }
+  if (cells >= (1LL << 31) / 9) return "grid too large for 32-bit cell indexing";
+  if (!(c->gamma > 1.0) || !(c->gas_R > 0) || !(c->prandtl > 0)) return "need gamma > 1, R > 0, Pr > 0";
+  if (c->visc_law < 0 || c->visc_law > 3) return "unknown viscosity law";
+  if (c->visc_law != FLUID_VISC_NONE && !(c->mu_ref > 0)) return "viscous runs need mu_ref > 0";
+  if (c->visc_law != FLUID_VISC_NONE && c->visc_law != FLUID_VISC_CONSTANT && !(c->T_ref > 0))
+    return "T_ref must be > 0";
+  if (c->visc_law == FLUID_VISC_SUTHERLAND && !(c->suth_S >= 0)) return "suth_S must be >= 0";
+  if (c->weno != FLUID_WENO_JS && c->weno != FLUID_WENO_Z) return "unknown WENO variant";
+  if (c->precision != FLUID_PREC_FP64) return "only FLUID_PREC_FP64 is built";
+  if (!(c->dt_fixed > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt_fixed > 0";
+  int nporous = 0;
+  for (int a = 0; a < c->ndim; ++a)
+    for (int s = 0; s < 2; ++s) nporous += c->bc[a][s] == FLUID_BC_POROUS;
+  if (nporous > 1) return "at most one porous face";
+  if (nporous == 1) {
+    const int a = c->porous_axis, s = c->porous_side;
+    if (a < 0 || a >= c->ndim || s < 0 || s > 1 || c->bc[a][s] != FLUID_BC_POROUS)
+      return "porous_axis/porous_side must name the porous face";
+    if (c->ndim < 2) return "a porous wall needs ndim >= 2";
+    const int t1 = a == 0 ? 1 : 0;
+    if (c->porous_count < 1 || c->porous_begin < 0 || c->porous_begin + c->porous_count > c->n[t1])
+      return "porous strip outside the wall";
+    if (!(c->porous_phi0 != 0)) return "porous_phi0 must be nonzero";
+  }
+  return "";
+}
+
+cudaStream_t as_stream(void* st) { return reinterpret_cast<cudaStream_t>(st); }
+
+int check_ptr(fluid_solver* s, const void* p, const char* what) {
+  if (!p) return fail(s, FLUID_EINVAL, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(s, FLUID_EINVAL, std::string(what) + " is not 8-byte aligned");
+  return FLUID_OK;
+}
+
+// Run one launch; when profiling is on, bracket it with an event pair on the same stream.
+template <class F>
+int timed(fluid_solver* s, int kind, cudaStream_t st, const char* what, F&& launch) {
+  fluid_solver::ProfEvent ev{kind, nullptr, nullptr};
+  if (s->prof_on) {
+    if (!s->prof_pool.empty()) {
+      ev.a = s->prof_pool.back().a;
+      ev.b = s->prof_pool.back().b;
+      s->prof_pool.pop_back();
+    } else {
+      FL_CUDA(s, cudaEventCreate(&ev.a));
+      FL_CUDA(s, cudaEventCreate(&ev.b));
+    }
+    FL_CUDA(s, cudaEventRecord(ev.a, st));
+  }
+  const cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(s, e, what);
+  if (s->prof_on) {
+    FL_CUDA(s, cudaEventRecord(ev.b, st));
+    s->prof_pending.push_back(ev);
+  }
+  return FLUID_OK;
+}
+
+#define FL_TIMED(s, kind, st, call)                                           \
+  do {                                                                       \
+    if (int r_ = timed((s), (kind), (st), #call, [&]() { return (call); })) \
+      return r_;                                                             \
+  } while (0)
+
+int rhs_into(fluid_solver* s, const double* U, double* R, cudaStream_t st) {
+  const Geo& g = s->geo;
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U, s->W, g, s->ph, s->bc, s->ctl, st));
+  if (s->ph.visc != FLUID_VISC_NONE)
+    FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
+  for (int d = 0; d < g.ndim; ++d)
+    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st, fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, st));
+  return FLUID_OK;
+}
+
+int dt_into(fluid_solver* s, double* dt_out, int clip, double t_end, cudaStream_t st) {
+  if (s->ph.dt_fixed <= 0.0)
+    FL_TIMED(s, FLUID_KERNEL_DT, st, fl::launch_dt_partial(s->W, s->geo, s->ph, s->partial, s->nparts, st));
+  FL_TIMED(s, FLUID_KERNEL_DT, st,
+           fl::launch_dt_final(s->partial, s->nparts, s->ph, s->ctl, dt_out, clip, t_end, st));
+  return FLUID_OK;
+}
+
+int stage_into(fluid_solver* s, int stage, const double* Un, const double* Us, double* Ud,
+               double t_end, cudaStream_t st) {
+  FL_TIMED(s, FLUID_KERNEL_STAGE, st,
+           fl::launch_stage(stage, Un, Us, s->R, Ud, s->W, s->geo, s->ph, s->ctl, t_end, st));
+  return FLUID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fluid_abi_version(void) { return FLUID_ABI_VERSION; }
+size_t fluid_config_size(void) { return sizeof(fluid_config); }
+
+const char* fluid_last_error(const fluid_solver* s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int fluid_create(const fluid_config* cfg, fluid_solver** out) {
+  if (!out) return fail(nullptr, FLUID_EINVAL, "out is NULL");
+  *out = nullptr;
+  const std::string why = validate(cfg);
+  if (!why.empty()) return fail(nullptr, FLUID_EINVAL, why);
+  fluid_solver* s = new (std::nothrow) fluid_solver();
+  if (!s) return fail(nullptr, FLUID_ENOMEM, "host allocation failed");
+  s->cfg = *cfg;
+  const fluid_config& c = *cfg;
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(nullptr, FLUID_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  Geo& g = s->geo;
+  g.ndim = c.ndim;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = c.n[a];
+    g.h[a] = a < c.ndim ? FLUID_HALO : 0;
+    g.p[a] = g.n[a] + 2 * g.h[a];
+  }
+  g.sy = g.p[0];
+  g.sz = g.p[0] * g.p[1];
+  g.ncell = g.p[0] * g.p[1] * g.p[2];
+
+  Phys& ph = s->ph;
+  ph.gamma = c.gamma;
+  ph.gm1 = c.gamma - 1.0;
+  ph.igm1 = 1.0 / (c.gamma - 1.0);
+  ph.R = c.gas_R;
+  ph.iR = 1.0 / c.gas_R;
+  ph.cp = c.gamma * c.gas_R / (c.gamma - 1.0);
+  ph.Pr = c.prandtl;
+  ph.lam_fac = ph.cp / c.prandtl;
+  ph.mu_ref = c.mu_ref;
+  ph.T_ref = c.T_ref;
+  ph.iT_ref = c.T_ref > 0 ? 1.0 / c.T_ref : 1.0;
+  ph.visc_exp = c.visc_exp;
+  ph.suth_S = c.suth_S;
+  ph.visc = c.visc_law;
+  ph.weno = c.weno;
+  ph.eps = c.weno_eps > 0 ? c.weno_eps : (c.weno == FLUID_WENO_JS ? 1e-6 : 1e-40);
+  ph.has_force = 0;
+  for (int a = 0; a < 3; ++a) {
+    ph.f[a] = c.body_force[a];
+    ph.has_force |= c.body_force[a] != 0.0;
+  }
+  ph.cfl = c.cfl;
+  ph.dt_fixed = c.dt_fixed;
+  ph.dt_visc_k = 2.0 * std::fmax(4.0 / 3.0, c.gamma / c.prandtl);
+
+  // device scratch
+  const size_t nc = (size_t)g.ncell;
+  size_t nmetric = 0;
+  for (int a = 0; a < 3; ++a) nmetric += 5 * (size_t)g.p[a];
+  s->nparts = fl::dt_partial_count(g);
+  auto bail = [&](cudaError_t err, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(err);
+    fluid_destroy(s);
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? FLUID_ENOMEM : FLUID_ECUDA, m);
+  };
+  if ((e = cudaMalloc(&s->metric, nmetric * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc metric");
+  if ((e = cudaMalloc(&s->W, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W");
+  if (c.visc_law != FLUID_VISC_NONE)
+    if ((e = cudaMalloc(&s->G, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G");
+  if ((e = cudaMalloc(&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
+  if ((e = cudaMalloc(&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
+  if ((e = cudaMalloc(&s->partial, s->nparts * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc partial");
+  if ((e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
+  Ctl c0{};
+  if ((e = cudaMemcpy(s->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "ctl init");
+
+  std::vector<double> all;
+  all.reserve(nmetric);
+  size_t off[3][5];
+  for (int a = 0; a < 3; ++a) {
+    std::vector<double> m[5];
+    axis_metrics(c, a, g.h[a], m);
+    s->host_xc[a] = m[0];
+    s->host_dx[a] = m[1];
+    for (int k = 0; k < 5; ++k) {
+      off[a][k] = all.size();
+      all.insert(all.end(), m[k].begin(), m[k].end());
+    }
+  }
+  if ((e = cudaMemcpy(s->metric, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "metric upload");
+  for (int a = 0; a < 3; ++a) {
+    g.xc[a] = s->metric + off[a][0];
+    g.dx[a] = s->metric + off[a][1];
+    g.idx[a] = s->metric + off[a][2];
+    g.mc[a] = s->metric + off[a][3];
+    g.mf[a] = s->metric + off[a][4];
+  }
+
+  BC& bc = s->bc;
+  bc.porous_axis = -1;
+  bc.porous_side = 0;
+  bc.porous_t1 = 0;
+  bc.vw = nullptr;
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd) {
+      bc.kind[a][sd] = a < c.ndim ? c.bc[a][sd] : FLUID_BC_PERIODIC;
+      bc.Tw[a][sd] = c.t_wall[a][sd];
+      bc.inflow[a][sd] = nullptr;
+      if (a < c.ndim && c.bc[a][sd] == FLUID_BC_INFLOW) {
+        const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+        const size_t cnt = 5 * (size_t)g.p[t1] * g.p[t2];
+        if ((e = cudaMalloc(&s->inflow[a][sd], cnt * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc inflow");
+        if ((e = cudaMemset(s->inflow[a][sd], 0, cnt * sizeof(double))) != cudaSuccess) return bail(e, "inflow init");
+        s->inflow_count[a][sd] = cnt;
+        bc.inflow[a][sd] = s->inflow[a][sd];
+      }
+    }
+  for (int a = 0; a < c.ndim; ++a)
+    for (int sd = 0; sd < 2; ++sd)
+      if (c.bc[a][sd] == FLUID_BC_POROUS) {
+        bc.porous_axis = a;
+        bc.porous_side = sd;
+        bc.porous_t1 = a == 0 ? 1 : 0;
+        const int t1 = bc.porous_t1;
+        if ((e = cudaMalloc(&s->vw, g.p[t1] * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc vw");
+        if ((e = cudaMalloc(&s->phi, c.porous_count * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc phi");
+        std::vector<double> phi0(c.porous_count, c.porous_phi0);
+        if ((e = cudaMemcpy(s->phi, phi0.data(), phi0.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+          return bail(e, "phi init");
+        bc.vw = s->vw;
+        if ((e = fl::launch_wall_velocity(s->phi, s->vw, g.xc[t1], g.p[t1], g.h[t1], c.porous_begin,
+                                          c.porous_count, c.porous_A / c.porous_phi0,
+                                          2.0 * M_PI * c.porous_kappa, 0)) != cudaSuccess)
+          return bail(e, "wall velocity");
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "wall velocity sync");
+      }
+  *out = s;
+  return FLUID_OK;
+}
+
+void fluid_destroy(fluid_solver* s) {
+  if (!s) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  cudaFree(s->metric);
+  cudaFree(s->W);
+  cudaFree(s->G);
+  cudaFree(s->A);
+  cudaFree(s->R);
+  cudaFree(s->partial);
+  cudaFree(s->ctl);
+  cudaFree(s->vw);
+  cudaFree(s->phi);
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd) cudaFree(s->inflow[a][sd]);
+  for (auto* v : {&s->prof_pending, &s->prof_pool})
+    for (auto& ev : *v) {
+      cudaEventDestroy(ev.a);
+      cudaEventDestroy(ev.b);
+    }
+  cudaSetDevice(cur);
+  delete s;
+}
+
+int fluid_padded_dims(const fluid_solver* s, int32_t p[3]) {
+  if (!s || !p) return FLUID_EINVAL;
+  for (int a = 0; a < 3; ++a) p[a] = s->geo.p[a];
+  return FLUID_OK;
+}
+
+int fluid_get_grid(const fluid_solver* s, int axis, double* xc, double* dx) {
+  if (!s || axis < 0 || axis > 2) return FLUID_EINVAL;
+  const size_t p = s->geo.p[axis];
+  if (xc) std::memcpy(xc, s->host_xc[axis].data(), p * sizeof(double));
+  if (dx) std::memcpy(dx, s->host_dx[axis].data(), p * sizeof(double));
+  return FLUID_OK;
+}
+
+int fluid_set_wall_params(fluid_solver* s, const double* phi_dev, int n, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (s->bc.porous_axis < 0) return fail(s, FLUID_EINVAL, "no porous face in this configuration");
+  if (n != s->cfg.porous_count) return fail(s, FLUID_EINVAL, "n must equal porous_count");
+  if (int r = check_ptr(s, phi_dev, "phi_dev")) return r;
+  cudaStream_t st = as_stream(stream);
+  FL_CUDA(s, cudaMemcpyAsync(s->phi, phi_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int t1 = s->bc.porous_t1;
+  FL_CUDA(s, fl::launch_wall_velocity(s->phi, s->vw, s->geo.xc[t1], s->geo.p[t1], s->geo.h[t1],
+                                      s->cfg.porous_begin, s->cfg.porous_count,
+                                      s->cfg.porous_A / s->cfg.porous_phi0,
+                                      2.0 * M_PI * s->cfg.porous_kappa, st));
+  return FLUID_OK;
+}
+
+int fluid_set_inflow(fluid_solver* s, int axis, int side, const double* W_dev, size_t count,
+                     void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (axis < 0 || axis > 2 || side < 0 || side > 1 || !s->inflow[axis][side])
+    return fail(s, FLUID_EINVAL, "face is not an inflow face");
+  if (count != s->inflow_count[axis][side]) return fail(s, FLUID_EINVAL, "inflow count mismatch");
+  if (int r = check_ptr(s, W_dev, "W_dev")) return r;
+  FL_CUDA(s, cudaMemcpyAsync(s->inflow[axis][side], W_dev, count * sizeof(double),
+                             cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return FLUID_OK;
+}
+
+int fluid_prim_to_cons(fluid_solver* s, const double* W_dev, double* U_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, W_dev, "W_dev")) return r;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  FL_CUDA(s, fl::launch_prim_to_cons(W_dev, U_dev, s->geo.ncell, s->ph, as_stream(stream)));
+  return FLUID_OK;
+}
+
+int fluid_rhs(fluid_solver* s, const double* U_dev, double* R_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, R_dev, "R_dev")) return r;
+  if (U_dev == R_dev) return fail(s, FLUID_EINVAL, "U and R must not alias");
+  cudaStream_t st = as_stream(stream);
+  if (int r = rhs_into(s, U_dev, R_dev, st)) return r;
+  if (s->ph.has_force)
+    FL_TIMED(s, FLUID_KERNEL_SOURCE, st, fl::launch_source(R_dev, s->W, s->geo, s->ph, st));
+  return FLUID_OK;
+}
+
+int fluid_compute_dt(fluid_solver* s, const double* U_dev, double* dt_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, dt_dev, "dt_dev")) return r;
+  cudaStream_t st = as_stream(stream);
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->geo, s->ph, s->bc, s->ctl, st));
+  return dt_into(s, dt_dev, 0, 0.0, st);
+}
+
+int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (nsteps < 0) return fail(s, FLUID_EINVAL, "nsteps < 0");
+  cudaStream_t st = as_stream(stream);
+  for (int k = 0; k < nsteps; ++k) {
+    // stage 1: U1 = Un + dt R(Un) into A; dt from the primitives of Un
+    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->geo, s->ph, s->bc, s->ctl, st));
+    if (int r = dt_into(s, nullptr, 1, t_end, st)) return r;
+    if (s->ph.visc != FLUID_VISC_NONE)
+      FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, s->geo, st));
+    for (int d = 0; d < s->geo.ndim; ++d)
+      FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
+               fl::launch_face(d, s->W, s->G, s->R, s->geo, s->ph, d > 0, st));
+    if (int r = stage_into(s, 1, U_dev, U_dev, s->A, t_end, st)) return r;
+    // stage 2: U2 = 3/4 Un + 1/4 (U1 + dt R(U1)) into A
+    if (int r = rhs_into(s, s->A, s->R, st)) return r;
+    if (int r = stage_into(s, 2, U_dev, s->A, s->A, t_end, st)) return r;
+    // stage 3: Un+1 = 1/3 Un + 2/3 (U2 + dt R(U2)) into U
+    if (int r = rhs_into(s, s->A, s->R, st)) return r;
+    if (int r = stage_into(s, 3, U_dev, s->A, U_dev, t_end, st)) return r;
+  }
+  return FLUID_OK;
+}
+
+int fluid_get_time(fluid_solver* s, double* t, double* last_dt, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  Ctl h;
+  cudaStream_t st = as_stream(stream);
+  FL_CUDA(s, cudaMemcpyAsync(&h, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  FL_CUDA(s, cudaStreamSynchronize(st));
+  if (t) *t = h.t;
+  if (last_dt) *last_dt = h.dt;
+  return FLUID_OK;
+}
+
+int fluid_set_time(fluid_solver* s, double t, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  FL_CUDA(s, cudaMemcpyAsync(&s->ctl->t, &t, sizeof(double), cudaMemcpyHostToDevice, st));
+  FL_CUDA(s, cudaStreamSynchronize(st));
+  return FLUID_OK;
+}
+
+int fluid_check(fluid_solver* s, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  unsigned flags = 0;
+  FL_CUDA(s, cudaStreamSynchronize(st));
+  FL_CUDA(s, cudaGetLastError());
+  FL_CUDA(s, cudaMemcpy(&flags, &s->ctl->flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (flags) {
+    const unsigned zero = 0;
+    FL_CUDA(s, cudaMemcpy(&s->ctl->flags, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
+    return fail(s, FLUID_ENONFINITE,
+                (flags & fl::FLAG_GHOST_T) ? "non-positive ghost temperature at an isothermal wall"
+                                           : "non-finite value in the state");
+  }
+  return FLUID_OK;
+}
+
+int fluid_profile_enable(fluid_solver* s, int enable) {
+  if (!s) return FLUID_EINVAL;
+  s->prof_on = enable != 0;
+  return FLUID_OK;
+}
+
+int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* launches, int reset) {
+  if (!s || kind < 0 || kind >= FLUID_KERNEL_COUNT) return FLUID_EINVAL;
+  for (auto& ev : s->prof_pending) {
+    FL_CUDA(s, cudaEventSynchronize(ev.b));
+    float ms = 0.f;
+    FL_CUDA(s, cudaEventElapsedTime(&ms, ev.a, ev.b));
+    s->prof_ms[ev.kind] += ms;
+    s->prof_n[ev.kind] += 1;
+    s->prof_pool.push_back(ev);
+  }
+  s->prof_pending.clear();
+  if (total_ms) *total_ms = s->prof_ms[kind];
+  if (launches) *launches = s->prof_n[kind];
+  if (reset)
+    for (int k = 0; k < FLUID_KERNEL_COUNT; ++k) {
+      s->prof_ms[k] = 0.0;
+      s->prof_n[k] = 0;
+    }
+  return FLUID_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// FMA-throughput probes: the ALU ceilings the FP64 stencil kernels are compared against.
+// Each thread runs 8 independent fused multiply-add chains, so the pipe (not latency) limits.
+#include <cuda_runtime.h>
+
+#include "fluid_internal.cuh"
+
+namespace {
+
+template <class T>
+__global__ void k_fma_chain(T* out, int iters, T a, T b) {
+  T x0 = (T)threadIdx.x, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+    x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+  }
+  const T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == (T)-1) out[blockIdx.x] = s;   // never true for these inputs; keeps the chains live
+}
+
+template <class T>
+int probe(double* gflops, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FLUID_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FLUID_ECUDA;
+  const int blocks = sms * 8, threads = 256;
+  const int iters = sizeof(T) == 8 ? 2048 : 65536;
+  T* out = nullptr;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return FLUID_ECUDA;
+  k_fma_chain<T><<<blocks, threads, 0, st>>>(out, iters / 8, (T)0.999999, (T)1e-7);   // warm-up
+  cudaEventRecord(a, st);
+  k_fma_chain<T><<<blocks, threads, 0, st>>>(out, iters, (T)0.999999, (T)1e-7);
+  cudaEventRecord(b, st);
+  cudaError_t e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess || ms <= 0.f) return FLUID_ECUDA;
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  *gflops = flops / (ms * 1e-3) / 1e9;
+  return FLUID_OK;
+}
+
+}  // namespace
+
+extern "C" int fluid_measure_peak(int kind, double* gflops, void* stream) {
+  if (!gflops || kind < 0 || kind > 1) return FLUID_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return kind == 0 ? probe<double>(gflops, st) : probe<float>(gflops, st);
+}

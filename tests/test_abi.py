@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol include/fluid.h
+declares, agrees with the binding on struct layout, and rejects bad configurations before touching
+the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+from paper_2406_19494_gb300 import build as B
+from paper_2406_19494_gb300 import native
+from paper_2406_19494_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return native.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fluid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fluid_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree_on_symbols():
+    assert declared_symbols() == sorted(native.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_config_layout(lib):
+    assert lib.fluid_abi_version() == 1
+    assert lib.fluid_config_size() == ctypes.sizeof(native.FluidConfig)
+
+
+def _create(lib, cfg):
+    h = ctypes.c_void_p()
+    st = lib.fluid_create(ctypes.byref(cfg), ctypes.byref(h))
+    return st, lib.fluid_last_error(None).decode()
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (lambda c: setattr(c, "ndim", 4), "ndim"),
+    (lambda c: c.n.__setitem__(0, 2), "3 <= n"),
+    (lambda c: c.n.__setitem__(0, 0), "3 <= n"),
+    (lambda c: c.n.__setitem__(2, 5), "inactive"),
+    (lambda c: c.bc[0].__setitem__(1, native.BC["wall"]), "periodic boundaries must pair"),
+    (lambda c: setattr(c, "gamma", 1.0), "gamma"),
+    (lambda c: setattr(c, "struct_size", 8), "struct_size"),
+    (lambda c: setattr(c, "precision", 7), "FP64"),
+    (lambda c: setattr(c, "weno", 9), "WENO"),
+    (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
+])
+def test_invalid_configs_are_rejected_before_any_gpu_call(lib, mutate, needle):
+    cfg = native.config_from_case(wl.random_box(2, (8, 8, 1)))
+    mutate(cfg)
+    st, msg = _create(lib, cfg)
+    assert st == native.FLUID_EINVAL and needle in msg, (st, msg)
+
+
+def test_porous_strip_must_fit(lib):
+    c = wl.porous_bl_case(nx=16, ny=8)
+    c["porous"] = dict(c["porous"], begin=10, count=10)
+    st, msg = _create(lib, native.config_from_case(c))
+    assert st == native.FLUID_EINVAL and "porous" in msg
+
+
+def test_null_out_pointer(lib):
+    cfg = native.config_from_case(wl.sod_case(16))
+    assert lib.fluid_create(ctypes.byref(cfg), None) == native.FLUID_EINVAL

@@ -1,0 +1,294 @@
+"""GPU (sm_103a) parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerance (per variable v, interior cells): max |X_gpu - X_oracle| / max |X_oracle| <= 1e-12,
+X = R for right-hand sides and X = U after one RK3 step.  Both sides compute in FP64; the residual
+differences come from operation order and fused multiply-adds (about 1e-16 relative per
+operation, amplified by the flux-difference cancellation of Eq. ODE to about 1e-14 here).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import padded_state, rel_err
+from oracle import ns_fv as nf
+from paper_2406_19494_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+P = ("periodic", "periodic")
+WALL = ("wall", "wall")
+ZG = ("zero_gradient", "zero_gradient")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19494_gb300 import build
+    build.build()
+
+
+def Solver(c):
+    from paper_2406_19494_gb300.solver import Solver as S
+    return S(c)
+
+
+def inner_of(case):
+    return (slice(None),) + case.interior()
+
+
+def inflows(c, case, grid):
+    out = {}
+    for a in range(case.ndim):
+        for s in range(2):
+            if case.bc[a][s] == "inflow":
+                t1 = 1 if a == 0 else 0
+                t2 = 1 if a == 2 else 2
+                sh = (5, case.p[t2], case.p[t1])
+                # a smooth profile over the face plane built from the interior edge state
+                rng = np.random.default_rng(a * 2 + s)
+                prof = np.empty(sh)
+                prof[0] = 1.0 + 0.1 * rng.uniform(-1, 1, sh[1:])
+                prof[1] = 0.5 + 0.1 * rng.uniform(-1, 1, sh[1:])
+                prof[2] = 0.05 * rng.uniform(-1, 1, sh[1:])
+                prof[3] = 0.05 * rng.uniform(-1, 1, sh[1:])
+                prof[4] = 1.0 + 0.1 * rng.uniform(-1, 1, sh[1:])
+                out[(a, s)] = prof
+    return out
+
+
+CASES = {
+    "sod1d": lambda: wl.sod_case(200),
+    "periodic3d_z_power": lambda: wl.random_box(3, (20, 18, 16)),
+    "periodic3d_js_const": lambda: wl.random_box(3, (17, 13, 11), weno="js", visc="constant"),
+    "channel3d_walls_force": lambda: wl.random_box(3, (16, 20, 12), bc=(P, WALL, P),
+                                                     stretch=("uniform", "tanh2", "uniform"),
+                                                     beta=(0.0, 2.0, 0.0), body_force=(0.05, 0.01, -0.02),
+                                                     t_wall=((1, 1), (2.5, 2.2), (1, 1))),
+    "mixed3d_adiabatic_zg_stretchx": lambda: wl.random_box(3, (14, 12, 10),
+                                                             bc=(ZG, ("adiabatic", "adiabatic"), P),
+                                                             stretch=("tanh1", "uniform", "uniform"),
+                                                             beta=(1.5, 0.0, 0.0), visc="sutherland"),
+    "bl2d_porous_inflow": lambda: wl.random_box(2, (24, 16, 1), bc=(("inflow", "zero_gradient"),
+                                                                    ("porous", "zero_gradient"), P),
+                                                  stretch=("uniform", "tanh1", "uniform"), beta=(0, 2.2, 0),
+                                                  visc="sutherland", t_wall=((1, 1), (2.5, 1), (1, 1)),
+                                                  porous=dict(axis=1, side=0, begin=4, count=12, A=0.05,
+                                                              kappa=3.0, phi0=0.1)),
+    "euler3d_minimal_n3": lambda: wl.random_box(3, (3, 3, 3), visc="none"),
+    "ragged2d_xwall": lambda: wl.random_box(2, (37, 5, 1), bc=(WALL, P, P), t_wall=((2.5, 2.6), (1, 1), (1, 1))),
+}
+
+
+def setup_case(name, seed=0):
+    c = CASES[name]()
+    if name == "sod1d":
+        case = nf.Case(c)
+        grid = nf.Grid(case)
+        W = wl.sod_prims(grid.axes[0].xc)[:, None, None, :]
+        U = nf.prim_to_cons(W, case)
+    else:
+        case, grid, U = padded_state(c, seed=seed)
+    phi = None
+    if case.porous:
+        phi = case.porous["phi0"] * (1.0 + 0.5 * np.sin(np.arange(case.porous["count"])))
+    return c, case, grid, U, phi, inflows(c, case, grid)
+
+
+def make_solver(c, phi, inflow):
+    s = Solver(c)
+    if phi is not None:
+        s.set_wall_params(torch.from_numpy(phi).cuda())
+    for (a, side), prof in inflow.items():
+        s.set_inflow(a, side, torch.from_numpy(np.ascontiguousarray(prof)).cuda())
+    return s
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_parity(name):
+    c, case, grid, U, phi, inflow = setup_case(name)
+    R_ref = nf.rhs(U.copy(), case, grid, phi, inflow)
+    s = make_solver(c, phi, inflow)
+    R = s.rhs(torch.from_numpy(U).cuda())
+    s.check()
+    R = R.cpu().numpy()
+    inner = inner_of(case)
+    err = rel_err(R[inner], R_ref[inner])
+    assert max(err) <= TOL, err
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_dt_parity(name):
+    c, case, grid, U, phi, inflow = setup_case(name)
+    dt_ref = nf.cfl_dt(U, case, grid)
+    s = make_solver(c, phi, inflow)
+    dt = s.compute_dt(torch.from_numpy(U).cuda()).item()
+    assert abs(dt - dt_ref) <= 1e-14 * dt_ref, (dt, dt_ref)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_parity(name):
+    c, case, grid, U, phi, inflow = setup_case(name, seed=3)
+    dt = nf.cfl_dt(U, case, grid)
+    U1 = nf.rk3_step(U.copy(), dt, case, grid, phi, inflow)
+    U2 = nf.rk3_step(U1.copy(), nf.cfl_dt(U1, case, grid), case, grid, phi, inflow)
+    s = make_solver(c, phi, inflow)
+    Ud = torch.from_numpy(U).cuda()
+    s.step(Ud, 1)
+    s.check()
+    inner = inner_of(case)
+    got1 = Ud.cpu().numpy()
+    assert max(rel_err(got1[inner], U1[inner])) <= TOL
+    t, last = s.time()
+    assert abs(last - dt) <= 1e-14 * dt and abs(t - dt) <= 1e-14 * dt
+    # per-step parity from the oracle's own state
+    Ud = torch.from_numpy(U1).cuda()
+    s.step(Ud, 1)
+    s.check()
+    assert max(rel_err(Ud.cpu().numpy()[inner], U2[inner])) <= TOL
+
+
+def test_sod_run_to_t02():
+    """Whole Sod run to t = 0.2 (175 steps, last step clipped): same number of steps, same final
+    time, and per-step parity at several points of the trajectory."""
+    c, case, grid, U0, _, _ = setup_case("sod1d")
+    s = Solver(c)
+    Ud = torch.from_numpy(U0).cuda()
+    s.step(Ud, 1000, t_end=0.2)
+    s.check()
+    t, _ = s.time()
+    assert t == 0.2
+    U, tt, k = nf.advance(U0.copy(), case, grid, 1000, 0.0, 0.2)
+    assert k == 175
+    inner = inner_of(case)
+    err = rel_err(Ud.cpu().numpy()[inner], U[inner])
+    assert max(err) <= 1e-11, err           # accumulated over 175 steps
+    # per-step parity at steps 50, 120, 174 of the oracle trajectory
+    Uk = U0.copy()
+    tk = 0.0
+    checkpoints = {50, 120, 174}
+    for step in range(175):
+        dt = min(nf.cfl_dt(Uk, case, grid), 0.2 - tk)
+        Unext = nf.rk3_step(Uk.copy(), dt, case, grid)
+        if step in checkpoints:
+            s2 = Solver(dict(c, dt_fixed=dt))
+            Ug = torch.from_numpy(Uk).cuda()
+            s2.step(Ug, 1)
+            assert max(rel_err(Ug.cpu().numpy()[inner], Unext[inner])) <= TOL
+        Uk, tk = Unext, tk + dt
+
+
+def test_nonfinite_state_is_reported():
+    c, case, grid, U, phi, inflow = setup_case("periodic3d_z_power")
+    U[4, 5, 5, 5] = np.nan
+    s = Solver(c)
+    Ud = torch.from_numpy(U).cuda()
+    s.step(Ud, 1)
+    from paper_2406_19494_gb300 import native
+    with pytest.raises(native.FluidError) as ei:
+        s.check()
+    assert ei.value.status == native.FLUID_ENONFINITE
+    s.check()                                     # the flag is cleared by the check
+
+
+def test_negative_ghost_temperature_is_reported():
+    c = CASES["channel3d_walls_force"]()
+    c["t_wall"] = ((1, 1), (0.05, 0.05), (1, 1))   # 2 T_w - T < 0 next to the walls
+    case, grid, U = padded_state(c, seed=1)
+    s = Solver(c)
+    s.rhs(torch.from_numpy(U).cuda())
+    from paper_2406_19494_gb300 import native
+    with pytest.raises(native.FluidError) as ei:
+        s.check()
+    assert ei.value.status == native.FLUID_ENONFINITE and "ghost" in str(ei.value)
+
+
+def test_null_and_aliased_pointers_rejected():
+    from paper_2406_19494_gb300 import native
+    import ctypes
+    s = Solver(CASES["periodic3d_z_power"]())
+    L = s.lib
+    st = L.fluid_rhs(s.handle, None, None, None)
+    assert st == native.FLUID_EINVAL
+    U = s.new_state()
+    p = ctypes.c_void_p(U.data_ptr())
+    assert L.fluid_rhs(s.handle, p, p, None) == native.FLUID_EINVAL
+    assert L.fluid_step(s.handle, p, -1, 0.0, None) == native.FLUID_EINVAL
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark uses: sampled cells
+# ---------------------------------------------------------------------------------------------
+class _SubAxis:
+    def __init__(self, ax, lo, hi):
+        for k in ("xc", "dx", "mc", "mf"):
+            setattr(self, k, getattr(ax, k)[lo:hi])
+
+
+class _SubGrid(nf.Grid):
+    def __init__(self, axes):
+        self.axes = axes
+
+
+def _patch_rhs(Ufilled, case, grid, cell):
+    """Oracle R at one interior cell from the 7^3 neighbourhood of an already halo-filled state."""
+    sub = dict(ndim=case.ndim, n=(1, 1, 1), lo=case.lo, hi=case.hi, bc=case.bc, gamma=case.gamma,
+               R=case.R, Pr=case.Pr, visc=case.visc, mu_ref=case.mu_ref, T_ref=case.T_ref,
+               visc_exp=case.visc_exp, suth_S=case.suth_S, weno=case.weno, weno_eps=case.weno_eps,
+               body_force=case.body_force, t_wall=case.t_wall)
+    sc = nf.Case(sub)
+    axes = [_SubAxis(grid.axes[a], cell[a] - 3, cell[a] + 4) for a in range(3)]
+    sl = (slice(None),) + tuple(slice(cell[a] - 3, cell[a] + 4) for a in (2, 1, 0))
+    R = nf.rhs_filled(Ufilled[sl].copy(), sc, _SubGrid(axes))
+    return R[:, 3, 3, 3]
+
+
+def _sampled_rhs_check(c, W, nsamp=48, seed=0, margin=3):
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    Wp = np.pad(W, [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U = nf.prim_to_cons(Wp, case)
+    s = Solver(c)
+    Rg = s.rhs(torch.from_numpy(U).cuda())
+    s.check()
+    Rg = Rg.cpu().numpy()
+    Uf = nf.fill_halos(U.copy(), case, grid)
+    rng = np.random.default_rng(seed)
+    cells = [tuple(int(rng.integers(3 + margin, 3 + case.n[a] - margin)) for a in range(3))
+             for _ in range(nsamp)]
+    cells += [(3, 3, 3), (3 + case.n[0] - 1, 3 + case.n[1] - 1, 3 + case.n[2] - 1)]
+    ref = np.array([_patch_rhs(Uf, case, grid, cl) for cl in cells])
+    got = np.array([Rg[:, cl[2], cl[1], cl[0]] for cl in cells])
+    scale = np.max(np.abs(ref), axis=0)
+    err = np.max(np.abs(got - ref), axis=0) / scale
+    assert np.all(err <= TOL), err
+    return Rg, case, grid
+
+
+@pytest.mark.slow
+def test_tgv_128_full_size_sampled():
+    c = wl.tgv_case(128)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xs = [grid.axes[a].xc[3:-3] for a in range(3)]
+    W = wl.tgv_prims(c, *xs)
+    Rg, case, grid = _sampled_rhs_check(c, W)
+    # property at any size: the periodic box conserves every variable
+    vol = grid.inner_volume(case)
+    inner = case.interior()
+    for v in range(5):
+        tot = np.sum(Rg[v][inner] * vol)
+        assert abs(tot) <= 1e-13 * np.sum(np.abs(Rg[v][inner]) * vol), v
+
+
+@pytest.mark.slow
+def test_channel_full_size_sampled():
+    c = wl.channel_case(192, 128, 128)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xs = [grid.axes[a].xc[3:-3] for a in range(3)]
+    W = wl.channel_prims(c, *xs, seed=0)
+    _sampled_rhs_check(c, W, margin=0)
