@@ -172,6 +172,11 @@ int fluid_set_time(fluid_solver* s, double t, void* stream);
  * non-positive ghost temperature since the last check (and clear the flag), else FLUID_OK. */
 int fluid_check(fluid_solver* s, void* stream);
 
+/* Launch shape of the face kernels: threads per block (a multiple of 32 in [32, 128]; 0 = 128)
+ * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8
+ * that still fills the GPU).  Results do not depend on the shape. */
+int fluid_tune_faces(fluid_solver* s, int block, int seg);
+
 /* Kernel classes reported by the profiler. */
 enum {
   FLUID_KERNEL_PRIM_BC = 0,  /* primitives + boundary halos */

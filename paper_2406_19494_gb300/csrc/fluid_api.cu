@@ -41,6 +41,7 @@ struct fluid_solver {
     int kind;
     cudaEvent_t a, b;
   };
+  int face_block = 0, face_seg = 0;   // launch shape of the face kernels (0 = automatic)
   bool prof_on = false;
   std::vector<ProfEvent> prof_pending, prof_pool;
   double prof_ms[FLUID_KERNEL_COUNT] = {0};
@@ -218,7 +219,7 @@ int rhs_into(fluid_solver* s, const double* U, double* R, cudaStream_t st) {
   if (s->ph.visc != FLUID_VISC_NONE)
     FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
   for (int d = 0; d < g.ndim; ++d)
-    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st, fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, st));
+    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st, fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg, st));
   return FLUID_OK;
 }
 
@@ -494,7 +495,7 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
       FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, s->geo, st));
     for (int d = 0; d < s->geo.ndim; ++d)
       FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
-               fl::launch_face(d, s->W, s->G, s->R, s->geo, s->ph, d > 0, st));
+               fl::launch_face(d, s->W, s->G, s->R, s->geo, s->ph, d > 0, s->face_block, s->face_seg, st));
     if (int r = stage_into(s, 1, U_dev, U_dev, s->A, t_end, st)) return r;
     // stage 2: U2 = 3/4 Un + 1/4 (U1 + dt R(U1)) into A
     if (int r = rhs_into(s, s->A, s->R, st)) return r;
@@ -539,6 +540,16 @@ int fluid_check(fluid_solver* s, void* stream) {
                 (flags & fl::FLAG_GHOST_T) ? "non-positive ghost temperature at an isothermal wall"
                                            : "non-finite value in the state");
   }
+  return FLUID_OK;
+}
+
+int fluid_tune_faces(fluid_solver* s, int block, int seg) {
+  if (!s) return FLUID_EINVAL;
+  if (block != 0 && (block < 32 || block > 128 || block % 32 != 0))
+    return fail(s, FLUID_EINVAL, "block must be 0 or a multiple of 32 in [32, 128]");
+  if (seg < 0) return fail(s, FLUID_EINVAL, "seg must be >= 0");
+  s->face_block = block;
+  s->face_seg = seg;
   return FLUID_OK;
 }
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ bool finite_bits(double x) {
 __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return ph.mu_ref;
   const double r = T * ph.iT_ref;
-  if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * pow(r, ph.visc_exp);
+  if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * exp(ph.visc_exp * log(r));
   // Sutherland
   return ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
 }
@@ -71,7 +71,7 @@ cudaError_t launch_prim_bc(const double* U, double* W, const Geo& g, const Phys&
                            Ctl* ctl, cudaStream_t st);
 cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t st);
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
-                        const Phys& ph, int accumulate, cudaStream_t st);
+                        const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st);
 cudaError_t launch_stage(int stage, const double* Un, const double* Us, const double* R, double* Ud,
                          const double* W, const Geo& g, const Phys& ph, Ctl* ctl, double t_end,

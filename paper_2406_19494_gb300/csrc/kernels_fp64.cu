@@ -172,25 +172,36 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
 template <int SCHEME>
 __device__ __forceinline__ double weno5(double qm2, double qm1, double q0, double qp1, double qp2,
                                         double eps) {
-  const double p0 = (2.0 * qm2 - 7.0 * qm1 + 11.0 * q0) * kSixth;
-  const double p1 = (-qm1 + 5.0 * q0 + 2.0 * qp1) * kSixth;
-  const double p2 = (2.0 * q0 + 5.0 * qp1 - qp2) * kSixth;
+  // candidate values times 6
+  const double C0 = 2.0 * qm2 - 7.0 * qm1 + 11.0 * q0;
+  const double C1 = -qm1 + 5.0 * q0 + 2.0 * qp1;
+  const double C2 = 2.0 * q0 + 5.0 * qp1 - qp2;
   double t = qm2 - 2.0 * qm1 + q0, s = qm2 - 4.0 * qm1 + 3.0 * q0;
   const double b0 = k1312 * t * t + 0.25 * s * s;
   t = qm1 - 2.0 * q0 + qp1; s = qm1 - qp1;
   const double b1 = k1312 * t * t + 0.25 * s * s;
   t = q0 - 2.0 * qp1 + qp2; s = 3.0 * q0 - 4.0 * qp1 + qp2;
   const double b2 = k1312 * t * t + 0.25 * s * s;
+  // Weights scaled by a common positive factor so that one division remains.  With
+  // e_k = beta_k + eps and Q_k = prod_{j != k} e_j:
+  //   JS: d_k / e_k^2                  = d_k Q_k^2 / P^2,              P = e0 e1 e2
+  //   Z : d_k (1 + (tau5 / e_k)^2)     = d_k (P^2 + tau5^2 Q_k^2) / P^2
+  // The common 1/P^2 cancels in omega_k = alpha_k / sum alpha.  Since e_k >= eps the scaled
+  // weights stay normal for eps = 1e-40 (P^2 >= 1e-240) and finite while beta_k < 1e50.
+  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
   double a0, a1, a2;
   if (SCHEME == FLUID_WENO_JS) {
-    const double r0 = 1.0 / (eps + b0), r1 = 1.0 / (eps + b1), r2 = 1.0 / (eps + b2);
-    a0 = 0.1 * r0 * r0; a1 = 0.6 * r1 * r1; a2 = 0.3 * r2 * r2;
+    a0 = 0.1 * (Q0 * Q0); a1 = 0.6 * (Q1 * Q1); a2 = 0.3 * (Q2 * Q2);
   } else {
     const double tau = fabs(b0 - b2);
-    const double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
-    a0 = 0.1 * (1.0 + r0 * r0); a1 = 0.6 * (1.0 + r1 * r1); a2 = 0.3 * (1.0 + r2 * r2);
+    const double P = e0 * Q0;
+    const double PP = P * P, tt = tau * tau;
+    a0 = 0.1 * (PP + tt * (Q0 * Q0));
+    a1 = 0.6 * (PP + tt * (Q1 * Q1));
+    a2 = 0.3 * (PP + tt * (Q2 * Q2));
   }
-  return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+  return (a0 * C0 + a1 * C1 + a2 * C2) / (6.0 * (a0 + a1 + a2));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -206,9 +217,11 @@ __device__ __forceinline__ void hllc(const double wl[5], const double wr[5], con
   const double q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
   const double EL = pL * ph.igm1 + 0.5 * rL * q2L;
   const double ER = pR * ph.igm1 + 0.5 * rR * q2R;
-  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  // 1/sqrt(rho) gives both sqrt(rho) (Roe weights) and 1/rho
+  const double qL = rsqrt(rL), qR = rsqrt(rR);
+  const double sL = rL * qL, sR = rR * qR;
+  const double irL = qL * qL, irR = qR * qR;
   const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
-  const double sL = sqrt(rL), sR = sqrt(rR);
   const double isum = 1.0 / (sL + sR);
   const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
   const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
@@ -521,24 +534,27 @@ __global__ void k_wall_velocity(const double* __restrict__ phi, double* __restri
 
 template <int D, int SCHEME, bool VISC>
 cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo& g,
-                          const Phys& ph, int accumulate, cudaStream_t st) {
+                          const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const long long lines = (long long)g.n[A1] * g.n[A2];
-  // longest segment (fewest redundant faces) that still gives >= 4 blocks of 128 per SM
-  int seg = 64;
-  while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
+  if (block <= 0) block = 128;
+  if (seg <= 0) {
+    // longest segment (fewest redundant faces) that still gives >= 4 blocks of 128 per SM
+    seg = 64;
+    while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
+  }
   const long long total = lines * ((g.n[D] + seg - 1) / seg);
-  k_face<D, SCHEME, VISC><<<grid_for(total, 128), 128, 0, st>>>(W, G, R, g, ph, accumulate, seg);
+  k_face<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
   return cudaGetLastError();
 }
 
 template <int SCHEME, bool VISC>
 cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, const Geo& g,
-                           const Phys& ph, int accumulate, cudaStream_t st) {
-  if (D == 0) return launch_face_t<0, SCHEME, VISC>(W, G, R, g, ph, accumulate, st);
-  if (D == 1) return launch_face_t<1, SCHEME, VISC>(W, G, R, g, ph, accumulate, st);
-  return launch_face_t<2, SCHEME, VISC>(W, G, R, g, ph, accumulate, st);
+                           const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  if (D == 0) return launch_face_t<0, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
+  if (D == 1) return launch_face_t<1, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_face_t<2, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
 }
 
 }  // namespace
@@ -557,13 +573,13 @@ cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t s
 }
 
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
-                        const Phys& ph, int accumulate, cudaStream_t st) {
+                        const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
   const bool visc = ph.visc != FLUID_VISC_NONE;
   if (ph.weno == FLUID_WENO_JS)
-    return visc ? launch_face_sv<FLUID_WENO_JS, true>(D, W, G, R, g, ph, accumulate, st)
-                : launch_face_sv<FLUID_WENO_JS, false>(D, W, G, R, g, ph, accumulate, st);
-  return visc ? launch_face_sv<FLUID_WENO_Z, true>(D, W, G, R, g, ph, accumulate, st)
-              : launch_face_sv<FLUID_WENO_Z, false>(D, W, G, R, g, ph, accumulate, st);
+    return visc ? launch_face_sv<FLUID_WENO_JS, true>(D, W, G, R, g, ph, accumulate, block, seg, st)
+                : launch_face_sv<FLUID_WENO_JS, false>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  return visc ? launch_face_sv<FLUID_WENO_Z, true>(D, W, G, R, g, ph, accumulate, block, seg, st)
+              : launch_face_sv<FLUID_WENO_Z, false>(D, W, G, R, g, ph, accumulate, block, seg, st);
 }
 
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st) {

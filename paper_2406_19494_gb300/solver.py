@@ -101,6 +101,9 @@ class Solver:
     def check(self, stream=None):
         self._check(self.lib.fluid_check(self.handle, _stream(stream)))
 
+    def tune_faces(self, block=0, seg=0):
+        self._check(self.lib.fluid_tune_faces(self.handle, int(block), int(seg)))
+
     def profile(self, enable=True):
         self._check(self.lib.fluid_profile_enable(self.handle, 1 if enable else 0))
 
