@@ -210,7 +210,9 @@ def run_fluid(args):
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_face (x, y, z)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                     "traffic": face_traffic(ncell),
+                     "traffic_note": "bytes per launch: ncu dram read+write of the 64^3 capture scaled by cells",
                      "peak_source": "FP64 units x max SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                      "fp64_fma_probe_tflops": fp64_probe / 1e3 if fp64_probe else None,
                      "flops_per_cell_axis": accounting.cell_axis_flops(3, case["weno"], case["visc"]),
@@ -226,6 +228,22 @@ def run_fluid(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def face_traffic(ncell):
+    """DRAM bytes per face-kernel launch from the committed ncu summary, scaled by cells; None if the
+    kernel sources changed since the counters were taken."""
+    import hashlib
+    try:
+        info = json.load(open(os.path.join(ROOT, "profiles", "k_face_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    csrc = os.path.join(ROOT, "paper_2406_19494_gb300", "csrc")
+    src = open(os.path.join(csrc, "kernels_fp64.cu"), "rb").read() + open(os.path.join(csrc, "fluid_internal.cuh"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != info.get("source_sha256_16"):
+        return None
+    per = sum(info["dram_bytes_per_launch"]) / len(info["dram_bytes_per_launch"])
+    return per * ncell / info["cells"]
 
 
 def ctypes_peak(s, kind):
