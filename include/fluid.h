@@ -202,6 +202,28 @@ int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* lau
  * (2 flops per FMA) of a kernel of independent FMA chains over every SM. */
 int fluid_measure_peak(int kind, double* gflops, void* stream);
 
+/* fluid_rhs without a solver object and without allocating: the same right-hand side as
+ * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is
+ * owned by its own pool or arena and which forbids allocations behind its back, or a
+ * latency-critical caller that cannot afford cudaMalloc's implicit device synchronisation.  The
+ * paper has no counterpart; it is an interface convenience of this library.
+ *
+ * All scratch (primitives, velocity gradients, grid metrics, flags) lives in one fixed file-scope
+ * device array of 2^21 doubles (16 MiB), reserved on every GPU the process uses until it exits.
+ * A grid fits when about 15 doubles per padded cell plus its metrics fit, e.g. up to 44^3 interior
+ * cells in 3-D or 256^2 in 2-D; larger grids return FLUID_EINVAL with a message saying so.  The
+ * caller passes the input U and the output R exactly as for fluid_rhs (same layout, R interior
+ * written, halos untouched).  Porous faces use phi_i = phi0; inflow faces return FLUID_ENOTSUP
+ * (they need fluid_set_inflow).  Non-finite / ghost-temperature flags are not reported.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call shares the one array and
+ * it keeps the last call's contents: calls whose work overlaps on the GPU (different streams or
+ * host threads without ordering) race and give wrong results.  Nothing is allocated on the device
+ * or the host; errbuf (may be NULL) receives a message of at most errlen - 1 characters. */
+int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, double* R_dev, void* stream,
+                      char* errbuf, size_t errlen);
+
 /* Library build information: ABI version, and sizeof(fluid_config) expected. */
 int fluid_abi_version(void);
 size_t fluid_config_size(void);

@@ -124,7 +124,7 @@ void axis_metrics(const fluid_config& c, int a, int h, std::vector<double> out[5
 }
 
 
-std::string validate(const fluid_config* c) {
+const char* validate(const fluid_config* c) {
   if (!c) return "cfg is NULL";
   if (c->struct_size != sizeof(fluid_config)) return "cfg->struct_size != sizeof(fluid_config)";
   if (c->ndim < 1 || c->ndim > 3) return "ndim must be 1, 2 or 3";
@@ -172,7 +172,7 @@ std::string validate(const fluid_config* c) {
       return "porous strip outside the wall";
     if (!(c->porous_phi0 != 0)) return "porous_phi0 must be nonzero";
   }
-  return "";
+  return nullptr;
 }
 
 cudaStream_t as_stream(void* st) { return reinterpret_cast<cudaStream_t>(st); }
@@ -240,6 +240,10 @@ int stage_into(fluid_solver* s, int stage, const double* Un, const double* Us, d
 
 }  // namespace
 
+namespace fl {
+const char* config_error(const fluid_config* c) { return validate(c); }
+}  // namespace fl
+
 extern "C" {
 
 int fluid_abi_version(void) { return FLUID_ABI_VERSION; }
@@ -252,8 +256,7 @@ const char* fluid_last_error(const fluid_solver* s) {
 int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   if (!out) return fail(nullptr, FLUID_EINVAL, "out is NULL");
   *out = nullptr;
-  const std::string why = validate(cfg);
-  if (!why.empty()) return fail(nullptr, FLUID_EINVAL, why);
+  if (const char* why = validate(cfg)) return fail(nullptr, FLUID_EINVAL, why);
   fluid_solver* s = new (std::nothrow) fluid_solver();
   if (!s) return fail(nullptr, FLUID_ENOMEM, "host allocation failed");
   s->cfg = *cfg;

@@ -66,6 +66,9 @@ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   return ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
 }
 
+// Configuration check shared by the entry points: NULL if valid, else a static message.
+const char* config_error(const fluid_config* c);
+
 // ---- launchers implemented in kernels_fp64.cu --------------------------------------------------
 cudaError_t launch_prim_bc(const double* U, double* W, const Geo& g, const Phys& ph, const BC& bc,
                            Ctl* ctl, cudaStream_t st);

@@ -43,6 +43,7 @@ SIGNATURES = {
     "fluid_profile_enable": (_i, [_vp, _i]),
     "fluid_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64), _i]),
     "fluid_measure_peak": (_i, [_i, ctypes.POINTER(_d), _vp]),
+    "fluid_rhs_noalloc": (_i, [_vp, _vp, _vp, _vp, ctypes.c_char_p, _sz]),
     "fluid_abi_version": (_i, []),
     "fluid_config_size": (_sz, []),
 }
