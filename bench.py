@@ -110,11 +110,40 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
+def timed_steps(s, U, steps, warmup, flush, stream, clock_gpu=None):
+    """Warm up, then time `steps` RK3 steps with CUDA events (L2 flushed before each) while the
+    library's event profiler records every kernel; returns (total ms, per-kernel profile, clocks)."""
+    import torch
+    for _ in range(warmup):
+        s.step(U, 1)
+    s.check()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    s.profile(True)
+    s.profile_read(reset=True)
+    clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
+    if clk:
+        clk.__enter__()
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        s.step(U, 1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    s.check()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), prof, clk
+
+
 def run_fluid(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2406_19494_gb300 import build, native
+    from paper_2406_19494_gb300 import build
     from paper_2406_19494_gb300.solver import Solver
 
     ws, rank, local = dist_env()
@@ -129,43 +158,30 @@ def run_fluid(args):
     Wd = torch.from_numpy(W).cuda()
     U0 = s.prim_to_cons(Wd)
     del Wd
-    U = U0.clone()
     ncell = case["n"][0] * case["n"][1] * case["n"][2]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    for _ in range(args.warmup):
-        s.step(U, 1)
-    s.check()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K steps, each bracketed by events, L2 flushed before each --------------
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # ---- timed region (FP64 path): K steps, barrier + synchronize on both sides ----------------
+    U = U0.clone()
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    s.profile(True)
-    s.profile_read(reset=True)
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            s.step(U, 1)
-            ends[k].record(stream)
-        torch.cuda.synchronize()
+    total_ms, prof, clk = timed_steps(s, U, args.steps, args.warmup, flush, stream, clock_gpu=local)
     if ws > 1:
         dist.barrier()
-    prof = s.profile_read(reset=True)
-    s.profile(False)
-    s.check()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = t.item()
     launches = sum(n for _, n in prof.values())
+
+    # ---- the mixed FP32-flux / FP64-state path on the same workload ------------------------------
+    sm = Solver(case, precision="mixed")
+    Um = U0.clone()
+    mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
+    if ws > 1:
+        t = torch.tensor([mixed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mixed_ms = t.item()
 
     # ---- end-to-end through the C ABI with host buffers ---------------------------------------
     Uh = U0.cpu().pin_memory()
@@ -190,15 +206,26 @@ def run_fluid(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = t.item()
 
-    # ---- roofline of the dominant kernel class (the face kernels) ------------------------------
-    face = {k: v for k, v in prof.items() if k.startswith("face_")}
-    face_ms = sum(v[0] for v in face.values())
-    face_n = sum(v[1] for v in face.values())
-    per_launch_flops = accounting.cell_axis_flops(3, case["weno"], case["visc"]) * ncell
-    achieved = per_launch_flops / (face_ms / face_n * 1e-3) / 1e12 if face_n else None
+    # ---- rooflines of the dominant kernel class (the face kernels) ----------------------------
+    def face_time(p):
+        f = {k: v for k, v in p.items() if k.startswith("face_")}
+        ms, n = sum(v[0] for v in f.values()), sum(v[1] for v in f.values())
+        return (ms / n * 1e-3) if n else None
+
     fp64_probe = ctypes_peak(s, 0)
-    # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz
-    peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    fp32_probe = ctypes_peak(s, 1)
+    # peaks from unit counts and the maximum SM clock: FP64 152 SMs x 2 FMA/clk x 2 flops, FP32
+    # 152 SMs x 128 lanes x 2 flops, at 2.07 GHz; HBM from the measured copy bandwidth
+    peak64 = 152 * 2 * 2 * 2.07e9 / 1e12
+    peak32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    hbm = measured_hbm_gbs()
+    t_face = face_time(prof)
+    per_launch_flops = accounting.cell_axis_flops(3, case["weno"], case["visc"]) * ncell
+    achieved = per_launch_flops / t_face / 1e12 if t_face else None
+    tm_face = face_time(mprof)
+    m64 = accounting.mixed_cell_axis_flops64() * ncell / tm_face / 1e12
+    m32 = accounting.mixed_cell_axis_flops32(case["weno"], case["visc"]) * ncell / tm_face / 1e12
+    mbytes = accounting.mixed_face_bytes() * ncell / tm_face / 1e9
 
     value = ncell * args.steps * ws / (total_ms * 1e-3)
     result = {
@@ -209,15 +236,30 @@ def run_fluid(args):
         "e2e": {"value": ncell * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_face (x, y, z)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+        "roofline": {"bound": "alu", "kernel": "k_face (x, y, z), FP64", "achieved": achieved, "peak": peak64,
+                     "unit": "TFLOP/s", "frac": achieved / peak64 if achieved else None,
                      "traffic": face_traffic(ncell),
                      "traffic_note": "bytes per launch: ncu dram read+write of the 64^3 capture scaled by cells",
-                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); "
+                                    "measured by the FMA probe as fp64_fma_probe_tflops",
                      "fp64_fma_probe_tflops": fp64_probe / 1e3 if fp64_probe else None,
                      "flops_per_cell_axis": accounting.cell_axis_flops(3, case["weno"], case["visc"]),
                      "flops_per_cell_update": accounting.cell_update_flops(3, case["weno"], case["visc"])},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "mixed": {
+            "value": ncell * args.steps * ws / (mixed_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": mixed_ms / args.steps, "speedup_vs_fp64": total_ms / mixed_ms,
+            "dtype": "f32 fluxes / f64 state",
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items() if v[1]},
+            "roofline_face": {
+                "fp64": {"achieved": m64, "peak": peak64, "unit": "TFLOP/s", "frac": m64 / peak64},
+                "fp32": {"achieved": m32, "peak": peak32, "unit": "TFLOP/s", "frac": m32 / peak32,
+                         "fp32_fma_probe_tflops": fp32_probe / 1e3 if fp32_probe else None},
+                "hbm": {"achieved": mbytes, "peak": hbm, "unit": "GB/s", "frac": mbytes / hbm},
+                "flops64_per_cell_axis": accounting.mixed_cell_axis_flops64(),
+                "flops32_per_cell_axis": accounting.mixed_cell_axis_flops32(case["weno"], case["visc"]),
+                "bytes_per_cell_axis": accounting.mixed_face_bytes()},
+        },
         "clocks": clk.summary(),
         "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
                   "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
@@ -228,6 +270,13 @@ def run_fluid(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0        # fallback copy bandwidth of an earlier GB300 measurement
 
 
 def face_traffic(ncell):

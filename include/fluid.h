@@ -86,7 +86,11 @@ enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
  *   body_force     constant force per unit volume f; source S = (0, f, f . u)
  *   cfl, dt_fixed  dt = cfl * min(dx/(|u|+c), dx^2/(2 max(4/3, gamma/Pr) mu/rho)) over cells and
  *                  active axes, or dt_fixed when > 0
- *   precision      FLUID_PREC_FP64 (all arithmetic in FP64)
+ *   precision      FLUID_PREC_FP64: all arithmetic in FP64.  FLUID_PREC_MIXED: WENO5 weights and
+ *                  reconstruction, HLLC wave speeds and star correction, and the dissipative
+ *                  stencils in FP32, in a delta form (FP64 cell differences rounded once, face
+ *                  flux = FP64 cell-centre Euler flux + FP32 increment); the state, primitive
+ *                  conversion, face-flux assembly, flux differences and RK3 combination stay FP64
  *   porous_*       porous strip on face (porous_axis, porous_side), which must have kind
  *                  FLUID_BC_POROUS: wall cells porous_begin .. porous_begin + porous_count - 1 along
  *                  the first other active axis carry v_w,i = (A / phi0) phi_i sin(2 pi kappa x_i)
@@ -214,7 +218,8 @@ int fluid_measure_peak(int kind, double* gflops, void* stream);
  * cells in 3-D or 256^2 in 2-D; larger grids return FLUID_EINVAL with a message saying so.  The
  * caller passes the input U and the output R exactly as for fluid_rhs (same layout, R interior
  * written, halos untouched).  Porous faces use phi_i = phi0; inflow faces return FLUID_ENOTSUP
- * (they need fluid_set_inflow).  Non-finite / ghost-temperature flags are not reported.
+ * (they need fluid_set_inflow); it computes in FP64 only (FLUID_PREC_MIXED returns
+ * FLUID_ENOTSUP).  Non-finite / ghost-temperature flags are not reported.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture.  Every call shares the one array and

@@ -51,3 +51,21 @@ def cell_update_bytes(nvar=5, word=8):
     """Compulsory HBM bytes of one cell over one RK3 step with a fully fused stage: stage 1 reads
     Un and writes U1 (2 arrays), stages 2 and 3 read two arrays and write one (3 each)."""
     return 8 * nvar * word
+
+
+# ---- mixed FP32-flux / FP64-state face kernel (FLUID_PREC_MIXED) ------------------------------
+# FP64 per cell and axis: 6 cell differences (5 primitives + T), the cell-centre Euler flux (15),
+# adding the FP32 increment (5) and the flux difference (15).  FP32: the WENO5 reconstructions,
+# the HLLC increment in jump form (about 150) and the dissipative flux (90).
+def mixed_cell_axis_flops64():
+    return 6 + 15 + 5 + 15
+
+
+def mixed_cell_axis_flops32(weno="z", visc="power"):
+    return 10 * WENO[weno] + 150 + (90 if visc != "none" else 0)
+
+
+def mixed_face_bytes():
+    """Compulsory bytes of one face-kernel launch per cell: FP64 primitives 6 x 8 read, FP32
+    primitives 6 x 4 read, FP32 tangential gradients 4 x 4 read, R read and written 2 x 40."""
+    return 48 + 24 + 16 + 80

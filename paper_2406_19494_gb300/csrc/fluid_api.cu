@@ -24,7 +24,10 @@ struct fluid_solver {
   int device = 0;
   double* metric = nullptr;        // 5 arrays x 3 axes, each of length p[a]
   double* W = nullptr;             // primitives, NW * ncell
-  double* G = nullptr;             // velocity gradients, NG * ncell (viscous only)
+  double* G = nullptr;             // velocity gradients, NG * ncell (viscous, FP64 path)
+  bool mixed = false;              // FLUID_PREC_MIXED: FP32 fluxes, FP64 state
+  float* W32 = nullptr;            // FP32 primitives (mixed)
+  float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
   double* R = nullptr;             // right-hand side accumulator, NV * ncell
   double* partial = nullptr;       // dt partial minima
@@ -156,7 +159,7 @@ const char* validate(const fluid_config* c) {
     return "T_ref must be > 0";
   if (c->visc_law == FLUID_VISC_SUTHERLAND && !(c->suth_S >= 0)) return "suth_S must be >= 0";
   if (c->weno != FLUID_WENO_JS && c->weno != FLUID_WENO_Z) return "unknown WENO variant";
-  if (c->precision != FLUID_PREC_FP64) return "only FLUID_PREC_FP64 is built";
+  if (c->precision != FLUID_PREC_FP64 && c->precision != FLUID_PREC_MIXED) return "unknown precision";
   if (!(c->dt_fixed > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt_fixed > 0";
   int nporous = 0;
   for (int a = 0; a < c->ndim; ++a)
@@ -213,19 +216,39 @@ int timed(fluid_solver* s, int kind, cudaStream_t st, const char* what, F&& laun
       return r_;                                                             \
   } while (0)
 
-int rhs_into(fluid_solver* s, const double* U, double* R, cudaStream_t st) {
+// velocity gradients and the per-axis face kernels of one right-hand side (primitives ready)
+int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
   const Geo& g = s->geo;
-  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U, s->W, g, s->ph, s->bc, s->ctl, st));
+  if (s->mixed) {
+    if (s->ph.visc != FLUID_VISC_NONE)
+      FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad32(s->W32, s->G32, g, st));
+    for (int d = 0; d < g.ndim; ++d)
+      FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
+               fl::launch_face_mixed(d, s->W, s->W32, s->G32, R, g, s->ph, d > 0, s->face_block,
+                                     s->face_seg, st));
+    return FLUID_OK;
+  }
   if (s->ph.visc != FLUID_VISC_NONE)
     FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
   for (int d = 0; d < g.ndim; ++d)
-    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st, fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg, st));
+    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
+             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg, st));
   return FLUID_OK;
 }
 
+int rhs_into(fluid_solver* s, const double* U, double* R, cudaStream_t st) {
+  const Geo& g = s->geo;
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U, s->W, s->W32, g, s->ph, s->bc, s->ctl, st));
+  return grad_faces(s, R, st);
+}
+
 int dt_into(fluid_solver* s, double* dt_out, int clip, double t_end, cudaStream_t st) {
-  if (s->ph.dt_fixed <= 0.0)
-    FL_TIMED(s, FLUID_KERNEL_DT, st, fl::launch_dt_partial(s->W, s->geo, s->ph, s->partial, s->nparts, st));
+  if (s->ph.dt_fixed <= 0.0) {
+    if (s->mixed)
+      FL_TIMED(s, FLUID_KERNEL_DT, st, fl::launch_dt_partial32(s->W32, s->geo, s->ph, s->partial, s->nparts, st));
+    else
+      FL_TIMED(s, FLUID_KERNEL_DT, st, fl::launch_dt_partial(s->W, s->geo, s->ph, s->partial, s->nparts, st));
+  }
   FL_TIMED(s, FLUID_KERNEL_DT, st,
            fl::launch_dt_final(s->partial, s->nparts, s->ph, s->ctl, dt_out, clip, t_end, st));
   return FLUID_OK;
@@ -315,8 +338,14 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   };
   if ((e = cudaMalloc(&s->metric, nmetric * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc metric");
   if ((e = cudaMalloc(&s->W, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W");
-  if (c.visc_law != FLUID_VISC_NONE)
+  s->mixed = c.precision == FLUID_PREC_MIXED;
+  if (s->mixed) {
+    if ((e = cudaMalloc(&s->W32, fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    if (c.visc_law != FLUID_VISC_NONE)
+      if ((e = cudaMalloc(&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
+  } else if (c.visc_law != FLUID_VISC_NONE) {
     if ((e = cudaMalloc(&s->G, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G");
+  }
   if ((e = cudaMalloc(&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
   if ((e = cudaMalloc(&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
   if ((e = cudaMalloc(&s->partial, s->nparts * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc partial");
@@ -398,6 +427,8 @@ void fluid_destroy(fluid_solver* s) {
   cudaFree(s->metric);
   cudaFree(s->W);
   cudaFree(s->G);
+  cudaFree(s->W32);
+  cudaFree(s->G32);
   cudaFree(s->A);
   cudaFree(s->R);
   cudaFree(s->partial);
@@ -481,7 +512,7 @@ int fluid_compute_dt(fluid_solver* s, const double* U_dev, double* dt_dev, void*
   if (int r = check_ptr(s, U_dev, "U_dev")) return r;
   if (int r = check_ptr(s, dt_dev, "dt_dev")) return r;
   cudaStream_t st = as_stream(stream);
-  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->geo, s->ph, s->bc, s->ctl, st));
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
   return dt_into(s, dt_dev, 0, 0.0, st);
 }
 
@@ -492,13 +523,9 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
   cudaStream_t st = as_stream(stream);
   for (int k = 0; k < nsteps; ++k) {
     // stage 1: U1 = Un + dt R(Un) into A; dt from the primitives of Un
-    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->geo, s->ph, s->bc, s->ctl, st));
+    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
     if (int r = dt_into(s, nullptr, 1, t_end, st)) return r;
-    if (s->ph.visc != FLUID_VISC_NONE)
-      FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, s->geo, st));
-    for (int d = 0; d < s->geo.ndim; ++d)
-      FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
-               fl::launch_face(d, s->W, s->G, s->R, s->geo, s->ph, d > 0, s->face_block, s->face_seg, st));
+    if (int r = grad_faces(s, s->R, st)) return r;
     if (int r = stage_into(s, 1, U_dev, U_dev, s->A, t_end, st)) return r;
     // stage 2: U2 = 3/4 Un + 1/4 (U1 + dt R(U1)) into A
     if (int r = rhs_into(s, s->A, s->R, st)) return r;

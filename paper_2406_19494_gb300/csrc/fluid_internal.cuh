@@ -70,8 +70,9 @@ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
 const char* config_error(const fluid_config* c);
 
 // ---- launchers implemented in kernels_fp64.cu --------------------------------------------------
-cudaError_t launch_prim_bc(const double* U, double* W, const Geo& g, const Phys& ph, const BC& bc,
-                           Ctl* ctl, cudaStream_t st);
+// W32 (optional, may be null): FP32 copy of the primitives for the mixed-precision path
+cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
+                           const BC& bc, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t st);
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
@@ -84,6 +85,14 @@ cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, dou
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,
                             double* dt_out, int clip_to_ctl, double t_end, cudaStream_t st);
 int dt_partial_count(const Geo& g);
+// ---- mixed-precision launchers implemented in kernels_mixed.cu --------------------------------
+cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
+                              const Geo& g, const Phys& ph, int accumulate, int block, int seg,
+                              cudaStream_t st);
+cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st);
+cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
+                                int nparts, cudaStream_t st);
+
 cudaError_t launch_prim_to_cons(const double* W, double* U, int ncell, const Phys& ph,
                                 cudaStream_t st);
 cudaError_t launch_wall_velocity(const double* phi, double* vw, const double* xc, int p, int h,

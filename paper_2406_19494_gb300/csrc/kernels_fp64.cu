@@ -80,8 +80,8 @@ __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a
   w[5] = w[4] / (w[0] * ph.R);
 }
 
-__global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W, Geo g, Phys ph,
-                          BC bc, Ctl* ctl) {
+__global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
+                          float* __restrict__ W32, Geo g, Phys ph, BC bc, Ctl* ctl) {
   const int total = g.ncell;
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < total;
        cell += gridDim.x * blockDim.x) {
@@ -128,6 +128,8 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W, 
       }
     }
     for (int v = 0; v < NW; ++v) W[v * g.ncell + cell] = w[v];
+    if (W32)
+      for (int v = 0; v < NW; ++v) W32[v * g.ncell + cell] = (float)w[v];
   }
 }
 
@@ -559,9 +561,9 @@ cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, c
 
 }  // namespace
 
-cudaError_t launch_prim_bc(const double* U, double* W, const Geo& g, const Phys& ph, const BC& bc,
-                           Ctl* ctl, cudaStream_t st) {
-  k_prim_bc<<<grid_for(g.ncell, 256), 256, 0, st>>>(U, W, g, ph, bc, ctl);
+cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
+                           const BC& bc, Ctl* ctl, cudaStream_t st) {
+  k_prim_bc<<<grid_for(g.ncell, 256), 256, 0, st>>>(U, W, W32, g, ph, bc, ctl);
   return cudaGetLastError();
 }
 

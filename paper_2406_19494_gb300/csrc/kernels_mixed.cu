@@ -1,0 +1,409 @@
+// Mixed-precision face kernels: WENO5 weights and reconstruction, HLLC wave speeds and star
+// correction, and the dissipative stencils in FP32; the state, the cell-centre convective flux,
+// the face-flux assembly and the flux-difference accumulation in FP64.
+//
+// Why a delta form.  At low Mach number the pressure (and total enthalpy) is large and nearly
+// uniform, so fluxes are large and their differences across a cell small: a flux rounded to FP32
+// carries an absolute error ~6e-8 |F| that the divergence divides by dx.  Here every FP32 quantity
+// is either a coefficient (used only as a factor) or a small increment that FP32 represents to
+// ~6e-8 of its own size:
+//   * cell differences D_j = q_{j+1} - q_j of the primitives are taken in FP64 and rounded once;
+//   * WENO5 works on offsets delta_k = q_{a+k} - q_a built from the D's (the smoothness
+//     indicators and the weights do not depend on the offset, the candidates are affine);
+//   * the face flux is F_{a+1/2} = F(q_a) [FP64] + X [FP32], where X is the change of the Euler
+//     flux from the cell state q_a to the upwind face state, written as a polynomial in the
+//     offsets, plus the HLLC star correction S_K (U*_K - U_K), written through the jumps of the
+//     reconstructed states (S* - u_K from the pressure and velocity jumps), minus the
+//     dissipative flux;
+//   * R += -(F_{a+1/2} - F_{a-1/2}) / dx in FP64, so the face fluxes telescope exactly as in the
+//     FP64 path (each face value is computed once and shared by its two cells).
+#include <cuda_runtime.h>
+
+#include "fluid_internal.cuh"
+
+namespace fl {
+
+namespace {
+
+constexpr float k1312f = 13.0f / 12.0f;
+constexpr float kZepsF = 1e-20f;      // WENO5-Z epsilon in FP32 (a normal float)
+constexpr float kZclampF = 1e18f;     // bound of tau5 / (beta + eps): keeps its square finite
+
+int grid_for(long long work, int block) {
+  long long b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > 152LL * 64) b = 152LL * 64;
+  return (int)b;
+}
+
+// WENO5 value at i+1/2 relative to an arbitrary offset, from offsets of q_{i-2..i+2}
+template <int SCHEME>
+__device__ __forceinline__ float weno5f(float qm2, float qm1, float q0, float qp1, float qp2, float eps) {
+  const float p0 = 2.0f * qm2 - 7.0f * qm1 + 11.0f * q0;
+  const float p1 = -qm1 + 5.0f * q0 + 2.0f * qp1;
+  const float p2 = 2.0f * q0 + 5.0f * qp1 - qp2;
+  float t = qm2 - 2.0f * qm1 + q0, s = qm2 - 4.0f * qm1 + 3.0f * q0;
+  const float b0 = k1312f * t * t + 0.25f * s * s;
+  t = qm1 - 2.0f * q0 + qp1; s = qm1 - qp1;
+  const float b1 = k1312f * t * t + 0.25f * s * s;
+  t = q0 - 2.0f * qp1 + qp2; s = 3.0f * q0 - 4.0f * qp1 + qp2;
+  const float b2 = k1312f * t * t + 0.25f * s * s;
+  float a0, a1, a2;
+  if (SCHEME == FLUID_WENO_JS) {
+    const float r0 = 1.0f / (eps + b0), r1 = 1.0f / (eps + b1), r2 = 1.0f / (eps + b2);
+    a0 = 0.1f * r0 * r0; a1 = 0.6f * r1 * r1; a2 = 0.3f * r2 * r2;
+  } else {
+    const float tau = fabsf(b0 - b2);
+    const float r0 = fminf(tau / (b0 + kZepsF), kZclampF);
+    const float r1 = fminf(tau / (b1 + kZepsF), kZclampF);
+    const float r2 = fminf(tau / (b2 + kZepsF), kZclampF);
+    a0 = 0.1f * (1.0f + r0 * r0); a1 = 0.6f * (1.0f + r1 * r1); a2 = 0.3f * (1.0f + r2 * r2);
+  }
+  return (a0 * p0 + a1 * p1 + a2 * p2) / (6.0f * (a0 + a1 + a2));
+}
+
+__device__ __forceinline__ float viscosity_f(float T, const Phys& ph) {
+  if (ph.visc == FLUID_VISC_CONSTANT) return (float)ph.mu_ref;
+  const float r = T * (float)ph.iT_ref;
+  if (ph.visc == FLUID_VISC_POWER) return (float)ph.mu_ref * powf(r, (float)ph.visc_exp);
+  return (float)ph.mu_ref * (r * sqrtf(r)) * (float)(ph.T_ref + ph.suth_S) / (T + (float)ph.suth_S);
+}
+
+// X: change of the face flux relative to F(q_a), in FP32 (see the file comment).
+//   b        FP32 cell state q_a (rho, u, v, w, p)
+//   dL, dR   offsets of the reconstructed left and right face states from q_a
+template <int D>
+__device__ __forceinline__ void hllc_delta(const float b[5], const float dL[5], const float dR[5],
+                                           const Phys& ph, float X[5]) {
+  const float g = (float)ph.gamma, gm1 = (float)ph.gm1, igm1 = (float)ph.igm1;
+  float wl[5], wr[5], J[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    wl[v] = b[v] + dL[v];
+    wr[v] = b[v] + dR[v];
+    J[v] = dR[v] - dL[v];                         // jumps, accurate to FP32 relative to themselves
+  }
+  const float rL = wl[0], pL = wl[4], rR = wr[0], pR = wr[4];
+  const float unL = wl[1 + D], unR = wr[1 + D];
+  const float q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+  const float q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+  const float EL = pL * igm1 + 0.5f * rL * q2L, ER = pR * igm1 + 0.5f * rR * q2R;
+  const float cL = sqrtf(g * pL / rL), cR = sqrtf(g * pR / rR);
+  const float sL = sqrtf(rL), sR = sqrtf(rR);
+  const float is = 1.0f / (sL + sR);
+  const float ut0 = (sL * wl[1] + sR * wr[1]) * is;
+  const float ut1 = (sL * wl[2] + sR * wr[2]) * is;
+  const float ut2 = (sL * wl[3] + sR * wr[3]) * is;
+  const float Ht = (sL * (EL + pL) / rL + sR * (ER + pR) / rR) * is;
+  const float ct = sqrtf(gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const float utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
+  const float SL = fminf(unL - cL, utn - ct);
+  const float SR = fmaxf(unR + cR, utn + ct);
+  const float mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const float den = mL - mR;
+  // S* - u_L and S* - u_R from the jumps: (dp - m_{R|L} du_n) / (m_L - m_R)
+  const float sigL = (J[4] - mR * J[1 + D]) / den;
+  const float sigR = (J[4] - mL * J[1 + D]) / den;
+  const float Ss = unL + sigL;
+
+  const bool left = (SL >= 0.0f) || (Ss >= 0.0f);
+  const bool star = left ? !(SL >= 0.0f) : (SR > 0.0f);
+  const float* d = left ? dL : dR;
+  const float* w = left ? wl : wr;
+
+  // Euler-flux change from q_a to the face state K = b + d
+  const float un = b[1 + D], unK = w[1 + D];
+  const float mn = b[0] * un;
+  const float dm = b[0] * d[1 + D] + d[0] * unK;          // rho' u_n' - rho u_n
+  X[0] = dm;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) X[1 + c] = dm * w[1 + c] + mn * d[1 + c];
+  X[1 + D] += d[4];
+  const float q2b = b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+  const float dq2 = d[1] * (2.0f * b[1] + d[1]) + d[2] * (2.0f * b[2] + d[2]) + d[3] * (2.0f * b[3] + d[3]);
+  const float gg = g * igm1;
+  const float Hv = gg * b[4] + 0.5f * b[0] * q2b;         // E + p of q_a
+  const float dHv = gg * d[4] + 0.5f * (d[0] * (q2b + dq2) + b[0] * dq2);
+  X[4] = d[1 + D] * (Hv + dHv) + un * dHv;
+
+  if (star) {
+    // S_K (U*_K - U_K) with theta = (S* - u_K)/(S_K - S*), chi = 1 + theta
+    const float S = left ? SL : SR;
+    const float sig = left ? sigL : sigR;
+    const float rK = w[0], pK = w[4];
+    const float EK = left ? EL : ER;
+    const float theta = sig / (S - Ss);
+    const float chi = 1.0f + theta;
+    float dU[5];
+    dU[0] = rK * theta;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dU[1 + c] = rK * theta * w[1 + c];
+    dU[1 + D] = rK * (theta * unK + chi * sig);
+    dU[4] = theta * EK + chi * sig * (rK * Ss + pK / (S - unK));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) X[v] += S * dU[v];
+  }
+}
+
+// D-window entry: difference of one primitive between consecutive cells, FP64 -> FP32
+__device__ __forceinline__ float diff32(const double* __restrict__ f, int cell, int s) {
+  return (float)(__ldg(f + cell + s) - __ldg(f + cell));
+}
+
+// Face flux F_{a+1/2} (FP64) along D.  `cell` is cell a; Dw[v][k] holds D_{a-2+k}, k = 0..4.
+template <int D, int SCHEME, bool VISC>
+__device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, const float* __restrict__ W32,
+                                                const float* __restrict__ G32, int cell, int s, int a,
+                                                const float Dw[6][5], const Geo& g, const Phys& ph,
+                                                double F[5]) {
+  const int nc = g.ncell;
+  const float eps = (float)ph.eps;
+  float b[5], dL[5], dR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    b[v] = __ldg(W32 + v * nc + cell);
+    // offsets from q_a of cells a-2 .. a+3
+    const float om1 = -Dw[v][1], om2 = -(Dw[v][0] + Dw[v][1]);
+    const float op1 = Dw[v][2], op2 = Dw[v][2] + Dw[v][3], op3 = op2 + Dw[v][4];
+    dL[v] = weno5f<SCHEME>(om2, om1, 0.0f, op1, op2, eps);
+    dR[v] = weno5f<SCHEME>(op3, op2, op1, 0.0f, om1, eps);
+  }
+  float X[5];
+  hllc_delta<D>(b, dL, dR, ph, X);
+
+  if (VISC) {
+    // u, v, w, T at cells a-1..a+2 through the D window (entries 1, 2, 3 = D_{a-1}, D_a, D_{a+1})
+    const float mfa = (float)g.mf[D][a];
+    float vf[3], Gf[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d0 = Dw[1 + c][1], d1 = Dw[1 + c][2], d2 = Dw[1 + c][3];
+      vf[c] = b[1 + c] + (8.0f * d1 + d0 - d2) * (1.0f / 16.0f);
+      Gf[c][D] = (26.0f * d1 - d0 - d2) * (1.0f / 24.0f) * mfa;
+    }
+    const float Tb = __ldg(W32 + 5 * nc + cell);
+    const float Tf = Tb + (8.0f * Dw[5][2] + Dw[5][1] - Dw[5][3]) * (1.0f / 16.0f);
+    const float dT = (26.0f * Dw[5][2] - Dw[5][1] - Dw[5][3]) * (1.0f / 24.0f) * mfa;
+    auto interp = [](float fm1, float f0, float f1, float f2) {
+      return (9.0f * (f0 + f1) - (fm1 + f2)) * (1.0f / 16.0f);
+    };
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+      if (bb == D) continue;
+      if (bb < g.ndim) {
+        const float* gd = G32 + (D * 3 + bb) * nc + cell;
+        const float* gb = G32 + (bb * 3 + bb) * nc + cell;
+        Gf[D][bb] = interp(__ldg(gd - s), __ldg(gd), __ldg(gd + s), __ldg(gd + 2 * s));
+        Gf[bb][bb] = interp(__ldg(gb - s), __ldg(gb), __ldg(gb + s), __ldg(gb + 2 * s));
+      } else {
+        Gf[D][bb] = 0.0f;
+        Gf[bb][bb] = 0.0f;
+      }
+    }
+    const float div = Gf[0][0] + Gf[1][1] + Gf[2][2];
+    const float mu = viscosity_f(Tf, ph);
+    const float lam = mu * (float)ph.lam_fac;
+    float tau[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c == D) tau[c] = mu * (Gf[D][D] + Gf[D][D]) - (2.0f / 3.0f) * mu * div;
+      else tau[c] = mu * (Gf[c][D] + Gf[D][c]);
+    }
+    X[1] -= tau[0];
+    X[2] -= tau[1];
+    X[3] -= tau[2];
+    X[4] -= vf[0] * tau[0] + vf[1] * tau[1] + vf[2] * tau[2] + lam * dT;
+  }
+
+  // FP64 cell-centre Euler flux of q_a plus the FP32 change
+  const double r = W[cell], u0 = W[nc + cell], u1 = W[2 * nc + cell], u2 = W[3 * nc + cell];
+  const double p = W[4 * nc + cell];
+  const double un = D == 0 ? u0 : (D == 1 ? u1 : u2);
+  const double E = p * ph.igm1 + 0.5 * r * (u0 * u0 + u1 * u1 + u2 * u2);
+  const double mn = r * un;
+  F[0] = mn + (double)X[0];
+  F[1] = mn * u0 + (double)X[1];
+  F[2] = mn * u1 + (double)X[2];
+  F[3] = mn * u2 + (double)X[3];
+  F[1 + D] += p;
+  F[4] = un * (E + p) + (double)X[4];
+}
+
+template <int D, int SCHEME, bool VISC>
+__global__ void __launch_bounds__(128) k_face_mixed(const double* __restrict__ W,
+                                                    const float* __restrict__ W32,
+                                                    const float* __restrict__ G32,
+                                                    double* __restrict__ R, Geo g, Phys ph,
+                                                    int accumulate, int seg) {
+  constexpr int A1 = (D == 0) ? 1 : 0;
+  constexpr int A2 = (D == 2) ? 1 : 2;
+  constexpr int NVW = VISC ? 6 : 5;          // windowed primitives (T only for the heat flux)
+  const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
+  const int nseg = (nd + seg - 1) / seg;
+  const long long total = (long long)n1 * n2 * nseg;
+  const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
+  const int nc = g.ncell;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t % n1);
+    const long long r = t / n1;
+    const int i2 = (int)(r % n2);
+    const int sg = (int)(r / n2);
+    int c[3];
+    c[A1] = i1 + g.h[A1];
+    c[A2] = i2 + g.h[A2];
+    const int a0 = g.h[D] + sg * seg;
+    const int a1 = min(a0 + seg, g.h[D] + nd);
+    c[D] = a0 - 1;
+    int cell = c[0] + c[1] * g.sy + c[2] * g.sz;   // cell a = a0 - 1
+    // window D_{a-2 .. a+2} for the first face a0 - 1/2
+    float Dw[6][5];
+#pragma unroll
+    for (int v = 0; v < NVW; ++v)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Dw[v][k] = diff32(W + v * nc, cell + (k - 2) * s, s);
+    double Fp[5], F[5];
+    face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, cell, s, a0 - 1, Dw, g, ph, Fp);
+    for (int a = a0; a < a1; ++a) {
+      cell += s;
+#pragma unroll
+      for (int v = 0; v < NVW; ++v) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Dw[v][k] = Dw[v][k + 1];
+        Dw[v][4] = diff32(W + v * nc, cell + 2 * s, s);
+      }
+      face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, cell, s, a, Dw, g, ph, F);
+      const double id = g.idx[D][a];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double val = -(F[v] - Fp[v]) * id;
+        double* dst = R + v * nc + cell;
+        *dst = accumulate ? *dst + val : val;
+        Fp[v] = F[v];
+      }
+    }
+  }
+}
+
+// centre velocity gradients in FP32 from the FP32 primitives (fourth-order central)
+__global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
+  int lo[3], ext[3];
+  for (int a = 0; a < 3; ++a) {
+    const int m = a < g.ndim ? 2 : 0;
+    lo[a] = g.h[a] - m;
+    ext[a] = g.n[a] + 2 * m;
+  }
+  const int total = ext[0] * ext[1] * ext[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int c[3];
+    c[0] = lo[0] + t % ext[0];
+    const int r = t / ext[0];
+    c[1] = lo[1] + r % ext[1];
+    c[2] = lo[2] + r / ext[1];
+    const int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
+    for (int b = 0; b < 3; ++b) {
+      const bool inb = b < g.ndim && c[b] >= g.h[b] && c[b] < g.h[b] + g.n[b];
+      const int s = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
+      const float m = inb ? (float)g.mc[b][c[b]] : 0.0f;
+      for (int comp = 0; comp < 3; ++comp) {
+        float d = 0.0f;
+        if (inb) {
+          const float* f = W32 + (1 + comp) * g.ncell + cell;
+          d = ((f[-2 * s] - f[2 * s]) + 8.0f * (f[s] - f[-s])) * (1.0f / 12.0f) * m;
+        }
+        G32[(comp * 3 + b) * g.ncell + cell] = d;
+      }
+    }
+  }
+}
+
+constexpr int kDtBlock = 256;
+
+// CFL partial minima from the FP32 primitives (the time step needs no more than FP32 accuracy)
+__global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, Phys ph,
+                                                           double* __restrict__ partial) {
+  const int total = g.n[0] * g.n[1] * g.n[2];
+  const int nc = g.ncell;
+  float best = __int_as_float(0x7f800000);
+  const float gam = (float)ph.gamma, k = (float)ph.dt_visc_k;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int i = t % g.n[0];
+    const int r = t / g.n[0];
+    const int j = r % g.n[1];
+    const int kk = r / g.n[1];
+    const int ci[3] = {i + g.h[0], j + g.h[1], kk + g.h[2]};
+    const int c = ci[0] + ci[1] * g.sy + ci[2] * g.sz;
+    const float rho = W32[c], p = W32[4 * nc + c];
+    const float cs = sqrtf(gam * p / rho);
+    float nu = 0.0f;
+    if (ph.visc != FLUID_VISC_NONE) nu = viscosity_f(W32[5 * nc + c], ph) / rho;
+    for (int d = 0; d < g.ndim; ++d) {
+      const float dx = (float)g.dx[d][ci[d]];
+      best = fminf(best, dx / (fabsf(W32[(1 + d) * nc + c]) + cs));
+      if (ph.visc != FLUID_VISC_NONE) best = fminf(best, dx * dx / (k * nu));
+    }
+  }
+  __shared__ float sm[kDtBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_down_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : __int_as_float(0x7f800000);
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_down_sync(0xffffffffu, best, o));
+    if (threadIdx.x == 0) partial[blockIdx.x] = (double)best;
+  }
+}
+
+template <int D, int SCHEME, bool VISC>
+cudaError_t launch_t(const double* W, const float* W32, const float* G32, double* R, const Geo& g,
+                     const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  constexpr int A1 = (D == 0) ? 1 : 0;
+  constexpr int A2 = (D == 2) ? 1 : 2;
+  const long long lines = (long long)g.n[A1] * g.n[A2];
+  if (block <= 0) block = 128;
+  if (seg <= 0) {
+    seg = 64;
+    while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
+  }
+  const long long total = lines * ((g.n[D] + seg - 1) / seg);
+  k_face_mixed<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(W, W32, G32, R, g, ph,
+                                                                           accumulate, seg);
+  return cudaGetLastError();
+}
+
+template <int SCHEME, bool VISC>
+cudaError_t launch_sv(int D, const double* W, const float* W32, const float* G32, double* R,
+                      const Geo& g, const Phys& ph, int accumulate, int block, int seg,
+                      cudaStream_t st) {
+  if (D == 0) return launch_t<0, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
+  if (D == 1) return launch_t<1, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
+  return launch_t<2, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
+}
+
+}  // namespace
+
+cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
+                              const Geo& g, const Phys& ph, int accumulate, int block, int seg,
+                              cudaStream_t st) {
+  const bool visc = ph.visc != FLUID_VISC_NONE;
+  if (ph.weno == FLUID_WENO_JS)
+    return visc ? launch_sv<FLUID_WENO_JS, true>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st)
+                : launch_sv<FLUID_WENO_JS, false>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st);
+  return visc ? launch_sv<FLUID_WENO_Z, true>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st)
+              : launch_sv<FLUID_WENO_Z, false>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st);
+}
+
+cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st) {
+  long long total = 1;
+  for (int a = 0; a < 3; ++a) total *= g.n[a] + (a < g.ndim ? 4 : 0);
+  k_grad32<<<grid_for(total, 256), 256, 0, st>>>(W32, G32, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
+                                int nparts, cudaStream_t st) {
+  k_dt_partial32<<<nparts, kDtBlock, 0, st>>>(W32, g, ph, partial);
+  return cudaGetLastError();
+}
+
+}  // namespace fl

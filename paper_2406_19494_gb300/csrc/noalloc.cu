@@ -136,6 +136,10 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
     put_msg(errbuf, errlen, "U and R must not alias");
     return FLUID_EINVAL;
   }
+  if (c.precision != FLUID_PREC_FP64) {
+    put_msg(errbuf, errlen, "the allocation-free entry point computes in FP64 only");
+    return FLUID_ENOTSUP;
+  }
   for (int a = 0; a < c.ndim; ++a)
     for (int s = 0; s < 2; ++s)
       if (c.bc[a][s] == FLUID_BC_INFLOW) {
@@ -271,7 +275,7 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
     k_noalloc_wall<<<4, 128, 0, st>>>(A);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = fl::launch_prim_bc(U_dev, W, g, ph, bc, ctl, st);
+  if (e == cudaSuccess) e = fl::launch_prim_bc(U_dev, W, nullptr, g, ph, bc, ctl, st);
   if (e == cudaSuccess && visc) e = fl::launch_grad(W, G, g, st);
   for (int d = 0; e == cudaSuccess && d < g.ndim; ++d)
     e = fl::launch_face(d, W, G, R_dev, g, ph, d > 0, 0, 0, st);

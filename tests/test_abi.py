@@ -53,7 +53,7 @@ def _create(lib, cfg):
     (lambda c: c.bc[0].__setitem__(1, native.BC["wall"]), "periodic boundaries must pair"),
     (lambda c: setattr(c, "gamma", 1.0), "gamma"),
     (lambda c: setattr(c, "struct_size", 8), "struct_size"),
-    (lambda c: setattr(c, "precision", 7), "FP64"),
+    (lambda c: setattr(c, "precision", 7), "precision"),
     (lambda c: setattr(c, "weno", 9), "WENO"),
     (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
 ])

@@ -1,0 +1,195 @@
+"""Mixed-precision path (FLUID_PREC_MIXED) against the FP64 oracle and the FP64 path.
+
+Stated bounds:
+  * right-hand side: per variable max |R_mixed - R_oracle| / max |R_oracle| <= 1e-5;
+  * one RK3 step: max |U_mixed - U_oracle| <= 1e-5 max |U_oracle^{n+1} - U^n| (error relative to the
+    step's increment);
+  * derived results after many steps, relative to the FP64 path (itself equal to the oracle to
+    1e-12 per step): the TGV kinetic-energy dissipation rate, and the wall shear stress and wall
+    heat flux of the channel and of the porous boundary layer, each <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from helpers import padded_state
+from oracle import ns_fv as nf
+from paper_2406_19494_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_RHS = 1e-5
+TOL_STEP = 1e-5
+TOL_DERIVED = 1e-5
+P = ("periodic", "periodic")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19494_gb300 import build
+    build.build()
+
+
+def Solver(c, precision):
+    from paper_2406_19494_gb300.solver import Solver as S
+    return S(c, precision=precision)
+
+
+CASES = {
+    "sod1d": lambda: wl.sod_case(200),
+    "periodic3d_z_power": lambda: wl.random_box(3, (20, 18, 16)),
+    "periodic3d_js_const": lambda: wl.random_box(3, (17, 13, 11), weno="js", visc="constant"),
+    "channel3d_walls_force": lambda: wl.random_box(3, (16, 20, 12), bc=(P, ("wall", "wall"), P),
+                                                     stretch=("uniform", "tanh2", "uniform"),
+                                                     beta=(0.0, 2.0, 0.0), body_force=(0.05, 0.01, -0.02),
+                                                     t_wall=((1, 1), (2.5, 2.2), (1, 1))),
+    "bl2d_porous": lambda: wl.random_box(2, (24, 16, 1), bc=(("zero_gradient", "zero_gradient"),
+                                                             ("porous", "zero_gradient"), P),
+                                         stretch=("uniform", "tanh1", "uniform"), beta=(0, 2.2, 0),
+                                         visc="sutherland", t_wall=((1, 1), (2.5, 1), (1, 1)),
+                                         porous=dict(axis=1, side=0, begin=4, count=12, A=0.05,
+                                                     kappa=3.0, phi0=0.1)),
+}
+
+
+def _state(name, seed):
+    c = CASES[name]()
+    if name == "sod1d":
+        case = nf.Case(c)
+        grid = nf.Grid(case)
+        U = nf.prim_to_cons(wl.sod_prims(grid.axes[0].xc)[:, None, None, :], case)
+        return c, case, grid, U
+    case, grid, U = padded_state(c, seed=seed)
+    return c, case, grid, U
+
+
+def _tgv_state(n, perturb_seed=None):
+    c = wl.tgv_case(n)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    W = wl.tgv_prims(c, *[grid.axes[a].xc[3:-3] for a in range(3)])
+    if perturb_seed is not None:
+        r = wl.uniform01(perturb_seed, W.size).reshape(W.shape) * 2 - 1
+        W = W.copy()
+        W[0] *= 1 + 0.05 * r[0]
+        W[1:4] += 0.05 * r[1:4]
+        W[4] *= 1 + 0.05 * r[4]
+    U = nf.prim_to_cons(np.pad(W, [(0, 0)] + [(3, 3)] * 3, mode="edge"), case)
+    return c, case, grid, U
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_rhs_against_oracle(name):
+    c, case, grid, U = _state(name, seed=0)
+    R_ref = nf.rhs(U.copy(), case, grid)
+    s = Solver(c, "mixed")
+    R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    s.check()
+    inner = (slice(None),) + case.interior()
+    for v in range(5):
+        m = np.max(np.abs(R_ref[inner][v]))
+        err = np.max(np.abs(R[inner][v] - R_ref[inner][v]))
+        assert err <= TOL_RHS * m, (name, v, err / m)
+
+
+def test_mixed_rhs_low_mach_tgv():
+    """Ma 0.1 Taylor-Green state (perturbed so that R is not a pure cancellation): the delta form
+    keeps the FP32 error relative to R, not to the pressure or enthalpy."""
+    c, case, grid, U = _tgv_state(32, perturb_seed=5)
+    R_ref = nf.rhs(U.copy(), case, grid)
+    s = Solver(c, "mixed")
+    R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    inner = (slice(None),) + case.interior()
+    for v in range(5):
+        m = np.max(np.abs(R_ref[inner][v]))
+        assert np.max(np.abs(R[inner][v] - R_ref[inner][v])) <= TOL_RHS * m, v
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_step_against_oracle(name):
+    c, case, grid, U = _state(name, seed=3)
+    dt = nf.cfl_dt(U, case, grid)
+    c2 = dict(c, dt_fixed=dt)
+    U1 = nf.rk3_step(U.copy(), dt, nf.Case(c2), grid)
+    s = Solver(c2, "mixed")
+    Ud = torch.from_numpy(U).cuda()
+    s.step(Ud, 1)
+    s.check()
+    inner = (slice(None),) + case.interior()
+    got = Ud.cpu().numpy()[inner]
+    inc = np.max(np.abs(U1[inner] - U[inner]))
+    assert np.max(np.abs(got - U1[inner])) <= TOL_STEP * inc
+
+
+def _run_pair(c, U0, nsteps, phi=None):
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(c, prec)
+        if phi is not None:
+            s.set_wall_params(torch.from_numpy(phi).cuda())
+        Ud = torch.from_numpy(U0.copy()).cuda()
+        s.step(Ud, nsteps)
+        s.check()
+        out[prec] = Ud.cpu().numpy()
+    return out
+
+
+def test_mixed_tgv_kinetic_energy_dissipation():
+    """-dE_k/dt of the 64^3 Taylor-Green vortex after 200 steps (t ~ 1.1), FP64 vs mixed."""
+    c, case, grid, U0 = _tgv_state(64)
+    dt = 0.9 * nf.cfl_dt(U0, case, grid)
+    c = dict(c, dt_fixed=dt)
+    case = nf.Case(c)
+    out = _run_pair(c, U0, 200)
+    rates = {}
+    for prec, U in out.items():
+        s = Solver(c, "fp64")
+        R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+        rates[prec] = -nf.kinetic_energy_rate(U, R, case, grid)
+    rel = abs(rates["mixed"] - rates["fp64"]) / abs(rates["fp64"])
+    assert rates["fp64"] > 0 and rel <= TOL_DERIVED, (rates, rel)
+
+
+def test_mixed_channel_wall_shear_and_heat_flux():
+    """Channel (Ma_b 1.5, Re_b 3000, 32 x 48 x 24, tanh walls, 5 % noise), 150 steps: mean wall
+    shear and mean wall heat flux on both walls, FP64 vs mixed."""
+    c = wl.channel_case(32, 48, 24)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    W = wl.channel_prims(c, *[grid.axes[a].xc[3:-3] for a in range(3)], seed=0)
+    U0 = nf.prim_to_cons(np.pad(W, [(0, 0)] + [(3, 3)] * 3, mode="edge"), case)
+    out = _run_pair(c, U0, 150)
+    res = {}
+    for prec, U in out.items():
+        q0, t0 = nf.wall_fluxes(U, case, grid, 1, 0)
+        q1, t1 = nf.wall_fluxes(U, case, grid, 1, 1)
+        res[prec] = (np.mean(t0) - np.mean(t1), np.mean(q0) - np.mean(q1))
+    for k in range(2):
+        rel = abs(res["mixed"][k] - res["fp64"][k]) / abs(res["fp64"][k])
+        assert rel <= TOL_DERIVED, (k, res, rel)
+
+
+def test_mixed_porous_bl_wall_heat_flux():
+    """Ma 6 porous boundary layer (128 x 48), 200 steps: integrated wall heat flux, FP64 vs mixed."""
+    c = wl.porous_bl_case(128, 48)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xc, yc = grid.axes[0].xc[3:-3], grid.axes[1].xc[3:-3]
+    W = wl.porous_bl_prims(c, xc, yc)
+    U0 = nf.prim_to_cons(np.pad(W, [(0, 0), (0, 0), (3, 3), (3, 3)], mode="edge"), case)
+    phi = wl.porous_phi(c, seed=0)
+    prof = wl.porous_bl_inflow(c, grid.axes[1].xc)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(c, prec)
+        s.set_wall_params(torch.from_numpy(phi).cuda())
+        s.set_inflow(0, 0, torch.from_numpy(prof).cuda())
+        Ud = torch.from_numpy(U0.copy()).cuda()
+        s.step(Ud, 200)
+        s.check()
+        out[prec] = Ud.cpu().numpy()
+    J = {p: nf.wall_heat_loss(U, case, grid, 1, 0, phi, {(0, 0): prof}) for p, U in out.items()}
+    rel = abs(J["mixed"] - J["fp64"]) / abs(J["fp64"])
+    assert rel <= TOL_DERIVED, (J, rel)
