@@ -285,6 +285,67 @@ __global__ void __launch_bounds__(128) k_face_mixed(const double* __restrict__ W
   }
 }
 
+// x-direction variant: lanes map to consecutive faces of one grid row so that every global load is
+// coalesced.  A warp covers 31 cells (32 faces) of a row; the cell differences D_j of the tile
+// (36 per primitive) are formed once in shared memory, each lane builds its face from that window,
+// and the flux difference takes the neighbouring face's flux from shared memory.
+constexpr int kXCells = 31;
+constexpr int kXRows = 4;
+
+template <int SCHEME, bool VISC>
+__global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(const double* __restrict__ W,
+                                                              const float* __restrict__ W32,
+                                                              const float* __restrict__ G32,
+                                                              double* __restrict__ R, Geo g,
+                                                              Phys ph, int accumulate) {
+  constexpr int NVW = VISC ? 6 : 5;
+  constexpr int ND = kXCells + 5;               // D_j for j in [x0-3, x0+kXCells+1]
+  __shared__ float sD[kXRows][6][ND];
+  __shared__ double sF[kXRows][5][kXCells + 1];
+  const int lane = threadIdx.x, row = threadIdx.y;
+  const int n0 = g.n[0], h0 = g.h[0];
+  const int line = blockIdx.y * kXRows + row;
+  const bool live = line < g.n[1] * g.n[2];
+  const int j1 = live ? line % g.n[1] : 0, j2 = live ? line / g.n[1] : 0;
+  const int x0 = h0 + blockIdx.x * kXCells;      // first interior cell of the tile (padded index)
+  const int nc = g.ncell;
+  const int rowbase = (j1 + g.h[1]) * g.sy + (j2 + g.h[2]) * g.sz;
+  const int xend = h0 + n0;                      // one past the last interior cell
+  if (live) {
+    for (int k = lane; k < ND; k += 32) {
+      const int j = x0 - 3 + k;
+      const bool ok = j + 1 <= xend + 2;         // W index j + 1 stays inside the padded row
+#pragma unroll
+      for (int v = 0; v < NVW; ++v) sD[row][v][k] = ok ? diff32(W + v * nc, rowbase + j, 1) : 0.0f;
+    }
+  }
+  __syncthreads();
+  const int a = x0 - 1 + lane;                   // this lane's face is a + 1/2
+  if (live && a < xend) {
+    float Dw[6][5];
+#pragma unroll
+    for (int v = 0; v < NVW; ++v)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Dw[v][k] = sD[row][v][lane + k];
+    double F[5];
+    face_flux_mixed<0, SCHEME, VISC>(W, W32, G32, rowbase + a, 1, a, Dw, g, ph, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sF[row][v][lane] = F[v];
+  }
+  __syncthreads();
+  const int cx = x0 + lane;                      // cell of the divergence
+  if (live && lane < kXCells && cx < xend) {
+    const double id = g.idx[0][cx];
+    const int cell = rowbase + cx;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double val = -(sF[row][v][lane + 1] - sF[row][v][lane]) * id;
+      double* dst = R + v * nc + cell;
+      *dst = accumulate ? *dst + val : val;
+    }
+  }
+}
+
 // centre velocity gradients in FP32 from the FP32 primitives (fourth-order central)
 __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
   int lo[3], ext[3];
@@ -375,7 +436,12 @@ template <int SCHEME, bool VISC>
 cudaError_t launch_sv(int D, const double* W, const float* W32, const float* G32, double* R,
                       const Geo& g, const Phys& ph, int accumulate, int block, int seg,
                       cudaStream_t st) {
-  if (D == 0) return launch_t<0, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
+  if (D == 0) {
+    const long long lines = (long long)g.n[1] * g.n[2];
+    const dim3 grid((g.n[0] + kXCells - 1) / kXCells, (unsigned)((lines + kXRows - 1) / kXRows));
+    k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(W, W32, G32, R, g, ph, accumulate);
+    return cudaGetLastError();
+  }
   if (D == 1) return launch_t<1, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
   return launch_t<2, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
 }

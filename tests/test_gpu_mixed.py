@@ -80,10 +80,15 @@ def _tgv_state(n, perturb_seed=None):
     return c, case, grid, U
 
 
+def _phi0(case):
+    """The solver's default porous parameters (phi_i = phi0) for the oracle."""
+    return None if not case.porous else np.full(case.porous["count"], case.porous["phi0"])
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_rhs_against_oracle(name):
     c, case, grid, U = _state(name, seed=0)
-    R_ref = nf.rhs(U.copy(), case, grid)
+    R_ref = nf.rhs(U.copy(), case, grid, _phi0(case))
     s = Solver(c, "mixed")
     R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
     s.check()
@@ -112,7 +117,7 @@ def test_mixed_step_against_oracle(name):
     c, case, grid, U = _state(name, seed=3)
     dt = nf.cfl_dt(U, case, grid)
     c2 = dict(c, dt_fixed=dt)
-    U1 = nf.rk3_step(U.copy(), dt, nf.Case(c2), grid)
+    U1 = nf.rk3_step(U.copy(), dt, nf.Case(c2), grid, _phi0(case))
     s = Solver(c2, "mixed")
     Ud = torch.from_numpy(U).cuda()
     s.step(Ud, 1)
