@@ -577,7 +577,7 @@ int fluid_tune_faces(fluid_solver* s, int block, int seg) {
   if (!s) return FLUID_EINVAL;
   if (block != 0 && (block < 32 || block > 128 || block % 32 != 0))
     return fail(s, FLUID_EINVAL, "block must be 0 or a multiple of 32 in [32, 128]");
-  if (seg < 0) return fail(s, FLUID_EINVAL, "seg must be >= 0");
+  if (seg < 0 && !s->mixed) return fail(s, FLUID_EINVAL, "seg must be >= 0 for the FP64 path");
   s->face_block = block;
   s->face_seg = seg;
   return FLUID_OK;

@@ -346,6 +346,74 @@ __global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(const double* __re
   }
 }
 
+// y / z variant: lanes map to 32 consecutive x columns (coalesced loads); a block covers 31 cells
+// along the face axis D (32 faces) of those columns at one index of the remaining axis.  The cell
+// differences along D and the face fluxes are staged in shared memory; each of the 8 warps takes
+// every 8th face and every 8th cell of the tile.
+constexpr int kTCells = 31;
+constexpr int kTWarps = 8;
+
+template <int D, int SCHEME, bool VISC>
+__global__ void __launch_bounds__(32 * kTWarps) k_face_mixed_t(const double* __restrict__ W,
+                                                               const float* __restrict__ W32,
+                                                               const float* __restrict__ G32,
+                                                               double* __restrict__ R, Geo g,
+                                                               Phys ph, int accumulate) {
+  static_assert(D == 1 || D == 2, "tiles along y or z");
+  constexpr int NVW = VISC ? 6 : 5;
+  constexpr int ND = kTCells + 5;
+  constexpr int OTHER = D == 1 ? 2 : 1;                     // the axis that is neither x nor D
+  extern __shared__ unsigned char smem_raw[];
+  float (*sD)[ND][32] = reinterpret_cast<float (*)[ND][32]>(smem_raw);                  // [6][ND][32]
+  double (*sF)[kTCells + 1][32] =
+      reinterpret_cast<double (*)[kTCells + 1][32]>(smem_raw + sizeof(float) * 6 * ND * 32);  // [5][32][32]
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int x = g.h[0] + blockIdx.x * 32 + lane;
+  const bool xok = x < g.h[0] + g.n[0];
+  const int d0 = g.h[D] + blockIdx.y * kTCells;             // first cell of the tile along D
+  const int dend = g.h[D] + g.n[D];
+  const int o = g.h[OTHER] + blockIdx.z;
+  const int s = D == 1 ? g.sy : g.sz;
+  const int so = OTHER == 1 ? g.sy : g.sz;
+  const int nc = g.ncell;
+  const int colbase = x + o * so;                           // cell index with D coordinate 0
+  for (int k = warp; k < ND; k += kTWarps) {
+    const int j = d0 - 3 + k;
+    const bool ok = xok && j + 1 <= dend + 2;
+#pragma unroll
+    for (int v = 0; v < NVW; ++v) sD[v][k][lane] = ok ? diff32(W + v * nc, colbase + j * s, s) : 0.0f;
+  }
+  __syncthreads();
+  for (int f = warp; f <= kTCells; f += kTWarps) {          // face a + 1/2, a = d0 - 1 + f
+    const int a = d0 - 1 + f;
+    if (!xok || a >= dend) continue;
+    float Dw[6][5];
+#pragma unroll
+    for (int v = 0; v < NVW; ++v)
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) Dw[v][kk] = sD[v][f + kk][lane];
+    double F[5];
+    face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, colbase + a * s, s, a, Dw, g, ph, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sF[v][f][lane] = F[v];
+  }
+  __syncthreads();
+  for (int cc = warp; cc < kTCells; cc += kTWarps) {
+    const int a = d0 + cc;
+    if (!xok || a >= dend) continue;
+    const double id = g.idx[D][a];
+    const int cell = colbase + a * s;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double val = -(sF[v][cc + 1][lane] - sF[v][cc][lane]) * id;
+      double* dst = R + v * nc + cell;
+      *dst = accumulate ? *dst + val : val;
+    }
+  }
+}
+
+constexpr size_t kTSmem = sizeof(float) * 6 * (kTCells + 5) * 32 + sizeof(double) * 5 * (kTCells + 1) * 32;
+
 // centre velocity gradients in FP32 from the FP32 primitives (fourth-order central)
 __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
   int lo[3], ext[3];
@@ -442,8 +510,26 @@ cudaError_t launch_sv(int D, const double* W, const float* W32, const float* G32
     k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(W, W32, G32, R, g, ph, accumulate);
     return cudaGetLastError();
   }
-  if (D == 1) return launch_t<1, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
-  return launch_t<2, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, seg, st);
+  const int other = D == 1 ? 2 : 1;
+  if (seg < 0 || g.n[other] > 65535) {   // register-window marching kernels
+    const int sg = seg < 0 ? -seg : 0;
+    if (D == 1) return launch_t<1, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, sg, st);
+    return launch_t<2, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, sg, st);
+  }
+  const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + kTCells - 1) / kTCells, g.n[other]);
+  // the tile needs more than the default 48 KB of dynamic shared memory (attribute is per device)
+  if (D == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    if (e != cudaSuccess) return e;
+    k_face_mixed_t<1, SCHEME, VISC><<<grid, dim3(32, kTWarps), kTSmem, st>>>(W, W32, G32, R, g, ph, accumulate);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    if (e != cudaSuccess) return e;
+    k_face_mixed_t<2, SCHEME, VISC><<<grid, dim3(32, kTWarps), kTSmem, st>>>(W, W32, G32, R, g, ph, accumulate);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
