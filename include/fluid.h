@@ -95,6 +95,8 @@ enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
  *                  FLUID_BC_POROUS: wall cells porous_begin .. porous_begin + porous_count - 1 along
  *                  the first other active axis carry v_w,i = (A / phi0) phi_i sin(2 pi kappa x_i)
  *                  (Section 3.2's disturbance v = A sin(2 pi kappa x) when phi_i = phi0)
+ *   adjoint        nonzero: allocate the adjoint scratch (about 92 doubles per padded cell) so
+ *                  that the fluid_adjoint_* entry points and fluid_wall_heat_loss can be used
  */
 typedef struct fluid_config {
   uint32_t struct_size;
@@ -114,6 +116,8 @@ typedef struct fluid_config {
   double body_force[3];
   double cfl, dt_fixed;
   double porous_A, porous_kappa, porous_phi0;
+  int32_t adjoint;          /* nonzero: also allocate the scratch of the adjoint entry points */
+  int32_t reserved;
 } fluid_config;
 
 typedef struct fluid_solver fluid_solver; /* opaque; owned by the library */
@@ -166,6 +170,37 @@ int fluid_compute_dt(fluid_solver* s, const double* U_dev, double* dt_dev, void*
  * solver time and last dt live on the device.  Halos of U are left unspecified. */
 int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* stream);
 
+/* One RK3 step like fluid_step (one step, no t_end) that also writes the two intermediate stage
+ * states U1 = Un + dt R(Un) and U2 = 3/4 Un + 1/4 (U1 + dt R(U1)) to the caller's buffers (same
+ * shape as U, interior written); used to replay a segment before its adjoint. */
+int fluid_step_stages(fluid_solver* s, double* U_dev, double* U1_dev, double* U2_dev, void* stream);
+
+/* ---- discrete adjoint (the gradient of Section 3.2's end-to-end optimisation through the
+ * differentiable disturbance wall, written by hand instead of automatic differentiation).  Needs
+ * cfg.adjoint != 0 and, for the step adjoint, a frozen time step (cfg.dt_fixed > 0).  FP64 only. */
+
+/* Vector-Jacobian product of the right-hand side (the operation of fluid_rhs) at state U: given a
+ * cotangent mu of R on the interior cells (padded shape; halos ignored), writes
+ * gU = (dR/dU)^T mu on the interior (halos untouched) and, if gphi_dev is not NULL and the
+ * configuration has a porous face, adds (dR/dphi)^T mu to gphi_dev[0 .. porous_count-1].  The
+ * WENO5 weights and the HLLC branch are differentiated exactly; ties take the forward's choice. */
+int fluid_adjoint_rhs(fluid_solver* s, const double* U_dev, const double* mu_dev, double* gU_dev,
+                      double* gphi_dev, void* stream);
+
+/* Adjoint of one RK3 step with the frozen dt: on input lam holds dJ/dU^{n+1} (interior), on output
+ * dJ/dU^n; (dU^{n+1}/dphi)^T lam is added to gphi_dev (may be NULL).  U1_dev / U2_dev are the stage
+ * states of the step from fluid_step_stages, or NULL to recompute them from Un.  lam must not
+ * alias the other arrays. */
+int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_dev,
+                       const double* U2_dev, double* lam_dev, double* gphi_dev, void* stream);
+
+/* Integrated wall heat flux J = sum over the wall cells of q_w * face area, q_w = -lambda(T_w)
+ * dT/dn by the fourth-order normal stencil through the mirrored halo (derivative along +axis), on
+ * the isothermal or porous face (axis, side).  Writes J to *J_dev (device) and, if dJdU_dev is not
+ * NULL, dJ/dU on the whole padded array (zero except the two wall-adjacent cell layers). */
+int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int side, double* J_dev,
+                         double* dJdU_dev, void* stream);
+
 /* Synchronise `stream` and read the solver time and the last step's dt (either may be NULL). */
 int fluid_get_time(fluid_solver* s, double* t, double* last_dt, void* stream);
 
@@ -193,7 +228,9 @@ enum {
   FLUID_KERNEL_STAGE = 5,    /* RK3 stage combination (+ source) */
   FLUID_KERNEL_DT = 6,       /* CFL reduction */
   FLUID_KERNEL_SOURCE = 7,   /* body-force source of fluid_rhs */
-  FLUID_KERNEL_COUNT = 8
+  FLUID_KERNEL_ADJ_FACE = 8, /* adjoint face kernels and their gathers */
+  FLUID_KERNEL_ADJ_CELL = 9, /* adjoint per-cell kernels (source, halos, primitives, phi) */
+  FLUID_KERNEL_COUNT = 10
 };
 
 /* Kernel timing.  While enabled, every kernel the solver launches is bracketed by a CUDA event

@@ -1,0 +1,381 @@
+// Reverse-mode (vector-Jacobian) forms of the per-face and per-cell arithmetic in flux_math.cuh,
+// written by hand.  Each *_vjp function recomputes the forward intermediates it needs and returns
+// the cotangents of its inputs given the cotangent of its output.  Non-smooth points follow the
+// forward's own decisions: the HLLC branch and the Einfeldt min / max take the derivative of the
+// selected argument (first argument on ties), |b0 - b2| in WENO5-Z has derivative +1 at zero.
+// The WENO weights are differentiated exactly (no frozen weights).
+#pragma once
+
+#include "flux_math.cuh"
+
+namespace fl {
+
+// ------------------------------------------------------------------------------------------------
+// WENO5: cotangent of the five stencil values q_{i-2..i+2} given the cotangent of the face value
+// ------------------------------------------------------------------------------------------------
+template <int SCHEME>
+FL_HD void weno5_vjp(const double q[5], double eps, double g_out, double gq[5]) {
+  const double C0 = 2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2];
+  const double C1 = -q[1] + 5.0 * q[2] + 2.0 * q[3];
+  const double C2 = 2.0 * q[2] + 5.0 * q[3] - q[4];
+  const double t0 = q[0] - 2.0 * q[1] + q[2], s0 = q[0] - 4.0 * q[1] + 3.0 * q[2];
+  const double t1 = q[1] - 2.0 * q[2] + q[3], s1 = q[1] - q[3];
+  const double t2 = q[2] - 2.0 * q[3] + q[4], s2 = 3.0 * q[2] - 4.0 * q[3] + q[4];
+  const double b0 = k1312 * t0 * t0 + 0.25 * s0 * s0;
+  const double b1 = k1312 * t1 * t1 + 0.25 * s1 * s1;
+  const double b2 = k1312 * t2 * t2 + 0.25 * s2 * s2;
+  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  double a0, a1, a2, ge0, ge1, ge2, gb0 = 0.0, gb2 = 0.0;
+  // face value = N / (6 S), N = sum a_k C_k, S = sum a_k
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0, sg = 1.0;
+  if (SCHEME == FLUID_WENO_JS) {
+    const double i0 = 1.0 / e0, i1 = 1.0 / e1, i2 = 1.0 / e2;
+    a0 = 0.1 * i0 * i0; a1 = 0.6 * i1 * i1; a2 = 0.3 * i2 * i2;
+    r0 = i0; r1 = i1; r2 = i2;
+  } else {
+    const double tau = b0 - b2 < 0.0 ? b2 - b0 : b0 - b2;
+    sg = b0 - b2 < 0.0 ? -1.0 : 1.0;
+    r0 = tau / e0; r1 = tau / e1; r2 = tau / e2;
+    a0 = 0.1 * (1.0 + r0 * r0); a1 = 0.6 * (1.0 + r1 * r1); a2 = 0.3 * (1.0 + r2 * r2);
+  }
+  const double S = a0 + a1 + a2;
+  const double N = a0 * C0 + a1 * C1 + a2 * C2;
+  const double out = N / (6.0 * S);
+  const double gN = g_out / (6.0 * S);
+  const double gS = -g_out * out / S;
+  const double ga0 = gN * C0 + gS, ga1 = gN * C1 + gS, ga2 = gN * C2 + gS;
+  const double gC0 = gN * a0, gC1 = gN * a1, gC2 = gN * a2;
+  if (SCHEME == FLUID_WENO_JS) {
+    // a_k = d_k / e_k^2: da/de = -2 a / e
+    ge0 = -2.0 * ga0 * a0 * r0;
+    ge1 = -2.0 * ga1 * a1 * r1;
+    ge2 = -2.0 * ga2 * a2 * r2;
+  } else {
+    // a_k = d_k (1 + r_k^2), r_k = tau / e_k
+    const double gr0 = ga0 * 0.2 * r0, gr1 = ga1 * 1.2 * r1, gr2 = ga2 * 0.6 * r2;
+    const double gtau = gr0 / e0 + gr1 / e1 + gr2 / e2;
+    ge0 = -gr0 * r0 / e0;
+    ge1 = -gr1 * r1 / e1;
+    ge2 = -gr2 * r2 / e2;
+    gb0 += sg * gtau;
+    gb2 -= sg * gtau;
+  }
+  gb0 += ge0;
+  const double gb1 = ge1;
+  gb2 += ge2;
+  const double gt0 = gb0 * 2.0 * k1312 * t0, gs0 = gb0 * 0.5 * s0;
+  const double gt1 = gb1 * 2.0 * k1312 * t1, gs1 = gb1 * 0.5 * s1;
+  const double gt2 = gb2 * 2.0 * k1312 * t2, gs2 = gb2 * 0.5 * s2;
+  gq[0] = 2.0 * gC0 + gt0 + gs0;
+  gq[1] = -7.0 * gC0 - gC1 - 2.0 * gt0 - 4.0 * gs0 + gt1 + gs1;
+  gq[2] = 11.0 * gC0 + 5.0 * gC1 + 2.0 * gC2 + gt0 + 3.0 * gs0 - 2.0 * gt1 + gt2 + 3.0 * gs2;
+  gq[3] = 2.0 * gC1 + 5.0 * gC2 + gt1 - gs1 - 2.0 * gt2 - 4.0 * gs2;
+  gq[4] = -gC2 + gt2 + gs2;
+}
+
+// ------------------------------------------------------------------------------------------------
+// HLLC along D: cotangents of the left and right primitive states given the flux cotangent
+// ------------------------------------------------------------------------------------------------
+template <int D>
+FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, const double gF[5],
+                    double gwl[5], double gwr[5]) {
+  // ---- forward (same operations as hllc<D>) ----
+  const double rL = wl[0], pL = wl[4], rR = wr[0], pR = wr[4];
+  const double unL = wl[1 + D], unR = wr[1 + D];
+  const double q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+  const double q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+  const double EL = pL * ph.igm1 + 0.5 * rL * q2L;
+  const double ER = pR * ph.igm1 + 0.5 * rR * q2R;
+  const double qL = fl_rsqrt(rL), qR = fl_rsqrt(rR);
+  const double sL = rL * qL, sR = rR * qR;
+  const double irL = qL * qL, irR = qR * qR;
+  const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
+  const double isum = 1.0 / (sL + sR);
+  double ut[3];
+  for (int c = 0; c < 3; ++c) ut[c] = (sL * wl[1 + c] + sR * wr[1 + c]) * isum;
+  const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+  const double Ht = (sL * HL + sR * HR) * isum;
+  const double ct = sqrt(ph.gm1 * (Ht - 0.5 * (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2])));
+  const double utn = ut[D];
+  const double aL = unL - cL, bL = utn - ct;
+  const bool selL = aL <= bL;
+  const double SL = selL ? aL : bL;
+  const double aR = unR + cR, bR = utn + ct;
+  const bool selR = aR >= bR;
+  const double SR = selR ? aR : bR;
+  const double mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const double Nn = pR - pL + unL * mL - unR * mR;
+  const double Dd = mL - mR;
+  const double Ss = Nn / Dd;
+  const bool left = (SL >= 0.0) || (Ss >= 0.0);
+  const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
+  const double r = left ? rL : rR, p = left ? pL : pR, E = left ? EL : ER;
+  const double un = left ? unL : unR, S = left ? SL : SR, m = left ? mL : mR;
+  const double ir = left ? irL : irR;
+  const double* w = left ? wl : wr;
+  const double u[3] = {w[1], w[2], w[3]};
+  const double mn = r * un;
+
+  // ---- reverse ----
+  // cotangents of the selected side's quantities
+  double g_r = 0.0, g_p = 0.0, g_E = 0.0, g_u[3] = {0.0, 0.0, 0.0}, g_S = 0.0, g_m = 0.0;
+  double g_ir = 0.0, g_Ss = 0.0;
+  // Euler flux of the selected side: F0 = mn, F_c = mn u_c (+ p), F4 = un (E + p)
+  double g_mn = gF[0];
+  for (int c = 0; c < 3; ++c) {
+    g_mn += gF[1 + c] * u[c];
+    g_u[c] += gF[1 + c] * mn;
+  }
+  g_p += gF[1 + D];
+  g_u[D] += gF[4] * (E + p);
+  g_E += gF[4] * un;
+  g_p += gF[4] * un;
+  if (star) {
+    const double d = S - Ss;
+    const double q = 1.0 / d;
+    const double fac = m * q;
+    const double A = E * ir, B = Ss - un, Cc = fac * Ss + p * q;
+    const double Es = fac * A + B * Cc;
+    double dU[5];
+    dU[0] = fac - r;
+    for (int c = 0; c < 3; ++c) dU[1 + c] = (fac - r) * u[c];
+    dU[1 + D] = fac * Ss - r * un;
+    dU[4] = Es - E;
+    for (int v = 0; v < 5; ++v) g_S += gF[v] * dU[v];
+    double g_fac = 0.0;
+    // dU0 = fac - r
+    g_fac += gF[0] * S;
+    g_r -= gF[0] * S;
+    for (int c = 0; c < 3; ++c) {
+      const double gd = gF[1 + c] * S;
+      if (c == D) {
+        g_fac += gd * Ss;
+        g_Ss += gd * fac;
+        g_r -= gd * un;
+        g_u[D] -= gd * r;
+      } else {
+        g_fac += gd * u[c];
+        g_r -= gd * u[c];
+        g_u[c] += gd * (fac - r);
+      }
+    }
+    const double gEs = gF[4] * S;
+    g_E -= gF[4] * S;
+    g_fac += gEs * A;
+    const double gA = gEs * fac, gB = gEs * Cc, gCc = gEs * B;
+    g_fac += gCc * Ss;
+    g_Ss += gCc * fac;
+    g_p += gCc * q;
+    double g_q = gCc * p;
+    g_Ss += gB;
+    g_u[D] -= gB;
+    g_E += gA * ir;
+    g_ir += gA * E;
+    g_m += g_fac * q;
+    g_q += g_fac * m;
+    const double g_d = -g_q * q * q;
+    g_S += g_d;
+    g_Ss -= g_d;
+  }
+  // mn = r un
+  g_r += g_mn * un;
+  g_u[D] += g_mn * r;
+
+  // distribute the selected side's cotangents onto L / R intermediates
+  double gSL = 0.0, gSR = 0.0, gmL = 0.0, gmR = 0.0, gEL = 0.0, gER = 0.0, girL = 0.0, girR = 0.0;
+  for (int v = 0; v < 5; ++v) {
+    gwl[v] = 0.0;
+    gwr[v] = 0.0;
+  }
+  double* gw = left ? gwl : gwr;
+  gw[0] += g_r;
+  gw[4] += g_p;
+  for (int c = 0; c < 3; ++c) gw[1 + c] += g_u[c];
+  if (left) {
+    gEL += g_E; gSL += g_S; gmL += g_m; girL += g_ir;
+  } else {
+    gER += g_E; gSR += g_S; gmR += g_m; girR += g_ir;
+  }
+  // Ss = Nn / Dd
+  const double gNn = g_Ss / Dd, gDd = -g_Ss * Ss / Dd;
+  gwr[4] += gNn;
+  gwl[4] -= gNn;
+  gwl[1 + D] += gNn * mL;
+  gmL += gNn * unL + gDd;
+  gwr[1 + D] -= gNn * mR;
+  gmR += -gNn * unR - gDd;
+  // m = rho (S - un)
+  gwl[0] += gmL * (SL - unL);
+  gSL += gmL * rL;
+  gwl[1 + D] -= gmL * rL;
+  gwr[0] += gmR * (SR - unR);
+  gSR += gmR * rR;
+  gwr[1 + D] -= gmR * rR;
+  // Einfeldt bounds
+  double gutn = 0.0, gct = 0.0, gcL = 0.0, gcR = 0.0;
+  if (selL) { gwl[1 + D] += gSL; gcL -= gSL; } else { gutn += gSL; gct -= gSL; }
+  if (selR) { gwr[1 + D] += gSR; gcR += gSR; } else { gutn += gSR; gct += gSR; }
+  // ct = sqrt(gm1 (Ht - |ut|^2 / 2))
+  double gut[3] = {0.0, 0.0, 0.0};
+  gut[D] += gutn;
+  const double gX = ct > 0.0 ? gct / (2.0 * ct) : 0.0;
+  const double gHt = ph.gm1 * gX;
+  for (int c = 0; c < 3; ++c) gut[c] -= ph.gm1 * gX * ut[c];
+  // Ht = (sL HL + sR HR) isum
+  double gsL = gHt * HL * isum, gsR = gHt * HR * isum;
+  const double gHL = gHt * sL * isum, gHR = gHt * sR * isum;
+  double gisum = gHt * (sL * HL + sR * HR);
+  // ut_c = (sL uL_c + sR uR_c) isum
+  for (int c = 0; c < 3; ++c) {
+    gsL += gut[c] * wl[1 + c] * isum;
+    gsR += gut[c] * wr[1 + c] * isum;
+    gwl[1 + c] += gut[c] * sL * isum;
+    gwr[1 + c] += gut[c] * sR * isum;
+    gisum += gut[c] * (sL * wl[1 + c] + sR * wr[1 + c]);
+  }
+  // H = (E + p) ir
+  gEL += gHL * irL;
+  gwl[4] += gHL * irL;
+  girL += gHL * (EL + pL);
+  gER += gHR * irR;
+  gwr[4] += gHR * irR;
+  girR += gHR * (ER + pR);
+  // isum = 1 / (sL + sR)
+  const double gsum = -gisum * isum * isum;
+  gsL += gsum;
+  gsR += gsum;
+  // c = sqrt(gamma p ir)
+  const double gYL = gcL / (2.0 * cL), gYR = gcR / (2.0 * cR);
+  gwl[4] += gYL * ph.gamma * irL;
+  girL += gYL * ph.gamma * pL;
+  gwr[4] += gYR * ph.gamma * irR;
+  girR += gYR * ph.gamma * pR;
+  // s = sqrt(rho), ir = 1 / rho
+  gwl[0] += gsL * 0.5 * qL - girL * irL * irL;
+  gwr[0] += gsR * 0.5 * qR - girR * irR * irR;
+  // E = p / (gamma - 1) + rho |u|^2 / 2
+  gwl[4] += gEL * ph.igm1;
+  gwl[0] += gEL * 0.5 * q2L;
+  gwr[4] += gER * ph.igm1;
+  gwr[0] += gER * 0.5 * q2R;
+  for (int c = 0; c < 3; ++c) {
+    gwl[1 + c] += gEL * rL * wl[1 + c];
+    gwr[1 + c] += gER * rR * wr[1 + c];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// dissipative face flux: cotangents of the stencil inputs given the cotangent gFd of
+// (tau_0D, tau_1D, tau_2D, energy)
+// ------------------------------------------------------------------------------------------------
+template <int D>
+FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double gd[3][4],
+                         const double gb[3][4], int ndim, double mfa, const Phys& ph,
+                         const double gFd[4], double gvel[3][4], double gT[4], double ggd[3][4],
+                         double ggb[3][4]) {
+  const double ci[4] = {-k16th, 9.0 * k16th, 9.0 * k16th, -k16th};
+  const double cn[4] = {k24th * mfa, -27.0 * k24th * mfa, 27.0 * k24th * mfa, -k24th * mfa};
+  double vf[3], Gf[3][3];
+  for (int c = 0; c < 3; ++c) {
+    vf[c] = interp4(vel[c]);
+    Gf[c][D] = dnorm4(vel[c], mfa);
+  }
+  const double Tf = interp4(T);
+  const double dT = dnorm4(T, mfa);
+  bool act[3];
+  for (int b = 0; b < 3; ++b) {
+    act[b] = b != D && b < ndim;
+    if (b == D) continue;
+    Gf[D][b] = act[b] ? interp4(gd[b]) : 0.0;
+    Gf[b][b] = act[b] ? interp4(gb[b]) : 0.0;
+  }
+  const double div = Gf[0][0] + Gf[1][1] + Gf[2][2];
+  const double mu = viscosity(Tf, ph);
+  const double lam = mu * ph.lam_fac;
+  double tau[3];
+  for (int c = 0; c < 3; ++c) {
+    if (c == D) tau[c] = mu * (Gf[D][D] + Gf[D][D]) - (2.0 / 3.0) * mu * div;
+    else tau[c] = mu * (Gf[c][D] + Gf[D][c]);
+  }
+  // reverse
+  double gtau[3], gvf[3], gG[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int c = 0; c < 3; ++c) {
+    gtau[c] = gFd[c] + gFd[3] * vf[c];
+    gvf[c] = gFd[3] * tau[c];
+  }
+  const double glam = gFd[3] * dT;
+  const double gdT = gFd[3] * lam;
+  double gmu = glam * ph.lam_fac, gdiv = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    if (c == D) {
+      gmu += gtau[c] * (2.0 * Gf[D][D] - (2.0 / 3.0) * div);
+      gG[D][D] += gtau[c] * 2.0 * mu;
+      gdiv -= gtau[c] * (2.0 / 3.0) * mu;
+    } else {
+      gmu += gtau[c] * (Gf[c][D] + Gf[D][c]);
+      gG[c][D] += gtau[c] * mu;
+      gG[D][c] += gtau[c] * mu;
+    }
+  }
+  for (int c = 0; c < 3; ++c) gG[c][c] += gdiv;
+  const double gTf = gmu * viscosity_dT(Tf, ph);
+  for (int k = 0; k < 4; ++k) {
+    gT[k] = gTf * ci[k] + gdT * cn[k];
+    for (int c = 0; c < 3; ++c) gvel[c][k] = gvf[c] * ci[k] + gG[c][D] * cn[k];
+  }
+  for (int b = 0; b < 3; ++b)
+    for (int k = 0; k < 4; ++k) {
+      ggd[b][k] = act[b] ? gG[D][b] * ci[k] : 0.0;
+      ggb[b][k] = act[b] ? gG[b][b] * ci[k] : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// conservative -> primitive (rho, u, v, w, p, T): cotangent of U given the cotangent of W
+// ------------------------------------------------------------------------------------------------
+FL_HD void prim_vjp(const double U[5], const Phys& ph, const double gW[6], double gU[5]) {
+  const double r = U[0];
+  const double ir = 1.0 / r;
+  const double u[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+  const double p = ph.gm1 * (U[4] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  // T = p / (rho R)
+  const double gp = gW[4] + gW[5] * ir * ph.iR;
+  double gr = gW[0] - gW[5] * p * ir * ir * ph.iR;
+  // p = (gamma - 1)(E - |m|^2 / (2 rho))
+  gU[4] = ph.gm1 * gp;
+  double q2 = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    gU[1 + c] = gW[1 + c] * ir - ph.gm1 * u[c] * gp;
+    gr -= gW[1 + c] * u[c] * ir;
+    q2 += u[c] * u[c];
+  }
+  gr += 0.5 * ph.gm1 * q2 * gp;
+  gU[0] = gr;
+}
+
+// ------------------------------------------------------------------------------------------------
+// wall halo maps of axis a (velocity mirrored; isothermal T_g = 2 T_w - T, p_g = p,
+// rho_g = p / (R T_g); porous adds 2 v_w to the wall-normal component): cotangent of the source
+// primitives w (rho, u, v, w, p, T) given the ghost cotangent; g_vw receives d/d v_w
+// ------------------------------------------------------------------------------------------------
+FL_HD void wall_map_vjp(const double w[6], int kind, double Tw, int a, const Phys& ph,
+                        const double gg[6], double gw[6], double* g_vw) {
+  for (int v = 0; v < 6; ++v) gw[v] = 0.0;
+  gw[1] = -gg[1];
+  gw[2] = -gg[2];
+  gw[3] = -gg[3];
+  *g_vw = 0.0;
+  if (kind == FLUID_BC_ADIABATIC) {
+    gw[0] = gg[0];
+    gw[4] = gg[4];
+    gw[5] = gg[5];
+    return;
+  }
+  const double Tg = 2.0 * Tw - w[5];
+  // rho_g = p / (R Tg): d/dp = 1/(R Tg), d/dT = p / (R Tg^2)
+  gw[4] = gg[4] + gg[0] / (ph.R * Tg);
+  gw[5] = -gg[5] + gg[0] * w[4] / (ph.R * Tg * Tg);
+  if (kind == FLUID_BC_POROUS) *g_vw = 2.0 * gg[1 + a];
+}
+
+}  // namespace fl

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -45,6 +46,22 @@ struct fluid_solver {
     cudaEvent_t a, b;
   };
   int face_block = 0, face_seg = 0;   // launch shape of the face kernels (0 = automatic)
+  // adjoint scratch (cfg.adjoint != 0)
+  double* gW = nullptr;            // cotangent of the primitives, NW * ncell
+  double* gG = nullptr;            // cotangent of the velocity gradients, NG * ncell
+  double* CW = nullptr;            // per-face contributions (6 slots x 6 primitives), 36 * ncell
+  double* CG = nullptr;            // per-face gradient contributions (4 x 4), 16 * ncell
+  double* S1 = nullptr;            // stage states recomputed by the step adjoint
+  double* S2 = nullptr;
+  double* MU = nullptr;            // scaled cotangent handed to the right-hand-side adjoint
+  double* L1 = nullptr;            // stage adjoints
+  double* L2 = nullptr;
+  double* GT = nullptr;            // right-hand-side adjoint result
+  double* gvw = nullptr;           // porous wall-velocity cotangent per wall column
+  size_t gvw_count = 0;
+  double* parts = nullptr;         // wall-loss partial sums
+  double* gT2 = nullptr;           // wall-loss dJ/dT of the two wall-adjacent cells per column
+  int nloss = 0;
   bool prof_on = false;
   std::vector<ProfEvent> prof_pending, prof_pool;
   double prof_ms[FLUID_KERNEL_COUNT] = {0};
@@ -261,6 +278,36 @@ int stage_into(fluid_solver* s, int stage, const double* Un, const double* Us, d
   return FLUID_OK;
 }
 
+// (dR/dX)^T mu on the interior into gX; (dR/dphi)^T mu added to gphi when given
+int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, double* gphi,
+            cudaStream_t st) {
+  const Geo& g = s->geo;
+  const bool visc = s->ph.visc != FLUID_VISC_NONE;
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(X, s->W, nullptr, g, s->ph, s->bc, s->ctl, st));
+  if (visc) FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
+  FL_CUDA(s, cudaMemsetAsync(s->gW, 0, fl::NW * (size_t)g.ncell * sizeof(double), st));
+  if (visc) FL_CUDA(s, cudaMemsetAsync(s->gG, 0, fl::NG * (size_t)g.ncell * sizeof(double), st));
+  FL_CUDA(s, cudaMemsetAsync(s->gvw, 0, s->gvw_count * sizeof(double), st));
+  FL_TIMED(s, FLUID_KERNEL_ADJ_FACE, st,
+           fl::launch_adj_faces(s->W, s->G, mu, s->CW, s->CG, s->gW, s->gG, g, s->ph, st));
+  if (s->ph.has_force) FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_source(mu, s->gW, g, s->ph, st));
+  FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_bc(s->W, s->gW, s->gvw, g, s->ph, s->bc, st));
+  FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_prim(X, s->gW, gX, g, s->ph, st));
+  if (gphi && s->bc.porous_axis >= 0) {
+    const int A = s->bc.porous_axis, t1 = s->bc.porous_t1, t2 = 3 - A - t1;
+    FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st,
+             fl::launch_adj_phi(s->gvw, g.xc[t1], gphi, g.p[t1], g.h[t1], g.p[t2], s->cfg.porous_begin,
+                                s->cfg.porous_count, s->cfg.porous_A / s->cfg.porous_phi0,
+                                2.0 * M_PI * s->cfg.porous_kappa, st));
+  }
+  return FLUID_OK;
+}
+
+int need_adjoint(fluid_solver* s) {
+  if (!s->gW) return fail(s, FLUID_EINVAL, "create the solver with cfg.adjoint != 0");
+  return FLUID_OK;
+}
+
 }  // namespace
 
 namespace fl {
@@ -414,6 +461,35 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
           return bail(e, "wall velocity");
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "wall velocity sync");
       }
+  if (c.adjoint) {
+    if (c.precision != FLUID_PREC_FP64) {
+      fluid_destroy(s);
+      return fail(nullptr, FLUID_ENOTSUP, "the adjoint is built for FLUID_PREC_FP64");
+    }
+    const bool visc = c.visc_law != FLUID_VISC_NONE;
+    if ((e = cudaMalloc(&s->gW, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gW");
+    if ((e = cudaMalloc(&s->CW, 36 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CW");
+    if (visc) {
+      if ((e = cudaMalloc(&s->gG, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gG");
+      if ((e = cudaMalloc(&s->CG, 16 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
+    }
+    double** bufs[] = {&s->S1, &s->S2, &s->MU, &s->L1, &s->L2, &s->GT};
+    for (double** b : bufs) {
+      if ((e = cudaMalloc(b, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc adjoint state");
+      if ((e = cudaMemset(*b, 0, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "adjoint init");
+    }
+    // wall columns: every face plane of the grid is covered by the largest padded plane
+    size_t plane = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int t1 = a == 0 ? 1 : 0, t2 = 3 - a - t1;
+      plane = std::max(plane, (size_t)g.p[t1] * g.p[t2]);
+    }
+    s->gvw_count = plane;
+    if ((e = cudaMalloc(&s->gvw, plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gvw");
+    if ((e = cudaMalloc(&s->gT2, 2 * plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gT2");
+    s->nloss = 1024;
+    if ((e = cudaMalloc(&s->parts, s->nloss * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc parts");
+  }
   *out = s;
   return FLUID_OK;
 }
@@ -429,6 +505,9 @@ void fluid_destroy(fluid_solver* s) {
   cudaFree(s->G);
   cudaFree(s->W32);
   cudaFree(s->G32);
+  for (double* p : {s->gW, s->gG, s->CW, s->CG, s->S1, s->S2, s->MU, s->L1, s->L2, s->GT, s->gvw,
+                    s->parts, s->gT2})
+    cudaFree(p);
   cudaFree(s->A);
   cudaFree(s->R);
   cudaFree(s->partial);
@@ -533,6 +612,92 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
     // stage 3: Un+1 = 1/3 Un + 2/3 (U2 + dt R(U2)) into U
     if (int r = rhs_into(s, s->A, s->R, st)) return r;
     if (int r = stage_into(s, 3, U_dev, s->A, U_dev, t_end, st)) return r;
+  }
+  return FLUID_OK;
+}
+
+int fluid_step_stages(fluid_solver* s, double* U_dev, double* U1_dev, double* U2_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, U1_dev, "U1_dev")) return r;
+  if (int r = check_ptr(s, U2_dev, "U2_dev")) return r;
+  cudaStream_t st = as_stream(stream);
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
+  if (int r = dt_into(s, nullptr, 1, 0.0, st)) return r;
+  if (int r = grad_faces(s, s->R, st)) return r;
+  if (int r = stage_into(s, 1, U_dev, U_dev, U1_dev, 0.0, st)) return r;
+  if (int r = rhs_into(s, U1_dev, s->R, st)) return r;
+  if (int r = stage_into(s, 2, U_dev, U1_dev, U2_dev, 0.0, st)) return r;
+  if (int r = rhs_into(s, U2_dev, s->R, st)) return r;
+  return stage_into(s, 3, U_dev, U2_dev, U_dev, 0.0, st);
+}
+
+int fluid_adjoint_rhs(fluid_solver* s, const double* U_dev, const double* mu_dev, double* gU_dev,
+                      double* gphi_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = need_adjoint(s)) return r;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, mu_dev, "mu_dev")) return r;
+  if (int r = check_ptr(s, gU_dev, "gU_dev")) return r;
+  return rhs_vjp(s, U_dev, mu_dev, gU_dev, gphi_dev, as_stream(stream));
+}
+
+int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_dev,
+                       const double* U2_dev, double* lam_dev, double* gphi_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = need_adjoint(s)) return r;
+  if (!(s->ph.dt_fixed > 0.0)) return fail(s, FLUID_EINVAL, "the step adjoint needs a frozen dt (cfg.dt_fixed > 0)");
+  if (int r = check_ptr(s, Un_dev, "Un_dev")) return r;
+  if (int r = check_ptr(s, lam_dev, "lam_dev")) return r;
+  if ((U1_dev == nullptr) != (U2_dev == nullptr)) return fail(s, FLUID_EINVAL, "pass both stage states or neither");
+  const double dt = s->ph.dt_fixed;
+  const Geo& g = s->geo;
+  cudaStream_t st = as_stream(stream);
+  const double* X1 = U1_dev;
+  const double* X2 = U2_dev;
+  if (!X1) {
+    // recompute the stage states of the step
+    if (int r = rhs_into(s, Un_dev, s->R, st)) return r;
+    FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_stage(1, Un_dev, Un_dev, s->R, s->S1, s->W, g, s->ph, s->ctl, 0.0, st, dt));
+    if (int r = rhs_into(s, s->S1, s->R, st)) return r;
+    FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_stage(2, Un_dev, s->S1, s->R, s->S2, s->W, g, s->ph, s->ctl, 0.0, st, dt));
+    X1 = s->S1;
+    X2 = s->S2;
+  }
+  // Un+1 = 1/3 Un + 2/3 U2 + 2/3 dt R(U2)
+  FL_CUDA(s, fl::launch_lincomb(s->MU, 2.0 / 3.0 * dt, lam_dev, 0, nullptr, 0, nullptr, 0, nullptr, g, st));
+  if (int r = rhs_vjp(s, X2, s->MU, s->GT, gphi_dev, st)) return r;
+  FL_CUDA(s, fl::launch_lincomb(s->L2, 2.0 / 3.0, lam_dev, 1.0, s->GT, 0, nullptr, 0, nullptr, g, st));
+  // U2 = 3/4 Un + 1/4 U1 + 1/4 dt R(U1)
+  FL_CUDA(s, fl::launch_lincomb(s->MU, 0.25 * dt, s->L2, 0, nullptr, 0, nullptr, 0, nullptr, g, st));
+  if (int r = rhs_vjp(s, X1, s->MU, s->GT, gphi_dev, st)) return r;
+  FL_CUDA(s, fl::launch_lincomb(s->L1, 0.25, s->L2, 1.0, s->GT, 0, nullptr, 0, nullptr, g, st));
+  // U1 = Un + dt R(Un)
+  FL_CUDA(s, fl::launch_lincomb(s->MU, dt, s->L1, 0, nullptr, 0, nullptr, 0, nullptr, g, st));
+  if (int r = rhs_vjp(s, Un_dev, s->MU, s->GT, gphi_dev, st)) return r;
+  FL_CUDA(s, fl::launch_lincomb(lam_dev, 1.0 / 3.0, lam_dev, 0.75, s->L2, 1.0, s->L1, 1.0, s->GT, g, st));
+  return FLUID_OK;
+}
+
+int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int side, double* J_dev,
+                         double* dJdU_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = need_adjoint(s)) return r;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, J_dev, "J_dev")) return r;
+  if (axis < 0 || axis >= s->geo.ndim || side < 0 || side > 1) return fail(s, FLUID_EINVAL, "bad wall face");
+  const int kind = s->bc.kind[axis][side];
+  if (kind != FLUID_BC_WALL && kind != FLUID_BC_POROUS)
+    return fail(s, FLUID_EINVAL, "the wall heat flux needs an isothermal or porous face");
+  cudaStream_t st = as_stream(stream);
+  const Geo& g = s->geo;
+  const int nparts = std::min(s->nloss, fl::wall_loss_parts(g, axis));
+  FL_CUDA(s, fl::launch_prim_bc(U_dev, s->W, nullptr, g, s->ph, s->bc, s->ctl, st));
+  FL_CUDA(s, fl::launch_wall_loss(s->W, s->parts, nparts, J_dev, dJdU_dev ? s->gT2 : nullptr, g, s->ph,
+                                  axis, side, s->bc.Tw[axis][side], st));
+  if (dJdU_dev) {
+    FL_CUDA(s, cudaMemsetAsync(dJdU_dev, 0, fl::NV * (size_t)g.ncell * sizeof(double), st));
+    FL_CUDA(s, fl::launch_wall_loss_grad(U_dev, s->gT2, dJdU_dev, g, s->ph, axis, side, st));
   }
   return FLUID_OK;
 }

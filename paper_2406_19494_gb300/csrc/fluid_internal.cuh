@@ -58,12 +58,22 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
 }
 
-__device__ __forceinline__ double viscosity(double T, const Phys& ph) {
+__host__ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return ph.mu_ref;
   const double r = T * ph.iT_ref;
   if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * exp(ph.visc_exp * log(r));
   // Sutherland
   return ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
+}
+
+// d mu / d T of the same laws
+__host__ __device__ __forceinline__ double viscosity_dT(double T, const Phys& ph) {
+  if (ph.visc == FLUID_VISC_CONSTANT) return 0.0;
+  const double r = T * ph.iT_ref;
+  if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * ph.visc_exp * exp((ph.visc_exp - 1.0) * log(r)) * ph.iT_ref;
+  // mu = C r^{3/2} / (T + S) with C = mu_ref (T_ref + S): dmu/dT = mu (1.5 / T - 1 / (T + S))
+  const double mu = ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
+  return mu * (1.5 / T - 1.0 / (T + ph.suth_S));
 }
 
 // Configuration check shared by the entry points: NULL if valid, else a static message.
@@ -77,9 +87,10 @@ cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t s
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st);
+// dt_arg > 0 replaces the solver's dt (used by the adjoint's stage recomputation)
 cudaError_t launch_stage(int stage, const double* Un, const double* Us, const double* R, double* Ud,
                          const double* W, const Geo& g, const Phys& ph, Ctl* ctl, double t_end,
-                         cudaStream_t st);
+                         cudaStream_t st, double dt_arg = 0.0);
 cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, double* partial,
                               int nparts, cudaStream_t st);
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,
@@ -92,6 +103,28 @@ cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const fl
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st);
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
                                 int nparts, cudaStream_t st);
+
+// ---- adjoint launchers implemented in kernels_adjoint.cu ----------------------------------------
+cudaError_t launch_adj_faces(const double* W, const double* G, const double* mu, double* CW,
+                             double* CG, double* gW, double* gG, const Geo& g, const Phys& ph,
+                             cudaStream_t st);
+cudaError_t launch_adj_source(const double* mu, double* gW, const Geo& g, const Phys& ph, cudaStream_t st);
+cudaError_t launch_adj_bc(const double* W, double* gW, double* gvw_col, const Geo& g,
+                          const Phys& ph, const BC& bc, cudaStream_t st);
+cudaError_t launch_adj_prim(const double* U, const double* gW, double* gU, const Geo& g,
+                            const Phys& ph, cudaStream_t st);
+cudaError_t launch_adj_phi(const double* gvw_col, const double* xc, double* gphi, int p_t1,
+                           int h_t1, int ext_t2, int begin, int count, double amp,
+                           double two_pi_kappa, cudaStream_t st);
+int wall_loss_parts(const Geo& g, int A);
+cudaError_t launch_wall_loss(const double* W, double* part, int nparts, double* J, double* gT2,
+                             const Geo& g, const Phys& ph, int A, int side, double Tw,
+                             cudaStream_t st);
+cudaError_t launch_wall_loss_grad(const double* U, const double* gT2, double* dJdU, const Geo& g,
+                                  const Phys& ph, int A, int side, cudaStream_t st);
+cudaError_t launch_lincomb(double* out, double c0, const double* x0, double c1, const double* x1,
+                           double c2, const double* x2, double c3, const double* x3, const Geo& g,
+                           cudaStream_t st);
 
 cudaError_t launch_prim_to_cons(const double* W, double* U, int ncell, const Phys& ph,
                                 cudaStream_t st);

@@ -1,0 +1,199 @@
+// Per-face FP64 arithmetic of the right-hand side, shared by the forward kernels, the adjoint
+// kernels and the host-compiled checks of the adjoint: WENO5 reconstruction (Jiang & Shu; Borges
+// et al. for the Z weights), the HLLC flux (Toro Ch. 10) and the constants they use.
+#pragma once
+
+#include <cmath>
+
+#include "fluid_internal.cuh"
+
+#ifndef FL_HD
+#define FL_HD __host__ __device__ __forceinline__
+#endif
+
+namespace fl {
+
+FL_HD double fl_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / std::sqrt(x);
+#endif
+}
+
+constexpr double kSixth = 1.0 / 6.0;
+constexpr double k1312 = 13.0 / 12.0;
+constexpr double kTwelfth = 1.0 / 12.0;
+constexpr double k24th = 1.0 / 24.0;
+constexpr double k16th = 1.0 / 16.0;
+
+// ------------------------------------------------------------------------------------------------
+// WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}
+// ------------------------------------------------------------------------------------------------
+template <int SCHEME>
+FL_HD double weno5(double qm2, double qm1, double q0, double qp1, double qp2,
+                                        double eps) {
+  // candidate values times 6
+  const double C0 = 2.0 * qm2 - 7.0 * qm1 + 11.0 * q0;
+  const double C1 = -qm1 + 5.0 * q0 + 2.0 * qp1;
+  const double C2 = 2.0 * q0 + 5.0 * qp1 - qp2;
+  double t = qm2 - 2.0 * qm1 + q0, s = qm2 - 4.0 * qm1 + 3.0 * q0;
+  const double b0 = k1312 * t * t + 0.25 * s * s;
+  t = qm1 - 2.0 * q0 + qp1; s = qm1 - qp1;
+  const double b1 = k1312 * t * t + 0.25 * s * s;
+  t = q0 - 2.0 * qp1 + qp2; s = 3.0 * q0 - 4.0 * qp1 + qp2;
+  const double b2 = k1312 * t * t + 0.25 * s * s;
+  // Weights scaled by a common positive factor so that one division remains.  With
+  // e_k = beta_k + eps and Q_k = prod_{j != k} e_j:
+  //   JS: d_k / e_k^2                  = d_k Q_k^2 / P^2,              P = e0 e1 e2
+  //   Z : d_k (1 + (tau5 / e_k)^2)     = d_k (P^2 + tau5^2 Q_k^2) / P^2
+  // The common 1/P^2 cancels in omega_k = alpha_k / sum alpha.  Since e_k >= eps the scaled
+  // weights stay normal for eps = 1e-40 (P^2 >= 1e-240) and finite while beta_k < 1e50.
+  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  double a0, a1, a2;
+  if (SCHEME == FLUID_WENO_JS) {
+    a0 = 0.1 * (Q0 * Q0); a1 = 0.6 * (Q1 * Q1); a2 = 0.3 * (Q2 * Q2);
+  } else {
+    const double tau = b0 - b2 < 0.0 ? b2 - b0 : b0 - b2;
+    const double P = e0 * Q0;
+    const double PP = P * P, tt = tau * tau;
+    a0 = 0.1 * (PP + tt * (Q0 * Q0));
+    a1 = 0.6 * (PP + tt * (Q1 * Q1));
+    a2 = 0.3 * (PP + tt * (Q2 * Q2));
+  }
+  return (a0 * C0 + a1 * C1 + a2 * C2) / (6.0 * (a0 + a1 + a2));
+}
+
+// ------------------------------------------------------------------------------------------------
+// HLLC along axis D (Toro Ch. 10) with Einfeldt/Roe wave-speed bounds.  Branch order:
+// S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
+// ------------------------------------------------------------------------------------------------
+template <int D>
+FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
+                                     double F[5]) {
+  const double rL = wl[0], pL = wl[4], rR = wr[0], pR = wr[4];
+  const double unL = wl[1 + D], unR = wr[1 + D];
+  const double q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+  const double q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+  const double EL = pL * ph.igm1 + 0.5 * rL * q2L;
+  const double ER = pR * ph.igm1 + 0.5 * rR * q2R;
+  // 1/sqrt(rho) gives both sqrt(rho) (Roe weights) and 1/rho
+  const double qL = fl_rsqrt(rL), qR = fl_rsqrt(rR);
+  const double sL = rL * qL, sR = rR * qR;
+  const double irL = qL * qL, irR = qR * qR;
+  const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
+  const double isum = 1.0 / (sL + sR);
+  const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
+  const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
+  const double ut2 = (sL * wl[3] + sR * wr[3]) * isum;
+  const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+  const double Ht = (sL * HL + sR * HR) * isum;
+  const double ct = sqrt(ph.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const double utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
+  const double SL = fmin(unL - cL, utn - ct);
+  const double SR = fmax(unR + cR, utn + ct);
+  const double mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const double Ss = (pR - pL + unL * mL - unR * mR) / (mL - mR);
+
+  const bool left = (SL >= 0.0) || (Ss >= 0.0);
+  const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
+  const double r = left ? rL : rR;
+  const double p = left ? pL : pR;
+  const double E = left ? EL : ER;
+  const double un = left ? unL : unR;
+  const double S = left ? SL : SR;
+  const double m = left ? mL : mR;
+  const double u0 = left ? wl[1] : wr[1];
+  const double u1 = left ? wl[2] : wr[2];
+  const double u2 = left ? wl[3] : wr[3];
+  // Euler flux of the selected side
+  const double mn = r * un;
+  F[0] = mn;
+  F[1] = mn * u0;
+  F[2] = mn * u1;
+  F[3] = mn * u2;
+  F[1 + D] += p;
+  F[4] = un * (E + p);
+  if (star) {
+    // U*_K = m/(S - S*) [1, S* (normal), tangential u, E/rho + (S* - un)(S* + p/m)]
+    const double q = 1.0 / (S - Ss);
+    const double fac = m * q;
+    const double ir = left ? irL : irR;
+    const double dU0 = fac - r;
+    double dU[3] = {fac * u0 - r * u0, fac * u1 - r * u1, fac * u2 - r * u2};
+    dU[D] = fac * Ss - r * un;
+    const double Es = fac * (E * ir) + (Ss - un) * (fac * Ss + p * q);
+    F[0] += S * dU0;
+    F[1] += S * dU[0];
+    F[2] += S * dU[1];
+    F[3] += S * dU[2];
+    F[4] += S * (Es - E);
+  }
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// conservative -> primitive (rho, u, v, w, p, T) with one division
+// ------------------------------------------------------------------------------------------------
+FL_HD void prim_from_cons(const double U[5], const Phys& ph, double w[6]) {
+  const double r = U[0];
+  const double ir = 1.0 / r;
+  const double u = U[1] * ir, v = U[2] * ir, ww = U[3] * ir;
+  const double p = ph.gm1 * (U[4] - 0.5 * r * (u * u + v * v + ww * ww));
+  w[0] = r; w[1] = u; w[2] = v; w[3] = ww; w[4] = p; w[5] = p * ir * ph.iR;
+}
+
+// wall halo map of axis a applied to primitives w: velocity mirrored; isothermal T_g = 2 T_w - T,
+// p_g = p, rho_g = p / (R T_g); porous adds 2 v_w to the wall-normal component.  Returns false
+// when the ghost temperature is not positive.
+FL_HD bool wall_map_prim(double w[6], int kind, double Tw, double vw, int a, const Phys& ph) {
+  w[1] = -w[1]; w[2] = -w[2]; w[3] = -w[3];
+  if (kind == FLUID_BC_ADIABATIC) return true;
+  const double Tg = 2.0 * Tw - w[5];
+  w[0] = w[4] / (ph.R * Tg);
+  w[5] = Tg;
+  if (kind == FLUID_BC_POROUS) w[1 + a] = 2.0 * vw + w[1 + a];
+  return Tg > 0.0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// dissipative face flux along D (fourth-order central; the face is between cells 1 and 2 of the
+// four-cell stencils): vel[c][k], T[k] at cells a-1..a+2; gd[b][k] = d u_D / d x_b and
+// gb[b][k] = d u_b / d x_b at the same cells for tangential axes b (ignored for b == D or b >=
+// ndim); mfa = d(index)/dx at the face.  Returns Fd = (tau_0D, tau_1D, tau_2D, energy).
+// ------------------------------------------------------------------------------------------------
+FL_HD double interp4(const double f[4]) { return (9.0 * (f[1] + f[2]) - (f[0] + f[3])) * k16th; }
+FL_HD double dnorm4(const double f[4], double mfa) { return ((f[0] - f[3]) + 27.0 * (f[2] - f[1])) * k24th * mfa; }
+
+template <int D>
+FL_HD void visc_face(const double vel[3][4], const double T[4], const double gd[3][4],
+                     const double gb[3][4], int ndim, double mfa, const Phys& ph, double Fd[4]) {
+  double vf[3], Gf[3][3];
+  for (int c = 0; c < 3; ++c) {
+    vf[c] = interp4(vel[c]);
+    Gf[c][D] = dnorm4(vel[c], mfa);
+  }
+  const double Tf = interp4(T);
+  const double dT = dnorm4(T, mfa);
+  for (int b = 0; b < 3; ++b) {
+    if (b == D) continue;
+    if (b < ndim) {
+      Gf[D][b] = interp4(gd[b]);
+      Gf[b][b] = interp4(gb[b]);
+    } else {
+      Gf[D][b] = 0.0;
+      Gf[b][b] = 0.0;
+    }
+  }
+  const double div = Gf[0][0] + Gf[1][1] + Gf[2][2];
+  const double mu = viscosity(Tf, ph);
+  const double lam = mu * ph.lam_fac;
+  for (int c = 0; c < 3; ++c) {
+    if (c == D) Fd[c] = mu * (Gf[D][D] + Gf[D][D]) - (2.0 / 3.0) * mu * div;
+    else Fd[c] = mu * (Gf[c][D] + Gf[D][c]);
+  }
+  Fd[3] = vf[0] * Fd[0] + vf[1] * Fd[1] + vf[2] * Fd[2] + lam * dT;
+}
+
+}  // namespace fl

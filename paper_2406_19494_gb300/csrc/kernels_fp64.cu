@@ -18,17 +18,12 @@
 // scratch with the same padded layout.
 #include <cuda_runtime.h>
 
+#include "flux_math.cuh"
 #include "fluid_internal.cuh"
 
 namespace fl {
 
 namespace {
-
-constexpr double kSixth = 1.0 / 6.0;
-constexpr double k1312 = 13.0 / 12.0;
-constexpr double kTwelfth = 1.0 / 12.0;
-constexpr double k24th = 1.0 / 24.0;
-constexpr double k16th = 1.0 / 16.0;
 
 int grid_for(long long work, int block) {
   long long b = (work + block - 1) / block;
@@ -48,25 +43,13 @@ __device__ __forceinline__ int bc_source(int kind, int side, int a, int n, int h
 
 __device__ __forceinline__ void prim_of(const double* __restrict__ U, int c, int nc, const Phys& ph,
                                         double w[NW]) {
-  const double r = U[c];
-  const double mx = U[nc + c], my = U[2 * nc + c], mz = U[3 * nc + c], E = U[4 * nc + c];
-  const double ir = 1.0 / r;
-  const double u = mx * ir, v = my * ir, ww = mz * ir;
-  const double p = ph.gm1 * (E - 0.5 * r * (u * u + v * v + ww * ww));
-  w[0] = r; w[1] = u; w[2] = v; w[3] = ww; w[4] = p; w[5] = p * ir * ph.iR;
+  const double u[5] = {U[c], U[nc + c], U[2 * nc + c], U[3 * nc + c], U[4 * nc + c]};
+  prim_from_cons(u, ph, w);
 }
 
-// wall map of axis a applied to primitives w (velocity mirrored; isothermal: T_g = 2 T_w - T,
-// p_g = p; porous adds the transpiration velocity to the wall-normal component)
 __device__ __forceinline__ void wall_map(double w[NW], int kind, double Tw, double vw, int a,
                                          const Phys& ph, unsigned* flags) {
-  w[1] = -w[1]; w[2] = -w[2]; w[3] = -w[3];
-  if (kind == FLUID_BC_ADIABATIC) return;
-  const double Tg = 2.0 * Tw - w[5];
-  if (!(Tg > 0.0)) atomicOr(flags, FLAG_GHOST_T);
-  w[0] = w[4] / (ph.R * Tg);
-  w[5] = Tg;
-  if (kind == FLUID_BC_POROUS) w[1 + a] = 2.0 * vw + w[1 + a];
+  if (!wall_map_prim(w, kind, Tw, vw, a, ph)) atomicOr(flags, FLAG_GHOST_T);
 }
 
 __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a, const int c[3],
@@ -169,111 +152,6 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
 }
 
 // ------------------------------------------------------------------------------------------------
-// WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}
-// ------------------------------------------------------------------------------------------------
-template <int SCHEME>
-__device__ __forceinline__ double weno5(double qm2, double qm1, double q0, double qp1, double qp2,
-                                        double eps) {
-  // candidate values times 6
-  const double C0 = 2.0 * qm2 - 7.0 * qm1 + 11.0 * q0;
-  const double C1 = -qm1 + 5.0 * q0 + 2.0 * qp1;
-  const double C2 = 2.0 * q0 + 5.0 * qp1 - qp2;
-  double t = qm2 - 2.0 * qm1 + q0, s = qm2 - 4.0 * qm1 + 3.0 * q0;
-  const double b0 = k1312 * t * t + 0.25 * s * s;
-  t = qm1 - 2.0 * q0 + qp1; s = qm1 - qp1;
-  const double b1 = k1312 * t * t + 0.25 * s * s;
-  t = q0 - 2.0 * qp1 + qp2; s = 3.0 * q0 - 4.0 * qp1 + qp2;
-  const double b2 = k1312 * t * t + 0.25 * s * s;
-  // Weights scaled by a common positive factor so that one division remains.  With
-  // e_k = beta_k + eps and Q_k = prod_{j != k} e_j:
-  //   JS: d_k / e_k^2                  = d_k Q_k^2 / P^2,              P = e0 e1 e2
-  //   Z : d_k (1 + (tau5 / e_k)^2)     = d_k (P^2 + tau5^2 Q_k^2) / P^2
-  // The common 1/P^2 cancels in omega_k = alpha_k / sum alpha.  Since e_k >= eps the scaled
-  // weights stay normal for eps = 1e-40 (P^2 >= 1e-240) and finite while beta_k < 1e50.
-  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
-  double a0, a1, a2;
-  if (SCHEME == FLUID_WENO_JS) {
-    a0 = 0.1 * (Q0 * Q0); a1 = 0.6 * (Q1 * Q1); a2 = 0.3 * (Q2 * Q2);
-  } else {
-    const double tau = fabs(b0 - b2);
-    const double P = e0 * Q0;
-    const double PP = P * P, tt = tau * tau;
-    a0 = 0.1 * (PP + tt * (Q0 * Q0));
-    a1 = 0.6 * (PP + tt * (Q1 * Q1));
-    a2 = 0.3 * (PP + tt * (Q2 * Q2));
-  }
-  return (a0 * C0 + a1 * C1 + a2 * C2) / (6.0 * (a0 + a1 + a2));
-}
-
-// ------------------------------------------------------------------------------------------------
-// HLLC along axis D (Toro Ch. 10) with Einfeldt/Roe wave-speed bounds.  Branch order:
-// S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
-// ------------------------------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ void hllc(const double wl[5], const double wr[5], const Phys& ph,
-                                     double F[5]) {
-  const double rL = wl[0], pL = wl[4], rR = wr[0], pR = wr[4];
-  const double unL = wl[1 + D], unR = wr[1 + D];
-  const double q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
-  const double q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-  const double EL = pL * ph.igm1 + 0.5 * rL * q2L;
-  const double ER = pR * ph.igm1 + 0.5 * rR * q2R;
-  // 1/sqrt(rho) gives both sqrt(rho) (Roe weights) and 1/rho
-  const double qL = rsqrt(rL), qR = rsqrt(rR);
-  const double sL = rL * qL, sR = rR * qR;
-  const double irL = qL * qL, irR = qR * qR;
-  const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
-  const double isum = 1.0 / (sL + sR);
-  const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
-  const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
-  const double ut2 = (sL * wl[3] + sR * wr[3]) * isum;
-  const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-  const double Ht = (sL * HL + sR * HR) * isum;
-  const double ct = sqrt(ph.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
-  const double utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
-  const double SL = fmin(unL - cL, utn - ct);
-  const double SR = fmax(unR + cR, utn + ct);
-  const double mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const double Ss = (pR - pL + unL * mL - unR * mR) / (mL - mR);
-
-  const bool left = (SL >= 0.0) || (Ss >= 0.0);
-  const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
-  const double r = left ? rL : rR;
-  const double p = left ? pL : pR;
-  const double E = left ? EL : ER;
-  const double un = left ? unL : unR;
-  const double S = left ? SL : SR;
-  const double m = left ? mL : mR;
-  const double u0 = left ? wl[1] : wr[1];
-  const double u1 = left ? wl[2] : wr[2];
-  const double u2 = left ? wl[3] : wr[3];
-  // Euler flux of the selected side
-  const double mn = r * un;
-  F[0] = mn;
-  F[1] = mn * u0;
-  F[2] = mn * u1;
-  F[3] = mn * u2;
-  F[1 + D] += p;
-  F[4] = un * (E + p);
-  if (star) {
-    // U*_K = m/(S - S*) [1, S* (normal), tangential u, E/rho + (S* - un)(S* + p/m)]
-    const double q = 1.0 / (S - Ss);
-    const double fac = m * q;
-    const double ir = left ? irL : irR;
-    const double dU0 = fac - r;
-    double dU[3] = {fac * u0 - r * u0, fac * u1 - r * u1, fac * u2 - r * u2};
-    dU[D] = fac * Ss - r * un;
-    const double Es = fac * (E * ir) + (Ss - un) * (fac * Ss + p * q);
-    F[0] += S * dU0;
-    F[1] += S * dU[0];
-    F[2] += S * dU[1];
-    F[3] += S * dU[2];
-    F[4] += S * (Es - E);
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
 // face flux F^c - F^d at face a+1/2 along D; `cell` is the padded index of cell a, s its stride
 // ------------------------------------------------------------------------------------------------
 template <int D, int SCHEME, bool VISC>
@@ -296,51 +174,31 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
   if (!VISC) return;
 
   // cells a-1 .. a+2 are q[.][1..4]
-  const double mfa = g.mf[D][a];
-  double T[4];
+  double vel[3][4], T[4], gd[3][4], gb[3][4];
 #pragma unroll
-  for (int o = 0; o < 4; ++o) T[o] = __ldg(W + 5 * nc + cell + (o - 1) * s);
-  auto interp = [](double fm1, double f0, double f1, double f2) {
-    return (9.0 * (f0 + f1) - (fm1 + f2)) * k16th;
-  };
-  auto dn = [&](double fm1, double f0, double f1, double f2) {
-    return ((fm1 - f2) + 27.0 * (f1 - f0)) * k24th * mfa;
-  };
-  double vf[3], Gf[3][3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    vf[c] = interp(q[1 + c][1], q[1 + c][2], q[1 + c][3], q[1 + c][4]);
-    Gf[c][D] = dn(q[1 + c][1], q[1 + c][2], q[1 + c][3], q[1 + c][4]);
+  for (int o = 0; o < 4; ++o) {
+    vel[0][o] = q[1][1 + o];
+    vel[1][o] = q[2][1 + o];
+    vel[2][o] = q[3][1 + o];
+    T[o] = __ldg(W + 5 * nc + cell + (o - 1) * s);
   }
-  const double Tf = interp(T[0], T[1], T[2], T[3]);
-  const double dT = dn(T[0], T[1], T[2], T[3]);
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    if (b == D) continue;
-    if (b < g.ndim) {
-      const double* gd = G + (D * 3 + b) * nc + cell;   // d u_D / d x_b
-      const double* gb = G + (b * 3 + b) * nc + cell;   // d u_b / d x_b
-      Gf[D][b] = interp(__ldg(gd - s), __ldg(gd), __ldg(gd + s), __ldg(gd + 2 * s));
-      Gf[b][b] = interp(__ldg(gb - s), __ldg(gb), __ldg(gb + s), __ldg(gb + 2 * s));
-    } else {
-      Gf[D][b] = 0.0;
-      Gf[b][b] = 0.0;
+    if (b == D || b >= g.ndim) continue;
+    const double* pd = G + (D * 3 + b) * nc + cell;   // d u_D / d x_b
+    const double* pb = G + (b * 3 + b) * nc + cell;   // d u_b / d x_b
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      gd[b][o] = __ldg(pd + (o - 1) * s);
+      gb[b][o] = __ldg(pb + (o - 1) * s);
     }
   }
-  const double div = Gf[0][0] + Gf[1][1] + Gf[2][2];
-  const double mu = viscosity(Tf, ph);
-  const double lam = mu * ph.lam_fac;
-  double tau[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (c == D) tau[c] = mu * (Gf[D][D] + Gf[D][D]) - (2.0 / 3.0) * mu * div;
-    else tau[c] = mu * (Gf[c][D] + Gf[D][c]);
-  }
-  const double en = vf[0] * tau[0] + vf[1] * tau[1] + vf[2] * tau[2] + lam * dT;
-  F[1] -= tau[0];
-  F[2] -= tau[1];
-  F[3] -= tau[2];
-  F[4] -= en;
+  double Fd[4];
+  visc_face<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, Fd);
+  F[1] -= Fd[0];
+  F[2] -= Fd[1];
+  F[3] -= Fd[2];
+  F[4] -= Fd[3];
 }
 
 template <int D, int SCHEME, bool VISC>
@@ -411,9 +269,9 @@ __global__ void k_source(double* __restrict__ R, const double* __restrict__ W, G
 // stage 1: Ud = Un + dt r; stage 2: Ud = 3/4 Un + 1/4 (Us + dt r); stage 3: Ud = 1/3 Un + 2/3 (Us + dt r)
 __global__ void k_stage(int stage, const double* Un, const double* Us, const double* __restrict__ R,
                         double* Ud, const double* __restrict__ W, Geo g, Phys ph, Ctl* ctl,
-                        double t_end) {
-  const double dt = ctl->dt;
-  if (stage == 3 && blockIdx.x == 0 && threadIdx.x == 0 && dt > 0.0) {
+                        double t_end, double dt_arg) {
+  const double dt = dt_arg > 0.0 ? dt_arg : ctl->dt;
+  if (stage == 3 && dt_arg <= 0.0 && blockIdx.x == 0 && threadIdx.x == 0 && dt > 0.0) {
     const double tn = ctl->t + dt;
     ctl->t = (t_end > 0.0 && !(tn < t_end)) ? t_end : tn;
   }
@@ -592,9 +450,9 @@ cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& 
 
 cudaError_t launch_stage(int stage, const double* Un, const double* Us, const double* R, double* Ud,
                          const double* W, const Geo& g, const Phys& ph, Ctl* ctl, double t_end,
-                         cudaStream_t st) {
+                         cudaStream_t st, double dt_arg) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_stage<<<grid_for(total, 256), 256, 0, st>>>(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end);
+  k_stage<<<grid_for(total, 256), 256, 0, st>>>(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end, dt_arg);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ STRETCH = {"uniform": 0, "tanh2": 1, "tanh1": 2}
 VISC = {"none": 0, "constant": 1, "power": 2, "sutherland": 3}
 WENO = {"js": 0, "z": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
-KERNELS = ("prim_bc", "grad", "face_x", "face_y", "face_z", "stage", "dt", "source")
+KERNELS = ("prim_bc", "grad", "face_x", "face_y", "face_z", "stage", "dt", "source", "adj_face", "adj_cell")
 
 # every symbol the header declares, with (restype, argtypes)
 _vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
@@ -36,6 +36,10 @@ SIGNATURES = {
     "fluid_rhs": (_i, [_vp, _vp, _vp, _vp]),
     "fluid_compute_dt": (_i, [_vp, _vp, _vp, _vp]),
     "fluid_step": (_i, [_vp, _vp, _i, _d, _vp]),
+    "fluid_step_stages": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fluid_adjoint_rhs": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "fluid_adjoint_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fluid_wall_heat_loss": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "fluid_get_time": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
     "fluid_set_time": (_i, [_vp, _d, _vp]),
     "fluid_check": (_i, [_vp, _vp]),
@@ -82,10 +86,12 @@ class FluidConfig(ctypes.Structure):
         ("porous_A", ctypes.c_double),
         ("porous_kappa", ctypes.c_double),
         ("porous_phi0", ctypes.c_double),
+        ("adjoint", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
-def config_from_case(case, precision="fp64"):
+def config_from_case(case, precision="fp64", adjoint=False):
     """Fill a FluidConfig from a case dict (the schema of workloads.py)."""
     c = FluidConfig()
     c.struct_size = ctypes.sizeof(FluidConfig)
@@ -114,6 +120,7 @@ def config_from_case(case, precision="fp64"):
     c.cfl = float(case.get("cfl", 0.5))
     c.dt_fixed = float(case.get("dt_fixed", 0.0))
     c.precision = PRECISION[precision]
+    c.adjoint = 1 if adjoint else 0
     pz = case.get("porous", None)
     if pz:
         c.porous_axis, c.porous_side = int(pz["axis"]), int(pz["side"])

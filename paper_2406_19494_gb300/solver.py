@@ -16,15 +16,23 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 class Solver:
     """One solve on the current CUDA device, configured from a case dict (see workloads.py)."""
 
-    def __init__(self, case, precision="fp64"):
+    def __init__(self, case, precision="fp64", adjoint=False):
         if not torch.cuda.is_available():
             raise RuntimeError("the fluid solver needs a CUDA device")
         self.lib = native.lib()
         self.case = case
-        self.cfg = native.config_from_case(case, precision)
+        self.cfg = native.config_from_case(case, precision, adjoint)
         h = ctypes.c_void_p()
         st = self.lib.fluid_create(ctypes.byref(self.cfg), ctypes.byref(h))
         if st != native.FLUID_OK:
@@ -89,6 +97,30 @@ class Solver:
         self._check(self.lib.fluid_step(self.handle, self._state(U), int(nsteps), float(t_end),
                                         _stream(stream)))
         return U
+
+    def step_stages(self, U, U1, U2, stream=None):
+        self._check(self.lib.fluid_step_stages(self.handle, self._state(U), self._state(U1, "U1"),
+                                               self._state(U2, "U2"), _stream(stream)))
+
+    def adjoint_rhs(self, U, mu, gU=None, gphi=None, stream=None):
+        gU = torch.zeros_like(U) if gU is None else gU
+        self._check(self.lib.fluid_adjoint_rhs(self.handle, self._state(U), self._state(mu, "mu"),
+                                               self._state(gU, "gU"), _ptr(gphi), _stream(stream)))
+        return gU
+
+    def adjoint_step(self, Un, lam, gphi=None, U1=None, U2=None, stream=None):
+        self._check(self.lib.fluid_adjoint_step(
+            self.handle, self._state(Un), None if U1 is None else self._state(U1, "U1"),
+            None if U2 is None else self._state(U2, "U2"), self._state(lam, "lam"), _ptr(gphi),
+            _stream(stream)))
+        return lam
+
+    def wall_heat_loss(self, U, axis, side, grad=False, stream=None):
+        J = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dJ = torch.zeros_like(U) if grad else None
+        self._check(self.lib.fluid_wall_heat_loss(self.handle, self._state(U), int(axis), int(side),
+                                                  ctypes.c_void_p(J.data_ptr()), _ptr(dJ), _stream(stream)))
+        return (J, dJ) if grad else J
 
     def time(self, stream=None):
         t, dt = ctypes.c_double(), ctypes.c_double()
