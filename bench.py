@@ -183,6 +183,9 @@ def run_fluid(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         mixed_ms = t.item()
 
+    # ---- adjoint / forward ratio (the metric's third part) -------------------------------------
+    adjoint = measure_adjoint(flush, stream) if not args.no_adjoint else None
+
     # ---- end-to-end through the C ABI with host buffers ---------------------------------------
     Uh = U0.cpu().pin_memory()
     Uout = torch.empty_like(Uh).pin_memory()
@@ -260,6 +263,7 @@ def run_fluid(args):
                 "flops32_per_cell_axis": accounting.mixed_cell_axis_flops32(case["weno"], case["visc"]),
                 "bytes_per_cell_axis": accounting.mixed_face_bytes()},
         },
+        "adjoint": adjoint,
         "clocks": clk.summary(),
         "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
                   "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
@@ -270,6 +274,67 @@ def run_fluid(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measure_adjoint(flush, stream, steps=5, warmup=3, grad_steps=400, K=20):
+    """Adjoint/forward time ratio on the porous boundary layer (512 x 128, Ma 6, frozen dt, FP64):
+    one RK3 step vs one adjoint step (with its stage recomputation, and with stored stages), and
+    the end-to-end gradient dJ/dphi of the wall heat flux after `grad_steps` steps with checkpoints
+    every K steps."""
+    import torch
+    from paper_2406_19494_gb300.adjoint import wall_heat_loss
+    from paper_2406_19494_gb300.solver import Solver
+    c = workloads.porous_bl_case(512, 128)
+    probe = Solver(c)
+    xc, _ = probe.grid(0)
+    yc, _ = probe.grid(1)
+    W = np.pad(workloads.porous_bl_prims(c, xc[3:-3], yc[3:-3]), [(0, 0), (0, 0), (3, 3), (3, 3)], mode="edge")
+    U0 = probe.prim_to_cons(torch.from_numpy(W).cuda())
+    dtd = probe.compute_dt(U0).item()
+    del probe
+    c = dict(c, dt_fixed=0.5 * dtd)
+    s = Solver(c, adjoint=True)
+    phi = torch.from_numpy(workloads.porous_phi(c, seed=0)).cuda()
+    s.set_wall_params(phi)
+    s.set_inflow(0, 0, torch.from_numpy(workloads.porous_bl_inflow(c, yc)).cuda())
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    U = U0.clone()
+    fwd = timed(lambda: s.step(U, 1))
+    Un = U0.clone()
+    U1, U2 = torch.zeros_like(U0), torch.zeros_like(U0)
+    s.step_stages(Un.clone(), U1, U2)
+    lam = torch.zeros_like(U0)
+    gphi = torch.zeros_like(phi)
+    adj = timed(lambda: s.adjoint_step(Un, lam, gphi))
+    adj_stored = timed(lambda: s.adjoint_step(Un, lam, gphi, U1, U2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = phi.clone().requires_grad_(True)
+    J = wall_heat_loss(p, s, U0, grad_steps, K, 1, 0)
+    J.backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    return {"workload": "porous boundary layer 512x128, Ma 6, 256 porous wall cells, frozen dt, FP64",
+            "forward_ms_per_step": fwd, "adjoint_ms_per_step": adj, "adjoint_stored_stages_ms_per_step": adj_stored,
+            "adjoint_forward_ratio": adj / fwd, "adjoint_forward_ratio_stored_stages": adj_stored / fwd,
+            "gradient": {"steps": grad_steps, "checkpoint_every": K, "wall_s": t_grad, "J": J.item(),
+                         "grad_norm_inf": float(p.grad.abs().max())}}
 
 
 def measured_hbm_gbs():
@@ -373,6 +438,7 @@ def main():
     ap.add_argument("--impl", default="fluid", choices=("fluid", "reference"))
     ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "fluid":
         args.warmup = 3

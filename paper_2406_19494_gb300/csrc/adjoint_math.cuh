@@ -14,7 +14,13 @@ namespace fl {
 // WENO5: cotangent of the five stencil values q_{i-2..i+2} given the cotangent of the face value
 // ------------------------------------------------------------------------------------------------
 template <int SCHEME>
-FL_HD void weno5_vjp(const double q[5], double eps, double g_out, double gq[5]) {
+FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]) {
+  // WENO5 is translation-equivariant (f(q - c) = f(q) - c), so its Jacobian is that of the data
+  // shifted by the centre value.  Working on the shifted data keeps every intermediate -- in
+  // particular the weight cotangents, proportional to C_k - 6 f -- free of the cancellation of
+  // two O(|q|) numbers, whose rounding the weight derivatives (~1 / spread of the data) would
+  // otherwise amplify in nearly uniform regions.
+  const double q[5] = {qin[0] - qin[2], qin[1] - qin[2], 0.0, qin[3] - qin[2], qin[4] - qin[2]};
   const double C0 = 2.0 * q[0] - 7.0 * q[1] + 11.0 * q[2];
   const double C1 = -q[1] + 5.0 * q[2] + 2.0 * q[3];
   const double C2 = 2.0 * q[2] + 5.0 * q[3] - q[4];
