@@ -186,6 +186,8 @@ def run_fluid(args):
     # ---- adjoint / forward ratio (the metric's third part) -------------------------------------
     adjoint = measure_adjoint(flush, stream) if not args.no_adjoint else None
 
+    serving = measure_serving() if not args.no_serving and ws == 1 else None
+
     # ---- end-to-end through the C ABI with host buffers ---------------------------------------
     Uh = U0.cpu().pin_memory()
     Uout = torch.empty_like(Uh).pin_memory()
@@ -264,6 +266,7 @@ def run_fluid(args):
                 "bytes_per_cell_axis": accounting.mixed_face_bytes()},
         },
         "adjoint": adjoint,
+        "serving": serving,
         "clocks": clk.summary(),
         "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
                   "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
@@ -335,6 +338,78 @@ def measure_adjoint(flush, stream, steps=5, warmup=3, grad_steps=400, K=20):
             "adjoint_forward_ratio": adj / fwd, "adjoint_forward_ratio_stored_stages": adj_stored / fwd,
             "gradient": {"steps": grad_steps, "checkpoint_every": K, "wall_s": t_grad, "J": J.item(),
                          "grad_norm_inf": float(p.grad.abs().max())}}
+
+
+def measure_serving(precision="mixed", count=64, rate_hz=40.0):
+    """Serving loop on a bounded sample of the serving stream: 70 % 2-D (isentropic vortex,
+    four-quadrant Riemann) on 64^2..512^2, 30 % 3-D Taylor-Green on 32^3..96^3, 10..200 steps,
+    Poisson arrivals.  Latency = finish - arrival; throughput = interior cell updates / makespan.
+    The baseline solves the same requests one at a time in arrival order (one solver, one stream,
+    no graphs), starting each when it has arrived and the previous one has finished."""
+    import torch
+    from paper_2406_19494_gb300.serve import Server
+    from paper_2406_19494_gb300.solver import Solver
+    stream = workloads.serving_stream(count, seed=3, n2d=(64, 512), n3d=(32, 96), steps=(10, 200),
+                                      rate_hz=rate_hz)
+
+    def centres_of(case):
+        s = Solver(case)
+        out = [s.grid(a)[0] for a in range(3)]
+        h = [3 if a < case["ndim"] else 0 for a in range(3)]
+        return [out[a][h[a]:len(out[a]) - h[a]] for a in range(3)]
+
+    reqs = []
+    for r in stream:
+        case, W = workloads.serving_case_and_prims(r, centres_of)
+        pad = [(0, 0)] + [(3 if a < case["ndim"] else 0,) * 2 for a in (2, 1, 0)]
+        s = Solver(case)
+        U = s.prim_to_cons(torch.from_numpy(np.ascontiguousarray(np.pad(W, pad, mode="edge"))).cuda())
+        cells = case["n"][0] * case["n"][1] * case["n"][2]
+        reqs.append((r, case, U.cpu().numpy(), cells))
+    total_cu = sum(r["nsteps"] * cells for r, _, _, cells in reqs)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    # continuous batching
+    srv = Server(budget_bytes=150e9, max_active=16, chunk_steps=10, graphs=True, autotune=True)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, case, U0, _ in reqs:
+        wait = r["arrival_s"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append((r, srv.submit(case, U0, r["nsteps"], precision=precision)))
+    lat, last = [], 0.0
+    for r, t in tickets:
+        res, _ = srv.poll(t, timeout_ms=600000)
+        lat.append(res["finish_s"] - res["submit_s"])
+        last = max(last, res["finish_s"])
+    st = srv.stats()
+    srv.close()
+    first = 0.0
+    makespan = last - first
+    # one solve per launch
+    lat1 = []
+    t0 = time.perf_counter()
+    for r, case, U0, _ in reqs:
+        now = time.perf_counter() - t0
+        if now < r["arrival_s"]:
+            time.sleep(r["arrival_s"] - now)
+        s = Solver(case, precision=precision)
+        U = torch.from_numpy(U0).cuda()
+        s.step(U, r["nsteps"])
+        U.cpu()
+        lat1.append(time.perf_counter() - t0 - r["arrival_s"])
+    makespan1 = time.perf_counter() - t0
+    return {"workload": "%d requests: 70%% 2-D vortex/Riemann 64^2..512^2, 30%% 3-D TGV 32^3..96^3, "
+                        "10..200 steps, Poisson %.0f/s (a bounded sample of the 512-request stream)" % (count, rate_hz),
+            "precision": precision, "cell_updates": total_cu,
+            "continuous_batching": {"p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "makespan_s": makespan,
+                                    "cell_updates_per_s": total_cu / makespan, "peak_hbm_bytes": st["peak_bytes"]},
+            "one_solve_per_launch": {"p50_s": pct(lat1, 0.5), "p99_s": pct(lat1, 0.99), "makespan_s": makespan1,
+                                     "cell_updates_per_s": total_cu / makespan1}}
 
 
 def measured_hbm_gbs():
@@ -439,6 +514,7 @@ def main():
     ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "fluid":
         args.warmup = 3

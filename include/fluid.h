@@ -268,6 +268,66 @@ int fluid_measure_peak(int kind, double* gflops, void* stream);
 int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, double* R_dev, void* stream,
                       char* errbuf, size_t errlen);
 
+/* ---- serving: continuous batching of many independent solves (a design sweep) -------------------
+ * A server owns one GPU and a scheduler thread.  Requests are admitted first-fit in arrival order
+ * as soon as their device footprint (fluid_serve_footprint) fits the HBM budget next to the solves
+ * already running and a slot is free; each running solve keeps its state on the device, runs on
+ * its own stream in chunks of steps replayed from a CUDA graph captured for it, and overlaps with
+ * the others; finished solves are copied back and their memory admits waiting requests.  The
+ * first solve of each grid shape times the face kernels' launch shapes (fluid_tune_faces) and the
+ * shape is kept for the bucket.  Results do not depend on the mix: every solve computes exactly
+ * what fluid_step computes alone. */
+typedef struct fluid_server fluid_server;
+
+typedef struct fluid_serve_config {
+  uint32_t struct_size;        /* sizeof(fluid_serve_config) */
+  int32_t device;              /* CUDA device of the server */
+  int32_t max_active;          /* concurrently running solves (streams), >= 1 */
+  int32_t chunk_steps;         /* RK3 steps per graph replay, >= 1 */
+  int32_t use_graphs;          /* capture a CUDA graph per solve */
+  int32_t autotune;            /* time launch shapes once per grid shape */
+  uint64_t hbm_budget_bytes;   /* admission budget for all running solves */
+} fluid_serve_config;
+
+typedef struct fluid_request {
+  uint32_t struct_size;        /* sizeof(fluid_request) */
+  int32_t nsteps;              /* RK3 steps */
+  fluid_config cfg;            /* the solve */
+  const double* U0_host;       /* initial padded state (copied during submit) */
+  double* U_out_host;          /* final state written here before the result is ready (may be NULL) */
+  double t_end;                /* as in fluid_step (<= 0: no limit) */
+} fluid_request;
+
+typedef struct fluid_result {
+  int32_t status;              /* fluid_status of the solve (FLUID_ENONFINITE, ...) */
+  int32_t steps_done;
+  double t_final;              /* solver time at the end */
+  double submit_s, start_s, finish_s;   /* server-clock seconds: submitted, admitted, done */
+} fluid_result;
+
+typedef struct fluid_serve_stats_t {
+  int64_t pending, active, admitted, completed;
+  uint64_t bytes_in_use, peak_bytes;
+  double cell_updates;         /* interior cells x steps of the completed solves */
+  double elapsed_s;
+} fluid_serve_stats_t;
+
+/* Start a server (spawns its scheduler thread).  FLUID_EINVAL for a bad config, FLUID_ECUDA when
+ * the device is unavailable. */
+int fluid_serve_create(const fluid_serve_config* cfg, fluid_server** out);
+/* Stop the scheduler (running solves finish with FLUID_EBUSY) and release everything. */
+void fluid_serve_destroy(fluid_server* s);
+/* Queue a request; never blocks on the GPU.  FLUID_EBUDGET if it can never fit the budget,
+ * FLUID_EINVAL for a bad request.  *ticket identifies it for fluid_serve_poll. */
+int fluid_serve_submit(fluid_server* s, const fluid_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (0: do not wait) for a result; FLUID_ETIMEOUT if it is not ready.  A
+ * delivered result is forgotten by the server (poll each ticket once). */
+int fluid_serve_poll(fluid_server* s, uint64_t ticket, fluid_result* out, int timeout_ms);
+/* Counters of the server (thread-safe). */
+int fluid_serve_stats(fluid_server* s, fluid_serve_stats_t* out);
+/* Device bytes a request of this configuration holds while it runs. */
+size_t fluid_serve_footprint(const fluid_config* cfg);
+
 /* Library build information: ABI version, and sizeof(fluid_config) expected. */
 int fluid_abi_version(void);
 size_t fluid_config_size(void);

@@ -48,6 +48,12 @@ SIGNATURES = {
     "fluid_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64), _i]),
     "fluid_measure_peak": (_i, [_i, ctypes.POINTER(_d), _vp]),
     "fluid_rhs_noalloc": (_i, [_vp, _vp, _vp, _vp, ctypes.c_char_p, _sz]),
+    "fluid_serve_create": (_i, [_vp, ctypes.POINTER(_vp)]),
+    "fluid_serve_destroy": (None, [_vp]),
+    "fluid_serve_submit": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "fluid_serve_poll": (_i, [_vp, ctypes.c_uint64, _vp, _i]),
+    "fluid_serve_stats": (_i, [_vp, _vp]),
+    "fluid_serve_footprint": (_sz, [_vp]),
     "fluid_abi_version": (_i, []),
     "fluid_config_size": (_sz, []),
 }
@@ -89,6 +95,31 @@ class FluidConfig(ctypes.Structure):
         ("adjoint", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
+
+
+class FluidServeConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("max_active", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class FluidRequest(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("nsteps", ctypes.c_int32),
+                ("cfg", FluidConfig), ("U0_host", ctypes.c_void_p), ("U_out_host", ctypes.c_void_p),
+                ("t_end", ctypes.c_double)]
+
+
+class FluidResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps_done", ctypes.c_int32), ("t_final", ctypes.c_double),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
+class FluidServeStats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("active", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("bytes_in_use", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("cell_updates", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double)]
 
 
 def config_from_case(case, precision="fp64", adjoint=False):

@@ -15,6 +15,8 @@ Cases (the configurations the solver is exercised and measured on):
   channel      3-D compressible channel, Ma_b 1.5, Re_b 3000, 192x128x128, tanh-stretched walls
   porous_bl    2-D Ma 6 laminar boundary layer, 512x128, disturbance/porous strip on the wall
   random_box   small random states on any boundary mix, for parity tests
+  serving      a stream of independent solves of uneven sizes (isentropic vortices, four-quadrant
+               Riemann problems, Taylor-Green vortices) with Poisson arrival times
 """
 import math
 
@@ -267,3 +269,86 @@ def random_prims(xc, yc, zc, seed=0, amp=1.0, modes=4, jump=True):
         out[0] = np.where(sel, out[0] * 0.6, out[0])
         out[4] = np.where(sel, out[4] * 0.7, out[4])
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# serving stream
+# ------------------------------------------------------------------------------------------------
+def vortex_case(n):
+    """2-D isentropic vortex on the periodic square [0, 10]^2, Euler, WENO5-Z."""
+    P = ("periodic", "periodic")
+    return _base(2, (n, n, 1), (0.0, 0.0, 0.0), (10.0, 10.0, 1.0), (P, P, P), weno="z",
+                 name="vortex%d" % n)
+
+
+def vortex_prims(xc, yc, strength=5.0, gamma=1.4):
+    """Textbook isentropic vortex (free stream rho = u = v = p = 1, R = 1) centred at (5, 5):
+    du = -b/(2 pi) e^{(1-r^2)/2} (y - 5), dv = b/(2 pi) e^{(1-r^2)/2} (x - 5),
+    T = 1 - (gamma - 1) b^2 / (8 gamma pi^2) e^{1 - r^2}, rho = T^{1/(gamma-1)}, p = rho T."""
+    y, x = np.meshgrid(yc, xc, indexing="ij")
+    dx, dy = x - 5.0, y - 5.0
+    r2 = dx * dx + dy * dy
+    f = np.exp(0.5 * (1.0 - r2))
+    u = 1.0 - strength / (2 * math.pi) * f * dy
+    v = 1.0 + strength / (2 * math.pi) * f * dx
+    T = 1.0 - (gamma - 1.0) * strength ** 2 / (8.0 * gamma * math.pi ** 2) * f * f
+    rho = T ** (1.0 / (gamma - 1.0))
+    z = np.zeros_like(u)
+    return np.stack([rho, u, v, z, rho * T])[:, None]
+
+
+def riemann2d_case(n):
+    """2-D four-quadrant Riemann problem on [0, 1]^2 with transmissive boundaries, Euler."""
+    Z = ("zero_gradient", "zero_gradient")
+    return _base(2, (n, n, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (Z, Z, ("periodic", "periodic")),
+                 weno="z", name="riemann%d" % n)
+
+
+def riemann2d_prims(xc, yc, seed):
+    """Seeded moderate four-quadrant data: per quadrant rho in [0.5, 1.5], p in [0.4, 1.2],
+    u, v in [-0.3, 0.3] (moderate jumps, no positivity limiter needed), split at (0.5, 0.5)."""
+    r = uniform01(seed, 16).reshape(4, 4)
+    y, x = np.meshgrid(yc, xc, indexing="ij")
+    q = (x >= 0.5).astype(int) + 2 * (y >= 0.5).astype(int)
+    rho = 0.5 + r[:, 0][q]
+    u = -0.3 + 0.6 * r[:, 1][q]
+    v = -0.3 + 0.6 * r[:, 2][q]
+    p = 0.4 + 0.8 * r[:, 3][q]
+    return np.stack([rho, u, v, np.zeros_like(u), p])[:, None]
+
+
+def serving_stream(count=512, seed=0, frac_2d=0.7, n2d=(64, 1024), n3d=(32, 160), steps=(100, 2000),
+                   rate_hz=None):
+    """Requests of the serving workload: dicts with kind, n, nsteps, arrival_s (Poisson process of
+    rate `rate_hz`, all at 0 when None) and seed.  2-D grids log-uniform in n2d^2 (half vortices,
+    half Riemann problems), 3-D Taylor-Green grids log-uniform in n3d^3, steps uniform."""
+    r = uniform01(seed + 77, 6 * count).reshape(count, 6)
+    out = []
+    t = 0.0
+    for i in range(count):
+        if rate_hz:
+            t += -math.log(1.0 - r[i, 5]) / rate_hz
+        if r[i, 0] < frac_2d:
+            n = int(round(math.exp(math.log(n2d[0]) + r[i, 1] * (math.log(n2d[1]) - math.log(n2d[0])))))
+            kind = "vortex" if r[i, 2] < 0.5 else "riemann"
+        else:
+            n = int(round(math.exp(math.log(n3d[0]) + r[i, 1] * (math.log(n3d[1]) - math.log(n3d[0])))))
+            kind = "tgv"
+        ns = int(steps[0] + r[i, 3] * (steps[1] - steps[0]))
+        out.append(dict(kind=kind, n=n, nsteps=ns, arrival_s=t, seed=int(seed * 1000 + i)))
+    return out
+
+
+def serving_case_and_prims(req, centres_of):
+    """(case, interior primitives) of one serving request; centres_of(case) gives (xc, yc, zc)."""
+    if req["kind"] == "vortex":
+        c = vortex_case(req["n"])
+        xc, yc, _ = centres_of(c)
+        return c, vortex_prims(xc, yc)
+    if req["kind"] == "riemann":
+        c = riemann2d_case(req["n"])
+        xc, yc, _ = centres_of(c)
+        return c, riemann2d_prims(xc, yc, req["seed"])
+    c = tgv_case(req["n"])
+    xc, yc, zc = centres_of(c)
+    return c, tgv_prims(c, xc, yc, zc)

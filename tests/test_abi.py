@@ -74,3 +74,20 @@ def test_porous_strip_must_fit(lib):
 def test_null_out_pointer(lib):
     cfg = native.config_from_case(wl.sod_case(16))
     assert lib.fluid_create(ctypes.byref(cfg), None) == native.FLUID_EINVAL
+
+
+def test_serve_config_rejected_before_any_gpu_call(lib):
+    c = native.FluidServeConfig(struct_size=4, device=0, max_active=1, chunk_steps=1, use_graphs=1,
+                                autotune=0, hbm_budget_bytes=1 << 30)
+    h = ctypes.c_void_p()
+    assert lib.fluid_serve_create(ctypes.byref(c), ctypes.byref(h)) == native.FLUID_EINVAL
+    c.struct_size = ctypes.sizeof(native.FluidServeConfig)
+    c.max_active = 0
+    assert lib.fluid_serve_create(ctypes.byref(c), ctypes.byref(h)) == native.FLUID_EINVAL
+
+
+def test_serve_footprint_grows_with_the_grid(lib):
+    small = native.config_from_case(wl.tgv_case(32))
+    big = native.config_from_case(wl.tgv_case(64))
+    fs, fb = lib.fluid_serve_footprint(ctypes.byref(small)), lib.fluid_serve_footprint(ctypes.byref(big))
+    assert 0 < fs < fb and fb > 8 * 38 ** 3 * 30
