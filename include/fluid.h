@@ -245,6 +245,11 @@ int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* lau
  * (2 flops per FMA) of a kernel of independent FMA chains over every SM. */
 int fluid_measure_peak(int kind, double* gflops, void* stream);
 
+/* Accuracy check of the reciprocal the kernels use in place of division (a Newton-Raphson step
+ * from the hardware estimate): fast[i] = that reciprocal of y[i], ieee[i] = 1.0 / y[i], for n
+ * device values.  For tests. */
+int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n, void* stream);
+
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as
  * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is
  * owned by its own pool or arena and which forbids allocations behind its back, or a

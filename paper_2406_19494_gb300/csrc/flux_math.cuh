@@ -21,6 +21,21 @@ FL_HD double fl_rsqrt(double x) {
 #endif
 }
 
+// Reciprocal by Newton-Raphson iteration for 1/y (one step with its second-order term,
+// r' = r + r (e + e^2), e = 1 - y r, which cubes the relative error) from the hardware estimate of
+// the PTX instruction rcp.approx.ftz.f64.  For positive normal y the result is within a few ulp of
+// 1/y (checked against CUDA's division by fluid_check_math).  Host code divides.
+FL_HD double fl_rcp(double y) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  const double e = fma(-y, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+#else
+  return 1.0 / y;
+#endif
+}
+
 constexpr double kSixth = 1.0 / 6.0;
 constexpr double k1312 = 13.0 / 12.0;
 constexpr double kTwelfth = 1.0 / 12.0;
@@ -30,19 +45,29 @@ constexpr double k16th = 1.0 / 16.0;
 // ------------------------------------------------------------------------------------------------
 // WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}
 // ------------------------------------------------------------------------------------------------
+// Smoothness indicators of the three-cell stencil (a, b, c) in the three positions WENO5 uses it:
+// as the left candidate (A), the centre one (B) and the right one (C) of a left-biased face value.
+FL_HD double weno_A(double a, double b, double c) {
+  const double t = a - 2.0 * b + c, s = a - 4.0 * b + 3.0 * c;
+  return k1312 * t * t + 0.25 * s * s;
+}
+FL_HD double weno_B(double a, double b, double c) {
+  const double t = a - 2.0 * b + c, s = a - c;
+  return k1312 * t * t + 0.25 * s * s;
+}
+FL_HD double weno_C(double a, double b, double c) {
+  const double t = a - 2.0 * b + c, s = 3.0 * a - 4.0 * b + c;
+  return k1312 * t * t + 0.25 * s * s;
+}
+
+// WENO5 face value from the stencil and its three smoothness indicators (beta_0, beta_1, beta_2)
 template <int SCHEME>
-FL_HD double weno5(double qm2, double qm1, double q0, double qp1, double qp2,
-                                        double eps) {
+FL_HD double weno5_beta(double qm2, double qm1, double q0, double qp1, double qp2, double b0,
+                        double b1, double b2, double eps) {
   // candidate values times 6
   const double C0 = 2.0 * qm2 - 7.0 * qm1 + 11.0 * q0;
   const double C1 = -qm1 + 5.0 * q0 + 2.0 * qp1;
   const double C2 = 2.0 * q0 + 5.0 * qp1 - qp2;
-  double t = qm2 - 2.0 * qm1 + q0, s = qm2 - 4.0 * qm1 + 3.0 * q0;
-  const double b0 = k1312 * t * t + 0.25 * s * s;
-  t = qm1 - 2.0 * q0 + qp1; s = qm1 - qp1;
-  const double b1 = k1312 * t * t + 0.25 * s * s;
-  t = q0 - 2.0 * qp1 + qp2; s = 3.0 * q0 - 4.0 * qp1 + qp2;
-  const double b2 = k1312 * t * t + 0.25 * s * s;
   // Weights scaled by a common positive factor so that one division remains.  With
   // e_k = beta_k + eps and Q_k = prod_{j != k} e_j:
   //   JS: d_k / e_k^2                  = d_k Q_k^2 / P^2,              P = e0 e1 e2
@@ -62,7 +87,14 @@ FL_HD double weno5(double qm2, double qm1, double q0, double qp1, double qp2,
     a1 = 0.6 * (PP + tt * (Q1 * Q1));
     a2 = 0.3 * (PP + tt * (Q2 * Q2));
   }
-  return (a0 * C0 + a1 * C1 + a2 * C2) / (6.0 * (a0 + a1 + a2));
+  return (a0 * C0 + a1 * C1 + a2 * C2) * fl_rcp(6.0 * (a0 + a1 + a2));
+}
+
+// WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}
+template <int SCHEME>
+FL_HD double weno5(double qm2, double qm1, double q0, double qp1, double qp2, double eps) {
+  return weno5_beta<SCHEME>(qm2, qm1, q0, qp1, qp2, weno_A(qm2, qm1, q0), weno_B(qm1, q0, qp1),
+                            weno_C(q0, qp1, qp2), eps);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -83,7 +115,7 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const double sL = rL * qL, sR = rR * qR;
   const double irL = qL * qL, irR = qR * qR;
   const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
-  const double isum = 1.0 / (sL + sR);
+  const double isum = fl_rcp(sL + sR);
   const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
   const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
   const double ut2 = (sL * wl[3] + sR * wr[3]) * isum;
@@ -94,7 +126,7 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const double SL = fmin(unL - cL, utn - ct);
   const double SR = fmax(unR + cR, utn + ct);
   const double mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const double Ss = (pR - pL + unL * mL - unR * mR) / (mL - mR);
+  const double Ss = (pR - pL + unL * mL - unR * mR) * fl_rcp(mL - mR);
 
   const bool left = (SL >= 0.0) || (Ss >= 0.0);
   const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
@@ -117,7 +149,7 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   F[4] = un * (E + p);
   if (star) {
     // U*_K = m/(S - S*) [1, S* (normal), tangential u, E/rho + (S* - un)(S* + p/m)]
-    const double q = 1.0 / (S - Ss);
+    const double q = fl_rcp(S - Ss);
     const double fac = m * q;
     const double ir = left ? irL : irR;
     const double dU0 = fac - r;
@@ -138,7 +170,7 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
 // ------------------------------------------------------------------------------------------------
 FL_HD void prim_from_cons(const double U[5], const Phys& ph, double w[6]) {
   const double r = U[0];
-  const double ir = 1.0 / r;
+  const double ir = fl_rcp(r);
   const double u = U[1] * ir, v = U[2] * ir, ww = U[3] * ir;
   const double p = ph.gm1 * (U[4] - 0.5 * r * (u * u + v * v + ww * ww));
   w[0] = r; w[1] = u; w[2] = v; w[3] = ww; w[4] = p; w[5] = p * ir * ph.iR;

@@ -157,7 +157,10 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
 template <int D, int SCHEME, bool VISC>
 __device__ __forceinline__ void face_flux(const double* __restrict__ W, const double* __restrict__ G,
                                           int cell, int s, int a, const Geo& g, const Phys& ph,
-                                          double F[5]) {
+                                          double F[5], double bA[5], double bB[5], double bC[5]) {
+  // bA, bB, bC hold the indicators A_{a-1}, B_a, C_{a+1} of the triples centred at a-1, a, a+1
+  // (computed at the previous face); the left state needs exactly these, the right state needs
+  // C_{a+2}, B_{a+1}, A_a, which become the next face's left indicators.
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -167,8 +170,14 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
   double wl[5], wr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    wl[v] = weno5<SCHEME>(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], ph.eps);
-    wr[v] = weno5<SCHEME>(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], ph.eps);
+    const double An = weno_A(q[v][1], q[v][2], q[v][3]);
+    const double Bn = weno_B(q[v][2], q[v][3], q[v][4]);
+    const double Cn = weno_C(q[v][3], q[v][4], q[v][5]);
+    wl[v] = weno5_beta<SCHEME>(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], bA[v], bB[v], bC[v], ph.eps);
+    wr[v] = weno5_beta<SCHEME>(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], Cn, Bn, An, ph.eps);
+    bA[v] = An;
+    bB[v] = Bn;
+    bC[v] = Cn;
   }
   hllc<D>(wl, wr, ph, F);
   if (!VISC) return;
@@ -225,11 +234,20 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5];
-    face_flux<D, SCHEME, VISC>(W, G, cell, s, a0 - 1, g, ph, Fp);
+    double Fp[5], F[5], bA[5], bB[5], bC[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double* f = W + v * nc + cell;
+      const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
+                   qp2 = __ldg(f + 2 * s);
+      bA[v] = weno_A(qm2, qm1, q0);
+      bB[v] = weno_B(qm1, q0, qp1);
+      bC[v] = weno_C(q0, qp1, qp2);
+    }
+    face_flux<D, SCHEME, VISC>(W, G, cell, s, a0 - 1, g, ph, Fp, bA, bB, bC);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux<D, SCHEME, VISC>(W, G, cell, s, a, g, ph, F);
+      face_flux<D, SCHEME, VISC>(W, G, cell, s, a, g, ph, F, bA, bB, bC);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

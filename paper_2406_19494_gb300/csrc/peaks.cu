@@ -50,3 +50,25 @@ extern "C" int fluid_measure_peak(int kind, double* gflops, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return kind == 0 ? probe<double>(gflops, st) : probe<float>(gflops, st);
 }
+
+// ---- accuracy check of the kernels' Newton reciprocal against the IEEE division ----------------
+#include "flux_math.cuh"
+
+namespace {
+__global__ void k_check_rcp(const double* __restrict__ y, double* __restrict__ fast,
+                            double* __restrict__ ieee, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    fast[i] = fl::fl_rcp(y[i]);
+    ieee[i] = 1.0 / y[i];
+  }
+}
+}  // namespace
+
+extern "C" int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n,
+                               void* stream) {
+  if (!y_dev || !fast_dev || !ieee_dev || n < 0) return FLUID_EINVAL;
+  if (n == 0) return FLUID_OK;
+  k_check_rcp<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0,
+                reinterpret_cast<cudaStream_t>(stream)>>>(y_dev, fast_dev, ieee_dev, n);
+  return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
+}

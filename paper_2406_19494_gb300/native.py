@@ -48,6 +48,7 @@ SIGNATURES = {
     "fluid_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64), _i]),
     "fluid_measure_peak": (_i, [_i, ctypes.POINTER(_d), _vp]),
     "fluid_rhs_noalloc": (_i, [_vp, _vp, _vp, _vp, ctypes.c_char_p, _sz]),
+    "fluid_check_rcp": (_i, [_vp, _vp, _vp, _i, _vp]),
     "fluid_serve_create": (_i, [_vp, ctypes.POINTER(_vp)]),
     "fluid_serve_destroy": (None, [_vp]),
     "fluid_serve_submit": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
