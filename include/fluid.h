@@ -214,8 +214,9 @@ int fluid_check(fluid_solver* s, void* stream);
 /* Launch shape of the face kernels: threads per block (a multiple of 32 in [32, 128]; 0 = 128)
  * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8
  * that still fills the GPU).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
- * tiles by default; seg < 0 selects the register-window marching kernels with |seg| cells per
- * segment instead.  Results do not depend on the shape. */
+ * tiles of 2 warps (block 64) or 4 warps (otherwise) by default; seg < 0 selects the register-window
+ * marching kernels with |seg| cells per segment and `block` threads instead.  Results do not
+ * depend on the shape. */
 int fluid_tune_faces(fluid_solver* s, int block, int seg);
 
 /* Kernel classes reported by the profiler. */

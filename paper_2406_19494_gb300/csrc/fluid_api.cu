@@ -27,7 +27,8 @@ struct fluid_solver {
   double* W = nullptr;             // primitives, NW * ncell
   double* G = nullptr;             // velocity gradients, NG * ncell (viscous, FP64 path)
   bool mixed = false;              // FLUID_PREC_MIXED: FP32 fluxes, FP64 state
-  float* W32 = nullptr;            // FP32 primitives (mixed)
+  float* W32 = nullptr;            // FP32 (hi, lo) primitives, 2 NW * ncell (mixed)
+  float* mf32 = nullptr;           // FP32 face metrics of the three axes (mixed)
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
   double* R = nullptr;             // right-hand side accumulator, NV * ncell
@@ -384,10 +385,13 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
     return fail(nullptr, err == cudaErrorMemoryAllocation ? FLUID_ENOMEM : FLUID_ECUDA, m);
   };
   if ((e = cudaMalloc(&s->metric, nmetric * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc metric");
-  if ((e = cudaMalloc(&s->W, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W");
   s->mixed = c.precision == FLUID_PREC_MIXED;
+  // the mixed path keeps H = E + p in one more FP64 row of W
+  if ((e = cudaMalloc(&s->W, (fl::NW + (s->mixed ? 1 : 0)) * nc * sizeof(double))) != cudaSuccess)
+    return bail(e, "cudaMalloc W");
   if (s->mixed) {
-    if ((e = cudaMalloc(&s->W32, fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    if ((e = cudaMalloc(&s->W32, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    if ((e = cudaMalloc(&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
     if (c.visc_law != FLUID_VISC_NONE)
       if ((e = cudaMalloc(&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
   } else if (c.visc_law != FLUID_VISC_NONE) {
@@ -415,6 +419,17 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   }
   if ((e = cudaMemcpy(s->metric, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(e, "metric upload");
+  if (s->mixed) {
+    std::vector<float> mf32;
+    size_t off32[3];
+    for (int a = 0; a < 3; ++a) {
+      off32[a] = mf32.size();
+      for (int k = 0; k < g.p[a]; ++k) mf32.push_back((float)all[off[a][4] + k]);
+    }
+    if ((e = cudaMemcpy(s->mf32, mf32.data(), mf32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "metric upload");
+    for (int a = 0; a < 3; ++a) g.mf32[a] = s->mf32 + off32[a];
+  }
   for (int a = 0; a < 3; ++a) {
     g.xc[a] = s->metric + off[a][0];
     g.dx[a] = s->metric + off[a][1];
@@ -504,6 +519,7 @@ void fluid_destroy(fluid_solver* s) {
   cudaFree(s->W);
   cudaFree(s->G);
   cudaFree(s->W32);
+  cudaFree(s->mf32);
   cudaFree(s->G32);
   for (double* p : {s->gW, s->gG, s->CW, s->CG, s->S1, s->S2, s->MU, s->L1, s->L2, s->GT, s->gvw,
                     s->parts, s->gT2})

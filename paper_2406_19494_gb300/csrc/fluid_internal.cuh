@@ -27,6 +27,7 @@ struct Geo {
   const double* idx[3];  // 1 / widths
   const double* mc[3];   // d(index)/dx at centres
   const double* mf[3];   // d(index)/dx at face a+1/2
+  const float* mf32[3];  // FP32 copy of mf (mixed path only, else null)
 };
 
 struct Phys {
@@ -80,7 +81,8 @@ __host__ __device__ __forceinline__ double viscosity_dT(double T, const Phys& ph
 const char* config_error(const fluid_config* c);
 
 // ---- launchers implemented in kernels_fp64.cu --------------------------------------------------
-// W32 (optional, may be null): FP32 copy of the primitives for the mixed-precision path
+// W32 (mixed path only, else null): exact FP32 (hi, lo) split of the primitives, [2 NW][ncell];
+// with it W must hold NW + 1 rows, the last receiving H = E + p
 cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
                            const BC& bc, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t st);

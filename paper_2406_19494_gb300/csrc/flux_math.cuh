@@ -90,6 +90,45 @@ FL_HD double weno5_beta(double qm2, double qm1, double q0, double qp1, double qp
   return (a0 * C0 + a1 * C1 + a2 * C2) * fl_rcp(6.0 * (a0 + a1 + a2));
 }
 
+// The same reconstruction split for marching along a grid line.  The indicator set of the
+// right-biased value at face a+1/2 is, with the roles of its outer members exchanged, the set of
+// the left-biased value at a+3/2; weno_x gives the scaled weights of a set (X_k = alpha_k / d_k
+// times the common factor of weno5_beta, which is symmetric under that exchange) so that one set
+// serves both faces, and weno_x_value forms the value from the stencil and the X's with the
+// linear weights d_k and 1/6 folded into the candidate coefficients.
+template <int SCHEME>
+FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
+  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  if (SCHEME == FLUID_WENO_JS) {
+    X[0] = Q0 * Q0; X[1] = Q1 * Q1; X[2] = Q2 * Q2;
+  } else {
+    const double tau = fabs(b0 - b2);
+    const double P = e0 * Q0;
+    const double PP = P * P, tt = tau * tau;
+    X[0] = fma(tt, Q0 * Q0, PP);
+    X[1] = fma(tt, Q1 * Q1, PP);
+    X[2] = fma(tt, Q2 * Q2, PP);
+  }
+}
+
+FL_HD double weno_x_value(double qm2, double qm1, double q0, double qp1, double qp2, const double X[3]) {
+  // d_k / 6 times the candidate values: d = (1/10, 6/10, 3/10)
+  const double C0 = fma(11.0 / 60.0, q0, fma(-7.0 / 60.0, qm1, (1.0 / 30.0) * qm2));
+  const double C1 = fma(0.2, qp1, fma(0.5, q0, -0.1 * qm1));
+  const double C2 = fma(-0.05, qp2, fma(0.25, qp1, 0.1 * q0));
+  const double num = fma(X[2], C2, fma(X[1], C1, X[0] * C0));
+  const double den = fma(0.3, X[2], fma(0.6, X[1], 0.1 * X[0]));
+  return num * fl_rcp(den);
+}
+
+// 13/12 t^2 with t the second difference of a three-cell stencil: the part the three indicator
+// positions A, B, C of one stencil have in common (A = K + s_A^2 / 4 and so on)
+FL_HD double weno_k(double a, double b, double c) {
+  const double t = fma(-2.0, b, a) + c;
+  return k1312 * t * t;
+}
+
 // WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}
 template <int SCHEME>
 FL_HD double weno5(double qm2, double qm1, double q0, double qp1, double qp2, double eps) {

@@ -63,57 +63,92 @@ __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a
   w[5] = w[4] / (w[0] * ph.R);
 }
 
+// primitives of padded cell own[] (interior: from U; halo: composed boundary maps); E receives the
+// total energy per volume of interior cells (halo cells leave it unset)
+__device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const int own[3], int cell,
+                                          const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
+                                          double w[NW], double& E) {
+  bool ghost[3];
+  int side[3], src[3];
+  bool any = false;
+  for (int a = 0; a < 3; ++a) {
+    ghost[a] = own[a] < g.h[a] || own[a] >= g.h[a] + g.n[a];
+    side[a] = own[a] < g.h[a] ? 0 : 1;
+    src[a] = ghost[a] ? bc_source(bc.kind[a][side[a]], side[a], own[a], g.n[a], g.h[a]) : own[a];
+    any |= ghost[a];
+  }
+  if (!any) {
+    prim_of(U, cell, g.ncell, ph, w);
+    E = U[4 * g.ncell + cell];
+    return false;
+  }
+  // Sequential halo passes x -> y -> z, composed: the pass of axis a sees own indices on the
+  // axes before it and source indices on the axes after it.
+  bool have = false;
+  for (int a = 0; a < 3; ++a) {
+    if (!ghost[a]) continue;
+    const int kind = bc.kind[a][side[a]];
+    int c[3];
+    for (int b = 0; b < 3; ++b) c[b] = b < a ? own[b] : src[b];
+    if (kind == FLUID_BC_INFLOW) {
+      inflow_at(bc.inflow[a][side[a]], a, c, g, ph, w);
+      have = true;
+      continue;
+    }
+    if (!have) {
+      c[a] = src[a];
+      prim_of(U, c[0] + c[1] * g.sy + c[2] * g.sz, g.ncell, ph, w);
+      have = true;
+    }
+    if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) continue;
+    double vw = 0.0;
+    if (kind == FLUID_BC_POROUS) vw = bc.vw[c[bc.porous_t1]];
+    wall_map(w, kind, bc.Tw[a][side[a]], vw, a, ph, &ctl->flags);
+  }
+  return true;
+}
+
+// Split x = hi + lo + r with |r| <= 2^-48 |x|, using integer operations only: hi keeps the sign,
+// the exponent and the leading 23 fraction bits of x (x truncated to FP32 precision, exact), lo the
+// remaining 29 fraction bits rounded to FP32.  Below 2^-73 lo is dropped (|r| < 2^-23 |x| <
+// 1.2e-29), below 2^-126 both are zero; |x| >= 2^128 or a non-finite x gives NaN, which the
+// non-finite check then reports.
+__device__ __forceinline__ void split_hi_lo(double x, float& hi, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);            // biased FP64 exponent
+  if (e < 1023 - 126) { hi = __int_as_float(sign); lo = 0.0f; return; }
+  if (e > 1023 + 127) { hi = __int_as_float(0x7fc00000); lo = hi; return; }
+  hi = __int_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // lo = (low 29 fraction bits) * 2^(e - 1075), with 2^(e - 1075) a normal float when e > 948
+  const int es = e - 1075 + 127;
+  const float m = (float)(lw & 0x1fffffffu);
+  lo = es > 0 ? __int_as_float(sign | __float_as_int(m * __int_as_float(es << 23))) : 0.0f;
+}
+
+// One thread per padded cell: x from the thread index, y and z from the block index.
+// MIXED: the primitives also go to W32 = [2 NW][ncell] floats as the split (hi, lo) above, and
+// H = E + p to the FP64 row W[NW]; the FP32 face kernels form their cell differences from the pairs.
+template <bool MIXED>
 __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
                           float* __restrict__ W32, Geo g, Phys ph, BC bc, Ctl* ctl) {
-  const int total = g.ncell;
-  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < total;
-       cell += gridDim.x * blockDim.x) {
-    int own[3];
-    own[0] = cell % g.p[0];
-    const int r = cell / g.p[0];
-    own[1] = r % g.p[1];
-    own[2] = r / g.p[1];
-    bool ghost[3];
-    int side[3], src[3];
-    bool any = false;
-    for (int a = 0; a < 3; ++a) {
-      ghost[a] = own[a] < g.h[a] || own[a] >= g.h[a] + g.n[a];
-      side[a] = own[a] < g.h[a] ? 0 : 1;
-      src[a] = ghost[a] ? bc_source(bc.kind[a][side[a]], side[a], own[a], g.n[a], g.h[a]) : own[a];
-      any |= ghost[a];
-    }
-    double w[NW];
-    if (!any) {
-      prim_of(U, cell, g.ncell, ph, w);
-    } else {
-      // Sequential halo passes x -> y -> z, composed: the pass of axis a sees own indices on the
-      // axes before it and source indices on the axes after it.
-      bool have = false;
-      for (int a = 0; a < 3; ++a) {
-        if (!ghost[a]) continue;
-        const int kind = bc.kind[a][side[a]];
-        int c[3];
-        for (int b = 0; b < 3; ++b) c[b] = b < a ? own[b] : src[b];
-        if (kind == FLUID_BC_INFLOW) {
-          inflow_at(bc.inflow[a][side[a]], a, c, g, ph, w);
-          have = true;
-          continue;
-        }
-        if (!have) {
-          c[a] = src[a];
-          prim_of(U, c[0] + c[1] * g.sy + c[2] * g.sz, g.ncell, ph, w);
-          have = true;
-        }
-        if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) continue;
-        double vw = 0.0;
-        if (kind == FLUID_BC_POROUS) vw = bc.vw[c[bc.porous_t1]];
-        wall_map(w, kind, bc.Tw[a][side[a]], vw, a, ph, &ctl->flags);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.p[0]) return;
+  for (int k = blockIdx.z; k < g.p[2]; k += gridDim.z)
+    for (int j = blockIdx.y; j < g.p[1]; j += gridDim.y) {
+      const int own[3] = {i, j, k};
+      const int cell = i + j * g.sy + k * g.sz;
+      double w[NW];
+      double E = 0.0;
+      const bool halo = prim_cell(U, own, cell, g, ph, bc, ctl, w, E);
+      for (int v = 0; v < NW; ++v) W[v * g.ncell + cell] = w[v];
+      if (MIXED) {
+        for (int v = 0; v < NW; ++v)
+          split_hi_lo(w[v], W32[v * g.ncell + cell], W32[(NW + v) * g.ncell + cell]);
+        if (halo) E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        W[NW * g.ncell + cell] = E + w[4];
       }
     }
-    for (int v = 0; v < NW; ++v) W[v * g.ncell + cell] = w[v];
-    if (W32)
-      for (int v = 0; v < NW; ++v) W32[v * g.ncell + cell] = (float)w[v];
-  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -157,10 +192,11 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
 template <int D, int SCHEME, bool VISC>
 __device__ __forceinline__ void face_flux(const double* __restrict__ W, const double* __restrict__ G,
                                           int cell, int s, int a, const Geo& g, const Phys& ph,
-                                          double F[5], double bA[5], double bB[5], double bC[5]) {
-  // bA, bB, bC hold the indicators A_{a-1}, B_a, C_{a+1} of the triples centred at a-1, a, a+1
-  // (computed at the previous face); the left state needs exactly these, the right state needs
-  // C_{a+2}, B_{a+1}, A_a, which become the next face's left indicators.
+                                          double F[5], double xl[5][3], double k0[5], double k1[5]) {
+  // Carried along the march, per primitive: xl, the scaled weights (weno_x) of the left-biased
+  // value at this face, whose indicator set (A_{a-1}, B_a, C_{a+1}) was the right-biased set of
+  // the previous face; k0, k1 = weno_k of the stencils centred at a and a+1.  The right-biased
+  // value needs C_{a+2}, B_{a+1}, A_a: one new stencil (centred at a+2) per face.
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -170,14 +206,23 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
   double wl[5], wr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double An = weno_A(q[v][1], q[v][2], q[v][3]);
-    const double Bn = weno_B(q[v][2], q[v][3], q[v][4]);
-    const double Cn = weno_C(q[v][3], q[v][4], q[v][5]);
-    wl[v] = weno5_beta<SCHEME>(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], bA[v], bB[v], bC[v], ph.eps);
-    wr[v] = weno5_beta<SCHEME>(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], Cn, Bn, An, ph.eps);
-    bA[v] = An;
-    bB[v] = Bn;
-    bC[v] = Cn;
+    // cells a-2 .. a+3 are q[v][0..5]
+    const double k2 = weno_k(q[v][3], q[v][4], q[v][5]);
+    const double sA = fma(3.0, q[v][3], fma(-4.0, q[v][2], q[v][1]));
+    const double sB = q[v][2] - q[v][4];
+    const double sC = fma(3.0, q[v][3], fma(-4.0, q[v][4], q[v][5]));
+    const double An = fma(0.25 * sA, sA, k0[v]);
+    const double Bn = fma(0.25 * sB, sB, k1[v]);
+    const double Cn = fma(0.25 * sC, sC, k2);
+    wl[v] = weno_x_value(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], xl[v]);
+    double xr[3];
+    weno_x<SCHEME>(Cn, Bn, An, ph.eps, xr);
+    wr[v] = weno_x_value(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], xr);
+    xl[v][0] = xr[2];
+    xl[v][1] = xr[1];
+    xl[v][2] = xr[0];
+    k0[v] = k1[v];
+    k1[v] = k2;
   }
   hllc<D>(wl, wr, ph, F);
   if (!VISC) return;
@@ -234,20 +279,21 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], bA[5], bB[5], bC[5];
+    double Fp[5], F[5], xl[5][3], k0[5], k1[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
+      // the left-biased set of face a0 - 1/2 and the stencil terms it carries forward
       const double* f = W + v * nc + cell;
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
-      bA[v] = weno_A(qm2, qm1, q0);
-      bB[v] = weno_B(qm1, q0, qp1);
-      bC[v] = weno_C(q0, qp1, qp2);
+      weno_x<SCHEME>(weno_A(qm2, qm1, q0), weno_B(qm1, q0, qp1), weno_C(q0, qp1, qp2), ph.eps, xl[v]);
+      k0[v] = weno_k(qm1, q0, qp1);
+      k1[v] = weno_k(q0, qp1, qp2);
     }
-    face_flux<D, SCHEME, VISC>(W, G, cell, s, a0 - 1, g, ph, Fp, bA, bB, bC);
+    face_flux<D, SCHEME, VISC>(W, G, cell, s, a0 - 1, g, ph, Fp, xl, k0, k1);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux<D, SCHEME, VISC>(W, G, cell, s, a, g, ph, F, bA, bB, bC);
+      face_flux<D, SCHEME, VISC>(W, G, cell, s, a, g, ph, F, xl, k0, k1);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -439,7 +485,13 @@ cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, c
 
 cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
                            const BC& bc, Ctl* ctl, cudaStream_t st) {
-  k_prim_bc<<<grid_for(g.ncell, 256), 256, 0, st>>>(U, W, W32, g, ph, bc, ctl);
+  // a padded row in nb near-equal chunks of whole warps, at most 256 threads each
+  const int nb = (g.p[0] + 255) / 256;
+  const int block = ((g.p[0] + nb - 1) / nb + 31) / 32 * 32;
+  const dim3 grid((g.p[0] + block - 1) / block, g.p[1] < 65535 ? g.p[1] : 65535,
+                  g.p[2] < 65535 ? g.p[2] : 65535);
+  if (W32) k_prim_bc<true><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl);
+  else k_prim_bc<false><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl);
   return cudaGetLastError();
 }
 

@@ -7,10 +7,14 @@
 // carries an absolute error ~6e-8 |F| that the divergence divides by dx.  Here every FP32 quantity
 // is either a coefficient (used only as a factor) or a small increment that FP32 represents to
 // ~6e-8 of its own size:
-//   * cell differences D_j = q_{j+1} - q_j of the primitives are taken in FP64 and rounded once;
+//   * cell differences D_j = q_{j+1} - q_j of the primitives come from the exact FP32 split
+//     q = hi + lo written by the primitive kernel: (hi_{j+1} - hi_j) + (lo_{j+1} - lo_j), each
+//     FP32 subtraction rounding relative to its own result, so D_j is within ~1 ulp (FP32) of the
+//     FP64 difference, up to 2^-48 |q| from the split;
 //   * WENO5 works on offsets delta_k = q_{a+k} - q_a built from the D's (the smoothness
 //     indicators and the weights do not depend on the offset, the candidates are affine);
-//   * the face flux is F_{a+1/2} = F(q_a) [FP64] + X [FP32], where X is the change of the Euler
+//   * the face flux is F_{a+1/2} = F(q_a) [FP64, from the primitives and H = E + p] + X [FP32],
+//     where X is the change of the Euler
 //     flux from the cell state q_a to the upwind face state, written as a polynomial in the
 //     offsets, plus the HLLC star correction S_K (U*_K - U_K), written through the jumps of the
 //     reconstructed states (S* - u_K from the pressure and velocity jumps), minus the
@@ -29,12 +33,53 @@ constexpr float k1312f = 13.0f / 12.0f;
 constexpr float kZepsF = 1e-20f;      // WENO5-Z epsilon in FP32 (a normal float)
 constexpr float kZclampF = 1e18f;     // bound of tau5 / (beta + eps): keeps its square finite
 
+// FP32 reciprocal, square root and reciprocal square root from the hardware approximations
+// (PTX rcp.approx / sqrt.approx / rsqrt.approx, each within a few ulp; denormal inputs flush
+// to zero). The FP32 increments need ~1e-7 relative accuracy, so the IEEE-rounded division and
+// square root, with their refinement steps and slow-path checks, are not needed here.
+__device__ __forceinline__ float rcpf(float y) {
+  float r; asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y)); return r;
+}
+__device__ __forceinline__ float sqrtf_a(float y) {
+  float r; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y)); return r;
+}
+__device__ __forceinline__ float rsqrtf_a(float y) {
+  float r; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y)); return r;
+}
+
 int grid_for(long long work, int block) {
   long long b = (work + block - 1) / block;
   if (b < 1) b = 1;
   if (b > 152LL * 64) b = 152LL * 64;
   return (int)b;
 }
+
+// FP32 copies of the physical constants the increments use (no per-face conversions)
+struct PhysF {
+  float gamma, gm1, igm1, gg;            // gg = gamma / (gamma - 1)
+  float mu_ref, iT_ref, visc_exp, TS, S; // TS = T_ref + S (Sutherland)
+  float lam_fac, eps, dt_visc_k;
+  int visc;
+};
+
+PhysF phys_f(const Phys& ph) {
+  PhysF f;
+  f.gamma = (float)ph.gamma; f.gm1 = (float)ph.gm1; f.igm1 = (float)ph.igm1;
+  f.gg = (float)(ph.gamma * ph.igm1);
+  f.mu_ref = (float)ph.mu_ref; f.iT_ref = (float)ph.iT_ref; f.visc_exp = (float)ph.visc_exp;
+  f.TS = (float)(ph.T_ref + ph.suth_S); f.S = (float)ph.suth_S;
+  f.lam_fac = (float)ph.lam_fac; f.eps = (float)ph.eps; f.dt_visc_k = (float)ph.dt_visc_k;
+  f.visc = ph.visc;
+  return f;
+}
+
+// inputs of the face kernels: FP64 primitives with the H = E + p row, their FP32 split, gradients
+struct MixedIn {
+  const double* W;     // [NW + 1][ncell]
+  const float* hi;     // [NW][ncell]
+  const float* lo;     // [NW][ncell]
+  const float* G32;    // [NG][ncell] (viscous only)
+};
 
 // WENO5 value at i+1/2 relative to an arbitrary offset, from offsets of q_{i-2..i+2}
 template <int SCHEME>
@@ -50,23 +95,23 @@ __device__ __forceinline__ float weno5f(float qm2, float qm1, float q0, float qp
   const float b2 = k1312f * t * t + 0.25f * s * s;
   float a0, a1, a2;
   if (SCHEME == FLUID_WENO_JS) {
-    const float r0 = 1.0f / (eps + b0), r1 = 1.0f / (eps + b1), r2 = 1.0f / (eps + b2);
+    const float r0 = rcpf(eps + b0), r1 = rcpf(eps + b1), r2 = rcpf(eps + b2);
     a0 = 0.1f * r0 * r0; a1 = 0.6f * r1 * r1; a2 = 0.3f * r2 * r2;
   } else {
     const float tau = fabsf(b0 - b2);
-    const float r0 = fminf(tau / (b0 + kZepsF), kZclampF);
-    const float r1 = fminf(tau / (b1 + kZepsF), kZclampF);
-    const float r2 = fminf(tau / (b2 + kZepsF), kZclampF);
+    const float r0 = fminf(tau * rcpf(b0 + kZepsF), kZclampF);
+    const float r1 = fminf(tau * rcpf(b1 + kZepsF), kZclampF);
+    const float r2 = fminf(tau * rcpf(b2 + kZepsF), kZclampF);
     a0 = 0.1f * (1.0f + r0 * r0); a1 = 0.6f * (1.0f + r1 * r1); a2 = 0.3f * (1.0f + r2 * r2);
   }
-  return (a0 * p0 + a1 * p1 + a2 * p2) / (6.0f * (a0 + a1 + a2));
+  return (a0 * p0 + a1 * p1 + a2 * p2) * rcpf(6.0f * (a0 + a1 + a2));
 }
 
-__device__ __forceinline__ float viscosity_f(float T, const Phys& ph) {
-  if (ph.visc == FLUID_VISC_CONSTANT) return (float)ph.mu_ref;
-  const float r = T * (float)ph.iT_ref;
-  if (ph.visc == FLUID_VISC_POWER) return (float)ph.mu_ref * powf(r, (float)ph.visc_exp);
-  return (float)ph.mu_ref * (r * sqrtf(r)) * (float)(ph.T_ref + ph.suth_S) / (T + (float)ph.suth_S);
+__device__ __forceinline__ float viscosity_f(float T, const PhysF& pf) {
+  if (pf.visc == FLUID_VISC_CONSTANT) return pf.mu_ref;
+  const float r = T * pf.iT_ref;
+  if (pf.visc == FLUID_VISC_POWER) return pf.mu_ref * __powf(r, pf.visc_exp);
+  return pf.mu_ref * (r * sqrtf_a(r)) * pf.TS * rcpf(T + pf.S);
 }
 
 // X: change of the face flux relative to F(q_a), in FP32 (see the file comment).
@@ -74,8 +119,8 @@ __device__ __forceinline__ float viscosity_f(float T, const Phys& ph) {
 //   dL, dR   offsets of the reconstructed left and right face states from q_a
 template <int D>
 __device__ __forceinline__ void hllc_delta(const float b[5], const float dL[5], const float dR[5],
-                                           const Phys& ph, float X[5]) {
-  const float g = (float)ph.gamma, gm1 = (float)ph.gm1, igm1 = (float)ph.igm1;
+                                           const PhysF& pf, float X[5]) {
+  const float g = pf.gamma, gm1 = pf.gm1, igm1 = pf.igm1;
   float wl[5], wr[5], J[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -88,28 +133,33 @@ __device__ __forceinline__ void hllc_delta(const float b[5], const float dL[5], 
   const float q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
   const float q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
   const float EL = pL * igm1 + 0.5f * rL * q2L, ER = pR * igm1 + 0.5f * rR * q2R;
-  const float cL = sqrtf(g * pL / rL), cR = sqrtf(g * pR / rR);
-  const float sL = sqrtf(rL), sR = sqrtf(rR);
-  const float is = 1.0f / (sL + sR);
+  const float isL = rsqrtf_a(rL), isR = rsqrtf_a(rR);        // 1/sqrt(rho)
+  const float irL = isL * isL, irR = isR * isR;               // 1/rho
+  const float cL = sqrtf_a(g * pL * irL), cR = sqrtf_a(g * pR * irR);
+  const float sL = rL * isL, sR = rR * isR;                   // sqrt(rho)
+  const float is = rcpf(sL + sR);
   const float ut0 = (sL * wl[1] + sR * wr[1]) * is;
   const float ut1 = (sL * wl[2] + sR * wr[2]) * is;
   const float ut2 = (sL * wl[3] + sR * wr[3]) * is;
-  const float Ht = (sL * (EL + pL) / rL + sR * (ER + pR) / rR) * is;
-  const float ct = sqrtf(gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const float Ht = ((EL + pL) * isL + (ER + pR) * isR) * is;   // sqrt(rho) (E+p)/rho
+  const float ct = sqrtf_a(gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
   const float utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
   const float SL = fminf(unL - cL, utn - ct);
   const float SR = fmaxf(unR + cR, utn + ct);
   const float mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const float den = mL - mR;
+  const float iden = rcpf(mL - mR);
   // S* - u_L and S* - u_R from the jumps: (dp - m_{R|L} du_n) / (m_L - m_R)
-  const float sigL = (J[4] - mR * J[1 + D]) / den;
-  const float sigR = (J[4] - mL * J[1 + D]) / den;
+  const float sigL = (J[4] - mR * J[1 + D]) * iden;
+  const float sigR = (J[4] - mL * J[1 + D]) * iden;
   const float Ss = unL + sigL;
 
   const bool left = (SL >= 0.0f) || (Ss >= 0.0f);
   const bool star = left ? !(SL >= 0.0f) : (SR > 0.0f);
-  const float* d = left ? dL : dR;
-  const float* w = left ? wl : wr;
+  // the upwind side's offsets and state, selected value by value so that both arrays stay
+  // in registers
+  float d[5], w[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { d[v] = left ? dL[v] : dR[v]; w[v] = left ? wl[v] : wr[v]; }
 
   // Euler-flux change from q_a to the face state K = b + d
   const float un = b[1 + D], unK = w[1 + D];
@@ -121,7 +171,7 @@ __device__ __forceinline__ void hllc_delta(const float b[5], const float dL[5], 
   X[1 + D] += d[4];
   const float q2b = b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
   const float dq2 = d[1] * (2.0f * b[1] + d[1]) + d[2] * (2.0f * b[2] + d[2]) + d[3] * (2.0f * b[3] + d[3]);
-  const float gg = g * igm1;
+  const float gg = pf.gg;
   const float Hv = gg * b[4] + 0.5f * b[0] * q2b;         // E + p of q_a
   const float dHv = gg * d[4] + 0.5f * (d[0] * (q2b + dq2) + b[0] * dq2);
   X[4] = d[1 + D] * (Hv + dHv) + un * dHv;
@@ -132,36 +182,36 @@ __device__ __forceinline__ void hllc_delta(const float b[5], const float dL[5], 
     const float sig = left ? sigL : sigR;
     const float rK = w[0], pK = w[4];
     const float EK = left ? EL : ER;
-    const float theta = sig / (S - Ss);
+    const float theta = sig * rcpf(S - Ss);
     const float chi = 1.0f + theta;
     float dU[5];
     dU[0] = rK * theta;
 #pragma unroll
     for (int c = 0; c < 3; ++c) dU[1 + c] = rK * theta * w[1 + c];
     dU[1 + D] = rK * (theta * unK + chi * sig);
-    dU[4] = theta * EK + chi * sig * (rK * Ss + pK / (S - unK));
+    dU[4] = theta * EK + chi * sig * (rK * Ss + pK * rcpf(S - unK));
 #pragma unroll
     for (int v = 0; v < 5; ++v) X[v] += S * dU[v];
   }
 }
 
-// D-window entry: difference of one primitive between consecutive cells, FP64 -> FP32
-__device__ __forceinline__ float diff32(const double* __restrict__ f, int cell, int s) {
-  return (float)(__ldg(f + cell + s) - __ldg(f + cell));
+// D-window entry: difference of one primitive between consecutive cells from its (hi, lo) split
+__device__ __forceinline__ float diff32(const float* __restrict__ hi, const float* __restrict__ lo,
+                                        int cell, int s) {
+  return (__ldg(hi + cell + s) - __ldg(hi + cell)) + (__ldg(lo + cell + s) - __ldg(lo + cell));
 }
 
 // Face flux F_{a+1/2} (FP64) along D.  `cell` is cell a; Dw[v][k] holds D_{a-2+k}, k = 0..4.
 template <int D, int SCHEME, bool VISC>
-__device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, const float* __restrict__ W32,
-                                                const float* __restrict__ G32, int cell, int s, int a,
-                                                const float Dw[6][5], const Geo& g, const Phys& ph,
+__device__ __forceinline__ void face_flux_mixed(const MixedIn& in, int cell, int s, int a,
+                                                const float Dw[6][5], const Geo& g, const PhysF& pf,
                                                 double F[5]) {
   const int nc = g.ncell;
-  const float eps = (float)ph.eps;
+  const float eps = pf.eps;
   float b[5], dL[5], dR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    b[v] = __ldg(W32 + v * nc + cell);
+    b[v] = __ldg(in.hi + v * nc + cell);
     // offsets from q_a of cells a-2 .. a+3
     const float om1 = -Dw[v][1], om2 = -(Dw[v][0] + Dw[v][1]);
     const float op1 = Dw[v][2], op2 = Dw[v][2] + Dw[v][3], op3 = op2 + Dw[v][4];
@@ -169,11 +219,11 @@ __device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, co
     dR[v] = weno5f<SCHEME>(op3, op2, op1, 0.0f, om1, eps);
   }
   float X[5];
-  hllc_delta<D>(b, dL, dR, ph, X);
+  hllc_delta<D>(b, dL, dR, pf, X);
 
   if (VISC) {
     // u, v, w, T at cells a-1..a+2 through the D window (entries 1, 2, 3 = D_{a-1}, D_a, D_{a+1})
-    const float mfa = (float)g.mf[D][a];
+    const float mfa = __ldg(g.mf32[D] + a);
     float vf[3], Gf[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -181,7 +231,7 @@ __device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, co
       vf[c] = b[1 + c] + (8.0f * d1 + d0 - d2) * (1.0f / 16.0f);
       Gf[c][D] = (26.0f * d1 - d0 - d2) * (1.0f / 24.0f) * mfa;
     }
-    const float Tb = __ldg(W32 + 5 * nc + cell);
+    const float Tb = __ldg(in.hi + 5 * nc + cell);
     const float Tf = Tb + (8.0f * Dw[5][2] + Dw[5][1] - Dw[5][3]) * (1.0f / 16.0f);
     const float dT = (26.0f * Dw[5][2] - Dw[5][1] - Dw[5][3]) * (1.0f / 24.0f) * mfa;
     auto interp = [](float fm1, float f0, float f1, float f2) {
@@ -191,8 +241,8 @@ __device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, co
     for (int bb = 0; bb < 3; ++bb) {
       if (bb == D) continue;
       if (bb < g.ndim) {
-        const float* gd = G32 + (D * 3 + bb) * nc + cell;
-        const float* gb = G32 + (bb * 3 + bb) * nc + cell;
+        const float* gd = in.G32 + (D * 3 + bb) * nc + cell;
+        const float* gb = in.G32 + (bb * 3 + bb) * nc + cell;
         Gf[D][bb] = interp(__ldg(gd - s), __ldg(gd), __ldg(gd + s), __ldg(gd + 2 * s));
         Gf[bb][bb] = interp(__ldg(gb - s), __ldg(gb), __ldg(gb + s), __ldg(gb + 2 * s));
       } else {
@@ -201,8 +251,8 @@ __device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, co
       }
     }
     const float div = Gf[0][0] + Gf[1][1] + Gf[2][2];
-    const float mu = viscosity_f(Tf, ph);
-    const float lam = mu * (float)ph.lam_fac;
+    const float mu = viscosity_f(Tf, pf);
+    const float lam = mu * pf.lam_fac;
     float tau[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -216,25 +266,33 @@ __device__ __forceinline__ void face_flux_mixed(const double* __restrict__ W, co
   }
 
   // FP64 cell-centre Euler flux of q_a plus the FP32 change
+  const double* W = in.W;
   const double r = W[cell], u0 = W[nc + cell], u1 = W[2 * nc + cell], u2 = W[3 * nc + cell];
-  const double p = W[4 * nc + cell];
+  const double p = W[4 * nc + cell], H = W[NW * nc + cell];
   const double un = D == 0 ? u0 : (D == 1 ? u1 : u2);
-  const double E = p * ph.igm1 + 0.5 * r * (u0 * u0 + u1 * u1 + u2 * u2);
   const double mn = r * un;
   F[0] = mn + (double)X[0];
-  F[1] = mn * u0 + (double)X[1];
-  F[2] = mn * u1 + (double)X[2];
-  F[3] = mn * u2 + (double)X[3];
+  F[1] = fma(mn, u0, (double)X[1]);
+  F[2] = fma(mn, u1, (double)X[2]);
+  F[3] = fma(mn, u2, (double)X[3]);
   F[1 + D] += p;
-  F[4] = un * (E + p) + (double)X[4];
+  F[4] = fma(un, H, (double)X[4]);
+}
+
+// R_v (+)= -(F_v - Fp_v) / dx in FP64
+__device__ __forceinline__ void divergence(double* __restrict__ R, int nc, int cell, double id,
+                                           const double F[5], const double Fp[5], int accumulate) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double dF = F[v] - Fp[v];
+    double* dst = R + v * nc + cell;
+    *dst = accumulate ? fma(-id, dF, *dst) : -id * dF;
+  }
 }
 
 template <int D, int SCHEME, bool VISC>
-__global__ void __launch_bounds__(128) k_face_mixed(const double* __restrict__ W,
-                                                    const float* __restrict__ W32,
-                                                    const float* __restrict__ G32,
-                                                    double* __restrict__ R, Geo g, Phys ph,
-                                                    int accumulate, int seg) {
+__global__ void __launch_bounds__(128) k_face_mixed(MixedIn in, double* __restrict__ R, Geo g,
+                                                    PhysF pf, int accumulate, int seg) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   constexpr int NVW = VISC ? 6 : 5;          // windowed primitives (T only for the heat flux)
@@ -261,26 +319,21 @@ __global__ void __launch_bounds__(128) k_face_mixed(const double* __restrict__ W
 #pragma unroll
     for (int v = 0; v < NVW; ++v)
 #pragma unroll
-      for (int k = 0; k < 5; ++k) Dw[v][k] = diff32(W + v * nc, cell + (k - 2) * s, s);
+      for (int k = 0; k < 5; ++k) Dw[v][k] = diff32(in.hi + v * nc, in.lo + v * nc, cell + (k - 2) * s, s);
     double Fp[5], F[5];
-    face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, cell, s, a0 - 1, Dw, g, ph, Fp);
+    face_flux_mixed<D, SCHEME, VISC>(in, cell, s, a0 - 1, Dw, g, pf, Fp);
     for (int a = a0; a < a1; ++a) {
       cell += s;
 #pragma unroll
       for (int v = 0; v < NVW; ++v) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) Dw[v][k] = Dw[v][k + 1];
-        Dw[v][4] = diff32(W + v * nc, cell + 2 * s, s);
+        Dw[v][4] = diff32(in.hi + v * nc, in.lo + v * nc, cell + 2 * s, s);
       }
-      face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, cell, s, a, Dw, g, ph, F);
-      const double id = g.idx[D][a];
+      face_flux_mixed<D, SCHEME, VISC>(in, cell, s, a, Dw, g, pf, F);
+      divergence(R, nc, cell, g.idx[D][a], F, Fp, accumulate);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const double val = -(F[v] - Fp[v]) * id;
-        double* dst = R + v * nc + cell;
-        *dst = accumulate ? *dst + val : val;
-        Fp[v] = F[v];
-      }
+      for (int v = 0; v < 5; ++v) Fp[v] = F[v];
     }
   }
 }
@@ -293,11 +346,8 @@ constexpr int kXCells = 31;
 constexpr int kXRows = 4;
 
 template <int SCHEME, bool VISC>
-__global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(const double* __restrict__ W,
-                                                              const float* __restrict__ W32,
-                                                              const float* __restrict__ G32,
-                                                              double* __restrict__ R, Geo g,
-                                                              Phys ph, int accumulate) {
+__global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(MixedIn in, double* __restrict__ R,
+                                                              Geo g, PhysF pf, int accumulate) {
   constexpr int NVW = VISC ? 6 : 5;
   constexpr int ND = kXCells + 5;               // D_j for j in [x0-3, x0+kXCells+1]
   __shared__ float sD[kXRows][6][ND];
@@ -316,7 +366,8 @@ __global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(const double* __re
       const int j = x0 - 3 + k;
       const bool ok = j + 1 <= xend + 2;         // W index j + 1 stays inside the padded row
 #pragma unroll
-      for (int v = 0; v < NVW; ++v) sD[row][v][k] = ok ? diff32(W + v * nc, rowbase + j, 1) : 0.0f;
+      for (int v = 0; v < NVW; ++v)
+        sD[row][v][k] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, rowbase + j, 1) : 0.0f;
     }
   }
   __syncthreads();
@@ -328,45 +379,46 @@ __global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(const double* __re
 #pragma unroll
       for (int k = 0; k < 5; ++k) Dw[v][k] = sD[row][v][lane + k];
     double F[5];
-    face_flux_mixed<0, SCHEME, VISC>(W, W32, G32, rowbase + a, 1, a, Dw, g, ph, F);
+    face_flux_mixed<0, SCHEME, VISC>(in, rowbase + a, 1, a, Dw, g, pf, F);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sF[row][v][lane] = F[v];
   }
   __syncthreads();
   const int cx = x0 + lane;                      // cell of the divergence
   if (live && lane < kXCells && cx < xend) {
-    const double id = g.idx[0][cx];
-    const int cell = rowbase + cx;
+    double F[5], Fp[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const double val = -(sF[row][v][lane + 1] - sF[row][v][lane]) * id;
-      double* dst = R + v * nc + cell;
-      *dst = accumulate ? *dst + val : val;
-    }
+    for (int v = 0; v < 5; ++v) { F[v] = sF[row][v][lane + 1]; Fp[v] = sF[row][v][lane]; }
+    divergence(R, nc, rowbase + cx, g.idx[0][cx], F, Fp, accumulate);
   }
 }
 
-// y / z variant: lanes map to 32 consecutive x columns (coalesced loads); a block covers 31 cells
-// along the face axis D (32 faces) of those columns at one index of the remaining axis.  The cell
-// differences along D and the face fluxes are staged in shared memory; each of the 8 warps takes
-// every 8th face and every 8th cell of the tile.
-constexpr int kTCells = 31;
-constexpr int kTWarps = 8;
+// y / z variant: lanes map to 32 consecutive x columns (coalesced loads); a block of NWARP warps
+// covers 4 NWARP - 1 cells along the face axis D (4 NWARP faces) of those columns at one index of
+// the remaining axis.  The cell differences along D are staged in shared memory; warp w computes
+// the four consecutive faces 4w .. 4w+3, keeps the previous face flux in registers for the
+// divergence of the cells between them and takes the flux of face 4w+4 from the next warp
+// through shared memory.  Registers are capped at 64 so that 32 / NWARP blocks (32 warps) fit an SM.
+constexpr int kTFaces = 4;                                   // faces per warp
 
-template <int D, int SCHEME, bool VISC>
-__global__ void __launch_bounds__(32 * kTWarps) k_face_mixed_t(const double* __restrict__ W,
-                                                               const float* __restrict__ W32,
-                                                               const float* __restrict__ G32,
-                                                               double* __restrict__ R, Geo g,
-                                                               Phys ph, int accumulate) {
+template <int NWARP>
+constexpr size_t t_smem() {
+  return sizeof(float) * 6 * (kTFaces * NWARP + 4) * 32 + sizeof(double) * NWARP * 5 * 32;
+}
+
+template <int D, int SCHEME, bool VISC, int NWARP>
+__global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn in, double* __restrict__ R,
+                                                                       Geo g, PhysF pf, int accumulate) {
   static_assert(D == 1 || D == 2, "tiles along y or z");
+  constexpr int kTCells = kTFaces * NWARP - 1;
+  constexpr int kTWarps = NWARP;
   constexpr int NVW = VISC ? 6 : 5;
   constexpr int ND = kTCells + 5;
   constexpr int OTHER = D == 1 ? 2 : 1;                     // the axis that is neither x nor D
   extern __shared__ unsigned char smem_raw[];
   float (*sD)[ND][32] = reinterpret_cast<float (*)[ND][32]>(smem_raw);                  // [6][ND][32]
-  double (*sF)[kTCells + 1][32] =
-      reinterpret_cast<double (*)[kTCells + 1][32]>(smem_raw + sizeof(float) * 6 * ND * 32);  // [5][32][32]
+  double (*sF)[5][32] =
+      reinterpret_cast<double (*)[5][32]>(smem_raw + sizeof(float) * 6 * ND * 32);      // [NWARP][5][32]
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int x = g.h[0] + blockIdx.x * 32 + lane;
   const bool xok = x < g.h[0] + g.n[0];
@@ -381,38 +433,42 @@ __global__ void __launch_bounds__(32 * kTWarps) k_face_mixed_t(const double* __r
     const int j = d0 - 3 + k;
     const bool ok = xok && j + 1 <= dend + 2;
 #pragma unroll
-    for (int v = 0; v < NVW; ++v) sD[v][k][lane] = ok ? diff32(W + v * nc, colbase + j * s, s) : 0.0f;
+    for (int v = 0; v < NVW; ++v)
+      sD[v][k][lane] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, colbase + j * s, s) : 0.0f;
   }
   __syncthreads();
-  for (int f = warp; f <= kTCells; f += kTWarps) {          // face a + 1/2, a = d0 - 1 + f
+  const int f0 = warp * kTFaces;                            // face a + 1/2, a = d0 - 1 + f
+  double Fp[5];
+  for (int f = f0; f < f0 + kTFaces; ++f) {
     const int a = d0 - 1 + f;
-    if (!xok || a >= dend) continue;
+    if (!xok || a >= dend) break;
     float Dw[6][5];
 #pragma unroll
     for (int v = 0; v < NVW; ++v)
 #pragma unroll
       for (int kk = 0; kk < 5; ++kk) Dw[v][kk] = sD[v][f + kk][lane];
     double F[5];
-    face_flux_mixed<D, SCHEME, VISC>(W, W32, G32, colbase + a * s, s, a, Dw, g, ph, F);
+    face_flux_mixed<D, SCHEME, VISC>(in, colbase + a * s, s, a, Dw, g, pf, F);
+    if (f == f0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sF[v][f][lane] = F[v];
+      for (int v = 0; v < 5; ++v) sF[warp][v][lane] = F[v];
+    } else {
+      divergence(R, nc, colbase + a * s, g.idx[D][a], F, Fp, accumulate);   // cell a, faces a -+ 1/2
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fp[v] = F[v];
   }
   __syncthreads();
-  for (int cc = warp; cc < kTCells; cc += kTWarps) {
-    const int a = d0 + cc;
-    if (!xok || a >= dend) continue;
-    const double id = g.idx[D][a];
-    const int cell = colbase + a * s;
+  // the last cell of this warp's run, d0 - 1 + f0 + kTFaces: right face from the next warp
+  const int a = d0 + f0 + kTFaces - 1;
+  if (warp + 1 < kTWarps && xok && a < dend) {
+    double F[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const double val = -(sF[v][cc + 1][lane] - sF[v][cc][lane]) * id;
-      double* dst = R + v * nc + cell;
-      *dst = accumulate ? *dst + val : val;
-    }
+    for (int v = 0; v < 5; ++v) F[v] = sF[warp + 1][v][lane];
+    divergence(R, nc, colbase + a * s, g.idx[D][a], F, Fp, accumulate);
   }
 }
 
-constexpr size_t kTSmem = sizeof(float) * 6 * (kTCells + 5) * 32 + sizeof(double) * 5 * (kTCells + 1) * 32;
 
 // centre velocity gradients in FP32 from the FP32 primitives (fourth-order central)
 __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
@@ -449,12 +505,12 @@ __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32,
 constexpr int kDtBlock = 256;
 
 // CFL partial minima from the FP32 primitives (the time step needs no more than FP32 accuracy)
-__global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, Phys ph,
+__global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, PhysF pf,
                                                            double* __restrict__ partial) {
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
   float best = __int_as_float(0x7f800000);
-  const float gam = (float)ph.gamma, k = (float)ph.dt_visc_k;
+  const float gam = pf.gamma, k = pf.dt_visc_k;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int i = t % g.n[0];
     const int r = t / g.n[0];
@@ -465,11 +521,11 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restri
     const float rho = W32[c], p = W32[4 * nc + c];
     const float cs = sqrtf(gam * p / rho);
     float nu = 0.0f;
-    if (ph.visc != FLUID_VISC_NONE) nu = viscosity_f(W32[5 * nc + c], ph) / rho;
+    if (pf.visc != FLUID_VISC_NONE) nu = viscosity_f(W32[5 * nc + c], pf) / rho;
     for (int d = 0; d < g.ndim; ++d) {
       const float dx = (float)g.dx[d][ci[d]];
       best = fminf(best, dx / (fabsf(W32[(1 + d) * nc + c]) + cs));
-      if (ph.visc != FLUID_VISC_NONE) best = fminf(best, dx * dx / (k * nu));
+      if (pf.visc != FLUID_VISC_NONE) best = fminf(best, dx * dx / (k * nu));
     }
   }
   __shared__ float sm[kDtBlock / 32];
@@ -484,8 +540,8 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restri
 }
 
 template <int D, int SCHEME, bool VISC>
-cudaError_t launch_t(const double* W, const float* W32, const float* G32, double* R, const Geo& g,
-                     const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+cudaError_t launch_t(const MixedIn& in, double* R, const Geo& g, const PhysF& pf, int accumulate,
+                     int block, int seg, cudaStream_t st) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const long long lines = (long long)g.n[A1] * g.n[A2];
@@ -495,41 +551,50 @@ cudaError_t launch_t(const double* W, const float* W32, const float* G32, double
     while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
   }
   const long long total = lines * ((g.n[D] + seg - 1) / seg);
-  k_face_mixed<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(W, W32, G32, R, g, ph,
-                                                                           accumulate, seg);
+  k_face_mixed<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(in, R, g, pf, accumulate, seg);
+  return cudaGetLastError();
+}
+
+template <int SCHEME, bool VISC, int NWARP>
+cudaError_t launch_tile(int D, const MixedIn& in, double* R, const Geo& g, const PhysF& pf,
+                        int accumulate, cudaStream_t st) {
+  constexpr int cells = kTFaces * NWARP - 1;
+  constexpr size_t smem = t_smem<NWARP>();
+  const int other = D == 1 ? 2 : 1;
+  const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + cells - 1) / cells, g.n[other]);
+  // a tile may need more than the default 48 KB of dynamic shared memory (attribute is per device)
+  if (D == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC, NWARP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_face_mixed_t<1, SCHEME, VISC, NWARP><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC, NWARP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_face_mixed_t<2, SCHEME, VISC, NWARP><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+  }
   return cudaGetLastError();
 }
 
 template <int SCHEME, bool VISC>
-cudaError_t launch_sv(int D, const double* W, const float* W32, const float* G32, double* R,
-                      const Geo& g, const Phys& ph, int accumulate, int block, int seg,
-                      cudaStream_t st) {
+cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const PhysF& pf,
+                      int accumulate, int block, int seg, cudaStream_t st) {
   if (D == 0) {
     const long long lines = (long long)g.n[1] * g.n[2];
     const dim3 grid((g.n[0] + kXCells - 1) / kXCells, (unsigned)((lines + kXRows - 1) / kXRows));
-    k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(W, W32, G32, R, g, ph, accumulate);
+    k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(in, R, g, pf, accumulate);
     return cudaGetLastError();
   }
   const int other = D == 1 ? 2 : 1;
   if (seg < 0 || g.n[other] > 65535) {   // register-window marching kernels
     const int sg = seg < 0 ? -seg : 0;
-    if (D == 1) return launch_t<1, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, sg, st);
-    return launch_t<2, SCHEME, VISC>(W, W32, G32, R, g, ph, accumulate, block, sg, st);
+    if (D == 1) return launch_t<1, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
+    return launch_t<2, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
   }
-  const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + kTCells - 1) / kTCells, g.n[other]);
-  // the tile needs more than the default 48 KB of dynamic shared memory (attribute is per device)
-  if (D == 1) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
-    if (e != cudaSuccess) return e;
-    k_face_mixed_t<1, SCHEME, VISC><<<grid, dim3(32, kTWarps), kTSmem, st>>>(W, W32, G32, R, g, ph, accumulate);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
-    if (e != cudaSuccess) return e;
-    k_face_mixed_t<2, SCHEME, VISC><<<grid, dim3(32, kTWarps), kTSmem, st>>>(W, W32, G32, R, g, ph, accumulate);
-  }
-  return cudaGetLastError();
+  // warps per tile: block 64 -> 2, otherwise 4
+  if (block == 64) return launch_tile<SCHEME, VISC, 2>(D, in, R, g, pf, accumulate, st);
+  return launch_tile<SCHEME, VISC, 4>(D, in, R, g, pf, accumulate, st);
 }
 
 }  // namespace
@@ -538,11 +603,13 @@ cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const fl
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,
                               cudaStream_t st) {
   const bool visc = ph.visc != FLUID_VISC_NONE;
+  const MixedIn in{W, W32, W32 + (size_t)NW * g.ncell, G32};
+  const PhysF pf = phys_f(ph);
   if (ph.weno == FLUID_WENO_JS)
-    return visc ? launch_sv<FLUID_WENO_JS, true>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st)
-                : launch_sv<FLUID_WENO_JS, false>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st);
-  return visc ? launch_sv<FLUID_WENO_Z, true>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st)
-              : launch_sv<FLUID_WENO_Z, false>(D, W, W32, G32, R, g, ph, accumulate, block, seg, st);
+    return visc ? launch_sv<FLUID_WENO_JS, true>(D, in, R, g, pf, accumulate, block, seg, st)
+                : launch_sv<FLUID_WENO_JS, false>(D, in, R, g, pf, accumulate, block, seg, st);
+  return visc ? launch_sv<FLUID_WENO_Z, true>(D, in, R, g, pf, accumulate, block, seg, st)
+              : launch_sv<FLUID_WENO_Z, false>(D, in, R, g, pf, accumulate, block, seg, st);
 }
 
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st) {
@@ -554,7 +621,7 @@ cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream
 
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
                                 int nparts, cudaStream_t st) {
-  k_dt_partial32<<<nparts, kDtBlock, 0, st>>>(W32, g, ph, partial);
+  k_dt_partial32<<<nparts, kDtBlock, 0, st>>>(W32, g, phys_f(ph), partial);
   return cudaGetLastError();
 }
 

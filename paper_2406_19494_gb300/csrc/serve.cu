@@ -72,7 +72,8 @@ size_t footprint(const fluid_config& c) {
   }
   const bool visc = c.visc_law != FLUID_VISC_NONE;
   size_t b = 8 * (nc * (fl::NW + 3 * fl::NV) + metric + 4096);   // W, A, R, the state U, metrics
-  if (c.precision == FLUID_PREC_MIXED) b += 4 * nc * (fl::NW + (visc ? fl::NG : 0));
+  // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients and face metrics
+  if (c.precision == FLUID_PREC_MIXED) b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
   else if (visc) b += 8 * nc * fl::NG;
   return b;
 }
@@ -128,7 +129,7 @@ struct fluid_server {
     auto it = tuned.find(key);
     if (it == tuned.end()) {
       std::vector<std::pair<int, int>> cand = {{0, 0}, {32, 64}, {64, 16}, {128, 32}};
-      if (c.precision == FLUID_PREC_MIXED) cand = {{0, 0}, {128, -16}, {128, -32}};
+      if (c.precision == FLUID_PREC_MIXED) cand = {{0, 0}, {64, 0}, {128, -32}};
       double* tmp = nullptr;
       float best = 1e30f;
       std::pair<int, int> pick{0, 0};
