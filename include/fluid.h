@@ -251,6 +251,12 @@ int fluid_measure_peak(int kind, double* gflops, void* stream);
  * device values.  For tests. */
 int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n, void* stream);
 
+/* Accuracy check of the reciprocal square root and square root the kernels use (a third-order
+ * step from the hardware estimate): rsqrt[i] and sqrt[i] of y[i] as the kernels compute them,
+ * ieee[i] = CUDA's correctly rounded sqrt(y[i]), for n device values.  For tests. */
+int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev, double* ieee_dev,
+                     int n, void* stream);
+
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as
  * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is
  * owned by its own pool or arena and which forbids allocations behind its back, or a

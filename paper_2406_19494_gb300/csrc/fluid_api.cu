@@ -32,7 +32,7 @@ struct fluid_solver {
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
   double* R = nullptr;             // right-hand side accumulator, NV * ncell
-  double* partial = nullptr;       // dt partial minima
+  double* partial = nullptr;       // dt: per-block maxima of the CFL rates
   int nparts = 0;
   Ctl* ctl = nullptr;
   double* vw = nullptr;            // porous transpiration velocities

@@ -375,11 +375,14 @@ __global__ void k_stage(int stage, const double* Un, const double* Us, const dou
 
 constexpr int kDtBlock = 256;
 
+// CFL: dt = cfl * min over cells and axes of dx / (|u| + c) and dx^2 / (k nu), taken as
+// cfl / max of the rates (|u| + c) / dx and k nu / dx^2 so that a cell costs no division.
+// Per-block maxima of the rate go to `partial`.
 __global__ void __launch_bounds__(kDtBlock) k_dt_partial(const double* __restrict__ W, Geo g, Phys ph,
                                                          double* __restrict__ partial) {
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
-  double best = __longlong_as_double(0x7ff0000000000000LL);   // +inf
+  double best = 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int i = t % g.n[0];
     const int r = t / g.n[0];
@@ -388,41 +391,41 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial(const double* __restric
     const int ci[3] = {i + g.h[0], j + g.h[1], k + g.h[2]};
     const int c = ci[0] + ci[1] * g.sy + ci[2] * g.sz;
     const double rho = W[c], p = W[4 * nc + c];
-    const double cs = sqrt(ph.gamma * p / rho);
-    double nu = 0.0;
-    if (ph.visc != FLUID_VISC_NONE) nu = viscosity(W[5 * nc + c], ph) / rho;
+    const double irho = fl_rcp(rho);
+    const double cs = fl_sqrt(ph.gamma * p * irho);
+    double knu = 0.0;
+    if (ph.visc != FLUID_VISC_NONE) knu = ph.dt_visc_k * viscosity(W[5 * nc + c], ph) * irho;
     for (int d = 0; d < g.ndim; ++d) {
-      const double dx = g.dx[d][ci[d]];
-      best = fmin(best, dx / (fabs(W[(1 + d) * nc + c]) + cs));
-      if (ph.visc != FLUID_VISC_NONE) best = fmin(best, dx * dx / (ph.dt_visc_k * nu));
+      const double id = g.idx[d][ci[d]];
+      best = fmax(best, (fabs(W[(1 + d) * nc + c]) + cs) * id);
+      if (ph.visc != FLUID_VISC_NONE) best = fmax(best, knu * id * id);
     }
   }
   __shared__ double sm[kDtBlock / 32];
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x < 32) {
-    best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
-    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+    best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
     if (threadIdx.x == 0) partial[blockIdx.x] = best;
   }
 }
 
-// dt = cfl * min(partials) (or dt_fixed); clip_to_ctl: clip so that t does not pass t_end and store
-// in ctl->dt; otherwise write *dt_out.
+// dt = cfl / max(partial rates) (or dt_fixed); clip_to_ctl: clip so that t does not pass t_end and
+// store in ctl->dt; otherwise write *dt_out.
 __global__ void __launch_bounds__(kDtBlock) k_dt_final(const double* __restrict__ partial, int nparts,
                                                        Phys ph, Ctl* ctl, double* dt_out, int clip,
                                                        double t_end) {
-  double best = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) best = fmin(best, partial[i]);
+  double best = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) best = fmax(best, partial[i]);
   __shared__ double sm[kDtBlock / 32];
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < kDtBlock / 32; ++i) best = fmin(best, sm[i]);
-    sm[0] = best;
-    double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl * sm[0];
+    for (int i = 1; i < kDtBlock / 32; ++i) best = fmax(best, sm[i]);
+    double dt = ph.dt_fixed > 0.0 ? ph.dt_fixed : ph.cfl / best;
     if (!clip) {
       *dt_out = dt;
       return;

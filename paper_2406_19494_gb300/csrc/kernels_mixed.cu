@@ -504,12 +504,13 @@ __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32,
 
 constexpr int kDtBlock = 256;
 
-// CFL partial minima from the FP32 primitives (the time step needs no more than FP32 accuracy)
+// CFL partial maxima of the rates (|u| + c) / dx and k nu / dx^2 (the inverse time steps, as in
+// the FP64 kernel) from the FP32 primitives: the time step needs no more than FP32 accuracy
 __global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, PhysF pf,
                                                            double* __restrict__ partial) {
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
-  float best = __int_as_float(0x7f800000);
+  float best = 0.0f;
   const float gam = pf.gamma, k = pf.dt_visc_k;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int i = t % g.n[0];
@@ -519,22 +520,23 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restri
     const int ci[3] = {i + g.h[0], j + g.h[1], kk + g.h[2]};
     const int c = ci[0] + ci[1] * g.sy + ci[2] * g.sz;
     const float rho = W32[c], p = W32[4 * nc + c];
-    const float cs = sqrtf(gam * p / rho);
-    float nu = 0.0f;
-    if (pf.visc != FLUID_VISC_NONE) nu = viscosity_f(W32[5 * nc + c], pf) / rho;
+    const float irho = rcpf(rho);
+    const float cs = sqrtf_a(gam * p * irho);
+    float knu = 0.0f;
+    if (pf.visc != FLUID_VISC_NONE) knu = k * viscosity_f(W32[5 * nc + c], pf) * irho;
     for (int d = 0; d < g.ndim; ++d) {
-      const float dx = (float)g.dx[d][ci[d]];
-      best = fminf(best, dx / (fabsf(W32[(1 + d) * nc + c]) + cs));
-      if (pf.visc != FLUID_VISC_NONE) best = fminf(best, dx * dx / (k * nu));
+      const float id = (float)g.idx[d][ci[d]];
+      best = fmaxf(best, (fabsf(W32[(1 + d) * nc + c]) + cs) * id);
+      if (pf.visc != FLUID_VISC_NONE) best = fmaxf(best, knu * id * id);
     }
   }
   __shared__ float sm[kDtBlock / 32];
-  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_down_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x < 32) {
-    best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : __int_as_float(0x7f800000);
-    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_down_sync(0xffffffffu, best, o));
+    best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
     if (threadIdx.x == 0) partial[blockIdx.x] = (double)best;
   }
 }

@@ -62,7 +62,24 @@ __global__ void k_check_rcp(const double* __restrict__ y, double* __restrict__ f
     ieee[i] = 1.0 / y[i];
   }
 }
+__global__ void k_check_sqrt(const double* __restrict__ y, double* __restrict__ rs,
+                             double* __restrict__ sq, double* __restrict__ ieee, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    rs[i] = fl::fl_rsqrt(y[i]);
+    sq[i] = fl::fl_sqrt(y[i]);
+    ieee[i] = sqrt(y[i]);
+  }
+}
 }  // namespace
+
+extern "C" int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev,
+                                double* ieee_dev, int n, void* stream) {
+  if (!y_dev || !rsqrt_dev || !sqrt_dev || !ieee_dev || n < 0) return FLUID_EINVAL;
+  if (n == 0) return FLUID_OK;
+  k_check_sqrt<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0,
+                 reinterpret_cast<cudaStream_t>(stream)>>>(y_dev, rsqrt_dev, sqrt_dev, ieee_dev, n);
+  return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
+}
 
 extern "C" int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n,
                                void* stream) {
