@@ -8,8 +8,9 @@ What it computes (paper sections in brackets):
 * ideal gas p = (gamma - 1) (E - rho |u|^2 / 2), T = p / (rho R)                        [Sec. 2.1, 3.2]
 * convective face fluxes F^c, G^c, H^c by WENO5 reconstruction of the primitive variables
   (rho, u, v, w, p) and the HLLC approximate Riemann solver                            [Sec. 2.1, 3.1]
+  or, as in the channel computation, TENO6-A with the interpolation limiter (oracle/teno.py)  [Sec. 3.1]
 * dissipative face fluxes F^d, G^d, H^d: Newtonian stress with the Stokes hypothesis and
-  Fourier heat flux, from fourth-order central differences                             [Sec. 2.1, Eq. tau]
+  Fourier heat flux, from fourth- or sixth-order central differences                   [Sec. 2.1, Eq. tau, Sec. 3.1]
 * the semi-discrete update R = dU/dt of Eq. ODE, with a body-force source               [Eq. ODE, Eq. NSE]
 * halo cells assigned by boundary conditions: periodic, zero-gradient, no-slip walls
   (isothermal, adiabatic), the "Disturbance Wall" transpiration wall, Dirichlet inflow  [Sec. 3.2]
@@ -30,6 +31,8 @@ All functions are generic over the scalar dtype: with complex128 inputs every no
 import math
 
 import numpy as np
+
+from . import teno
 
 H = 3                       # halo width
 NVAR = 5
@@ -66,7 +69,8 @@ class Case:
     Keys: ndim, n (3-tuple of interior cells), lo, hi (domain), stretch ('uniform' | 'tanh2' |
     'tanh1'), beta, bc (per axis a pair of kinds from BC_KINDS), t_wall (per axis a pair),
     gamma, R, Pr, visc ('none' | 'constant' | 'power' | 'sutherland'), mu_ref, T_ref, visc_exp,
-    suth_S, weno ('js' | 'z'), weno_eps (None = textbook default), body_force, cfl, dt_fixed,
+    suth_S, weno ('js' | 'z' | 'teno6a'), weno_eps (None = textbook default), visc_order (4 | 6),
+    body_force, cfl, dt_fixed,
     porous (dict: axis, side, begin, count, A, kappa, phi0) or None.
     """
 
@@ -91,6 +95,13 @@ class Case:
         eps = d.get("weno_eps", None)
         # Jiang & Shu use eps = 1e-6; Borges et al. use a tiny eps (1e-40) so that it never masks beta
         self.weno_eps = float(eps) if eps is not None else (1e-6 if self.weno == "js" else 1e-40)
+        if self.weno not in ("js", "z", "teno6a", "linear"):
+            raise ValueError("unknown reconstruction %r" % (self.weno,))
+        # order of the central differences of the dissipative fluxes: 4 (default), or 6 as in the
+        # paper's channel computation (Sec. 3.1)
+        self.visc_order = int(d.get("visc_order", 4))
+        if self.visc_order not in (4, 6):
+            raise ValueError("visc_order must be 4 or 6")
         self.body_force = tuple(float(v) for v in d.get("body_force", (0.0, 0.0, 0.0)))
         self.cfl = float(d.get("cfl", 0.5))
         self.dt_fixed = float(d.get("dt_fixed", 0.0))
@@ -443,38 +454,54 @@ def hllc_flux(WL, WR, d, gamma):
 # --------------------------------------------------------------------------------------------
 # dissipative fluxes (Sec. 2.1: F^d, G^d, H^d; Newtonian stress, Fourier heat flux)
 # --------------------------------------------------------------------------------------------
-def _centre_derivative(f, a, grid):
-    """Fourth-order central derivative along axis a at every cell centre that has two neighbours on
-    both sides; other cells are left zero (they are never used)."""
+def _centre_derivative(f, a, grid, order=4):
+    """Central derivative along axis a at every cell centre that has order/2 neighbours on both
+    sides; other cells are left zero (they are never used).
+      order 4: ((f_{j-2} - f_{j+2}) + 8 (f_{j+1} - f_{j-1})) / 12 * (d index/dx)_j
+      order 6: (45 (f_{j+1} - f_{j-1}) - 9 (f_{j+2} - f_{j-2}) + (f_{j+3} - f_{j-3})) / 60 * (d index/dx)_j
+    """
     out = np.zeros_like(f)
     pa = f.shape[2 - a]
-    if pa < 5:
+    r = order // 2
+    if pa < 2 * r + 1:
         return out
-    s = lambda o: _sl(a, 2 + o, pa - 2 + o)
-    out[s(0)] = ((f[s(-2)] - f[s(2)]) + 8.0 * (f[s(1)] - f[s(-1)])) / 12.0 * grid.along("mc", a)[s(0)]
+    s = lambda o: _sl(a, r + o, pa - r + o)
+    mc = grid.along("mc", a)[s(0)]
+    if order == 4:
+        out[s(0)] = ((f[s(-2)] - f[s(2)]) + 8.0 * (f[s(1)] - f[s(-1)])) / 12.0 * mc
+    else:
+        out[s(0)] = (45.0 * (f[s(1)] - f[s(-1)]) - 9.0 * (f[s(2)] - f[s(-2)])
+                     + (f[s(3)] - f[s(-3)])) / 60.0 * mc
     return out
 
 
 def viscous_face_flux(W, T, case, grid, d):
     """F^d at every face a+1/2, a = h-1 .. h+n-1, along axis d, over all tangential cells.
 
-    Reading (the paper uses "central finite-differences", Sec. 2.1; sixth order in Sec. 3.1; this
-    build uses fourth order):
-      normal derivative   ((f_{a-1} - f_{a+2}) + 27 (f_{a+1} - f_a)) / 24 * (d index/dx)_{a+1/2}
-      face interpolation  (9 (f_a + f_{a+1}) - (f_{a-1} + f_{a+2})) / 16
-      tangential derivative: fourth-order central derivative at the four cell centres a-1..a+2,
-      then face-interpolated.  mu = mu(T_face), lambda = mu c_p / Pr.
+    Reading (the paper uses "central finite-differences", Sec. 2.1, of sixth order in the channel
+    computation, Sec. 3.1): case.visc_order 4 or 6,
+      order 4: normal derivative ((f_{a-1} - f_{a+2}) + 27 (f_{a+1} - f_a)) / 24 * (d index/dx)_{a+1/2}
+               face interpolation (9 (f_a + f_{a+1}) - (f_{a-1} + f_{a+2})) / 16
+      order 6: normal derivative (2250 (f_{a+1} - f_a) - 125 (f_{a+2} - f_{a-1})
+                                  + 9 (f_{a+3} - f_{a-2})) / 1920 * (d index/dx)_{a+1/2}
+               face interpolation (150 (f_a + f_{a+1}) - 25 (f_{a-1} + f_{a+2}) + 3 (f_{a-2} + f_{a+3})) / 256
+      tangential derivative: central derivative of the same order at the cell centres of the
+      stencil, then face-interpolated.  mu = mu(T_face), lambda = mu c_p / Pr.
     Returns the five components (mass component zero) on faces a = h-1 .. h+n-1 (n+1 faces).
     """
     n, h = case.n[d], case.h[d]
     a0, a1 = h - 1, h + n                          # faces a+1/2 for a in [a0, a1)
-    f_m1 = lambda f: f[_sl(d, a0 - 1, a1 - 1)]
-    f_0 = lambda f: f[_sl(d, a0, a1)]
-    f_p1 = lambda f: f[_sl(d, a0 + 1, a1 + 1)]
-    f_p2 = lambda f: f[_sl(d, a0 + 2, a1 + 2)]
-    interp = lambda f: (9.0 * (f_0(f) + f_p1(f)) - (f_m1(f) + f_p2(f))) / 16.0
+    at = lambda f, o: f[_sl(d, a0 + o, a1 + o)]
     mf = grid.along("mf", d)[_sl(d, a0, a1)]
-    dn = lambda f: ((f_m1(f) - f_p2(f)) + 27.0 * (f_p1(f) - f_0(f))) / 24.0 * mf
+    order = case.visc_order
+    if order == 4:
+        interp = lambda f: (9.0 * (at(f, 0) + at(f, 1)) - (at(f, -1) + at(f, 2))) / 16.0
+        dn = lambda f: ((at(f, -1) - at(f, 2)) + 27.0 * (at(f, 1) - at(f, 0))) / 24.0 * mf
+    else:
+        interp = lambda f: (150.0 * (at(f, 0) + at(f, 1)) - 25.0 * (at(f, -1) + at(f, 2))
+                            + 3.0 * (at(f, -2) + at(f, 3))) / 256.0
+        dn = lambda f: (2250.0 * (at(f, 1) - at(f, 0)) - 125.0 * (at(f, 2) - at(f, -1))
+                        + 9.0 * (at(f, 3) - at(f, -2))) / 1920.0 * mf
 
     vel = [W[1], W[2], W[3]]
     vf = [interp(vel[c]) for c in range(3)]
@@ -487,8 +514,8 @@ def viscous_face_flux(W, T, case, grid, d):
     for b in range(case.ndim):
         if b == d:
             continue
-        G[d][b] = interp(_centre_derivative(vel[d], b, grid))     # d u_d / d x_b
-        G[b][b] = interp(_centre_derivative(vel[b], b, grid))     # d u_b / d x_b
+        G[d][b] = interp(_centre_derivative(vel[d], b, grid, order))     # d u_d / d x_b
+        G[b][b] = interp(_centre_derivative(vel[b], b, grid, order))     # d u_b / d x_b
     div = G[0][0] + G[1][1] + G[2][2]
     mu = viscosity(Tf, case)
     lam = mu * case.cp / case.Pr
@@ -506,16 +533,24 @@ def viscous_face_flux(W, T, case, grid, d):
 # right-hand side (Eq. ODE)
 # --------------------------------------------------------------------------------------------
 def convective_face_flux(W, case, d):
-    """WENO5 + HLLC flux at faces a+1/2, a = h-1 .. h+n-1, along axis d, over all tangential cells.
-    Reconstruction is component-wise on the primitive variables (reading; the paper is silent)."""
+    """WENO5 (or TENO6-A) + HLLC flux at faces a+1/2, a = h-1 .. h+n-1, along axis d, over all
+    tangential cells.  Reconstruction is component-wise on the primitive variables (reading; the
+    paper is silent).  The right state at a+1/2 is the left-biased value of the mirrored stencil."""
     n, h = case.n[d], case.h[d]
     a0, a1 = h - 1, h + n
     sh = lambda o: _sl(d, a0 + o, a1 + o)
     WL, WR = [], []
     for c in range(NVAR):
         q = W[c]
-        WL.append(weno5(q[sh(-2)], q[sh(-1)], q[sh(0)], q[sh(1)], q[sh(2)], case.weno, case.weno_eps))
-        WR.append(weno5(q[sh(3)], q[sh(2)], q[sh(1)], q[sh(0)], q[sh(-1)], case.weno, case.weno_eps))
+        if case.weno == "teno6a":
+            WL.append(teno.teno6a([q[sh(o)] for o in (-2, -1, 0, 1, 2, 3)]))
+            WR.append(teno.teno6a([q[sh(o)] for o in (3, 2, 1, 0, -1, -2)]))
+        else:
+            WL.append(weno5(q[sh(-2)], q[sh(-1)], q[sh(0)], q[sh(1)], q[sh(2)], case.weno, case.weno_eps))
+            WR.append(weno5(q[sh(3)], q[sh(2)], q[sh(1)], q[sh(0)], q[sh(-1)], case.weno, case.weno_eps))
+    if case.weno == "teno6a":
+        WL, WR = teno.limit_states(WL, WR, [W[c][sh(0)] for c in range(NVAR)],
+                                   [W[c][sh(1)] for c in range(NVAR)])
     return hllc_flux(WL, WR, d, case.gamma)
 
 
