@@ -66,7 +66,9 @@ enum {
   FLUID_STRETCH_TANH1 = 2     /* x = lo + (hi-lo) (1 - tanh(beta (1 - eta)) / tanh beta) */
 };
 enum { FLUID_VISC_NONE = 0, FLUID_VISC_CONSTANT = 1, FLUID_VISC_POWER = 2, FLUID_VISC_SUTHERLAND = 3 };
-enum { FLUID_WENO_JS = 0, FLUID_WENO_Z = 1 };
+/* Reconstruction of the face states (config field `weno`): WENO5-JS, WENO5-Z, or the paper's
+ * channel scheme TENO6-A with its interpolation limiter (Sec. 3.1; FP64 path only). */
+enum { FLUID_WENO_JS = 0, FLUID_WENO_Z = 1, FLUID_TENO6A = 2 };
 enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
 
 /*
@@ -117,7 +119,8 @@ typedef struct fluid_config {
   double cfl, dt_fixed;
   double porous_A, porous_kappa, porous_phi0;
   int32_t adjoint;          /* nonzero: also allocate the scratch of the adjoint entry points */
-  int32_t reserved;
+  int32_t visc_order;       /* central differences of the dissipative fluxes: 4 (or 0), or 6 as in
+                               the paper's channel computation (FP64 path only, no adjoint) */
 } fluid_config;
 
 typedef struct fluid_solver fluid_solver; /* opaque; owned by the library */

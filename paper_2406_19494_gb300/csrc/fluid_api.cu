@@ -176,7 +176,13 @@ const char* validate(const fluid_config* c) {
   if (c->visc_law != FLUID_VISC_NONE && c->visc_law != FLUID_VISC_CONSTANT && !(c->T_ref > 0))
     return "T_ref must be > 0";
   if (c->visc_law == FLUID_VISC_SUTHERLAND && !(c->suth_S >= 0)) return "suth_S must be >= 0";
-  if (c->weno != FLUID_WENO_JS && c->weno != FLUID_WENO_Z) return "unknown WENO variant";
+  if (c->weno != FLUID_WENO_JS && c->weno != FLUID_WENO_Z && c->weno != FLUID_TENO6A)
+    return "unknown reconstruction (weno)";
+  if (c->visc_order != 0 && c->visc_order != 4 && c->visc_order != 6) return "visc_order must be 0, 4 or 6";
+  if ((c->weno == FLUID_TENO6A || c->visc_order == 6) && c->precision != FLUID_PREC_FP64)
+    return "TENO6-A and sixth-order dissipative fluxes run in FP64 only";
+  if ((c->weno == FLUID_TENO6A || c->visc_order == 6) && c->adjoint)
+    return "the adjoint covers WENO5 with fourth-order dissipative fluxes only";
   if (c->precision != FLUID_PREC_FP64 && c->precision != FLUID_PREC_MIXED) return "unknown precision";
   if (!(c->dt_fixed > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt_fixed > 0";
   int nporous = 0;
@@ -247,7 +253,7 @@ int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
     return FLUID_OK;
   }
   if (s->ph.visc != FLUID_VISC_NONE)
-    FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
+    FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
   for (int d = 0; d < g.ndim; ++d)
     FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
              fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg, st));
@@ -285,7 +291,7 @@ int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, doub
   const Geo& g = s->geo;
   const bool visc = s->ph.visc != FLUID_VISC_NONE;
   FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(X, s->W, nullptr, g, s->ph, s->bc, s->ctl, st));
-  if (visc) FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, st));
+  if (visc) FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
   FL_CUDA(s, cudaMemsetAsync(s->gW, 0, fl::NW * (size_t)g.ncell * sizeof(double), st));
   if (visc) FL_CUDA(s, cudaMemsetAsync(s->gG, 0, fl::NG * (size_t)g.ncell * sizeof(double), st));
   FL_CUDA(s, cudaMemsetAsync(s->gvw, 0, s->gvw_count * sizeof(double), st));
@@ -364,6 +370,7 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   ph.suth_S = c.suth_S;
   ph.visc = c.visc_law;
   ph.weno = c.weno;
+  ph.visc_order = c.visc_order == 6 ? 6 : 4;
   ph.eps = c.weno_eps > 0 ? c.weno_eps : (c.weno == FLUID_WENO_JS ? 1e-6 : 1e-40);
   ph.has_force = 0;
   for (int a = 0; a < 3; ++a) {

@@ -34,6 +34,7 @@ struct Phys {
   double gamma, gm1, igm1, R, iR, cp, Pr, lam_fac;
   double mu_ref, T_ref, iT_ref, visc_exp, suth_S;
   int visc, weno;
+  int visc_order;     // central differences of the dissipative fluxes: 4 or 6
   double eps;
   double f[3];
   int has_force;
@@ -85,7 +86,9 @@ const char* config_error(const fluid_config* c);
 // with it W must hold NW + 1 rows, the last receiving H = E + p
 cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
                            const BC& bc, Ctl* ctl, cudaStream_t st);
-cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t st);
+cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph, cudaStream_t st);
+// launch shape of the marching FP64 face kernels: block/seg 0 pick the defaults; grid out
+void face_shape(int D, const Geo& g, int& block, int& seg, int& grid);
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st);
@@ -98,6 +101,9 @@ cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, dou
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,
                             double* dt_out, int clip_to_ctl, double t_end, cudaStream_t st);
 int dt_partial_count(const Geo& g);
+// ---- TENO6-A face kernels implemented in kernels_teno.cu ----------------------------------------
+cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R, const Geo& g,
+                             const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
 // ---- mixed-precision launchers implemented in kernels_mixed.cu --------------------------------
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,

@@ -249,29 +249,49 @@ FL_HD bool wall_map_prim(double w[6], int kind, double Tw, double vw, int a, con
 }
 
 // ------------------------------------------------------------------------------------------------
-// dissipative face flux along D (fourth-order central; the face is between cells 1 and 2 of the
-// four-cell stencils): vel[c][k], T[k] at cells a-1..a+2; gd[b][k] = d u_D / d x_b and
-// gb[b][k] = d u_b / d x_b at the same cells for tangential axes b (ignored for b == D or b >=
-// ndim); mfa = d(index)/dx at the face.  Returns Fd = (tau_0D, tau_1D, tau_2D, energy).
+// dissipative face flux along D by central differences of order NP (4 or 6 points); the face is
+// between cells NP/2 - 1 and NP/2 of the NP-cell stencils: vel[c][k], T[k] at cells
+// a-NP/2+1 .. a+NP/2; gd[b][k] = d u_D / d x_b and gb[b][k] = d u_b / d x_b at the same cells for
+// tangential axes b (ignored for b == D or b >= ndim); mfa = d(index)/dx at the face.  Returns
+// Fd = (tau_0D, tau_1D, tau_2D, energy).
+//   4 points: value (9 (f1 + f2) - (f0 + f3)) / 16, derivative ((f0 - f3) + 27 (f2 - f1)) / 24
+//   6 points: value (150 (f2 + f3) - 25 (f1 + f4) + 3 (f0 + f5)) / 256,
+//             derivative (2250 (f3 - f2) - 125 (f4 - f1) + 9 (f5 - f0)) / 1920
 // ------------------------------------------------------------------------------------------------
 FL_HD double interp4(const double f[4]) { return (9.0 * (f[1] + f[2]) - (f[0] + f[3])) * k16th; }
 FL_HD double dnorm4(const double f[4], double mfa) { return ((f[0] - f[3]) + 27.0 * (f[2] - f[1])) * k24th * mfa; }
+FL_HD double interp6(const double f[6]) {
+  return (150.0 * (f[2] + f[3]) - 25.0 * (f[1] + f[4]) + 3.0 * (f[0] + f[5])) * (1.0 / 256.0);
+}
+FL_HD double dnorm6(const double f[6], double mfa) {
+  return (2250.0 * (f[3] - f[2]) - 125.0 * (f[4] - f[1]) + 9.0 * (f[5] - f[0])) * (1.0 / 1920.0) * mfa;
+}
+template <int NP>
+FL_HD double interp_np(const double f[NP]) {
+  if constexpr (NP == 4) return interp4(f);
+  else return interp6(f);
+}
+template <int NP>
+FL_HD double dnorm_np(const double f[NP], double mfa) {
+  if constexpr (NP == 4) return dnorm4(f, mfa);
+  else return dnorm6(f, mfa);
+}
 
-template <int D>
-FL_HD void visc_face(const double vel[3][4], const double T[4], const double gd[3][4],
-                     const double gb[3][4], int ndim, double mfa, const Phys& ph, double Fd[4]) {
+template <int D, int NP = 4>
+FL_HD void visc_face(const double vel[3][NP], const double T[NP], const double gd[3][NP],
+                     const double gb[3][NP], int ndim, double mfa, const Phys& ph, double Fd[4]) {
   double vf[3], Gf[3][3];
   for (int c = 0; c < 3; ++c) {
-    vf[c] = interp4(vel[c]);
-    Gf[c][D] = dnorm4(vel[c], mfa);
+    vf[c] = interp_np<NP>(vel[c]);
+    Gf[c][D] = dnorm_np<NP>(vel[c], mfa);
   }
-  const double Tf = interp4(T);
-  const double dT = dnorm4(T, mfa);
+  const double Tf = interp_np<NP>(T);
+  const double dT = dnorm_np<NP>(T, mfa);
   for (int b = 0; b < 3; ++b) {
     if (b == D) continue;
     if (b < ndim) {
-      Gf[D][b] = interp4(gd[b]);
-      Gf[b][b] = interp4(gb[b]);
+      Gf[D][b] = interp_np<NP>(gd[b]);
+      Gf[b][b] = interp_np<NP>(gb[b]);
     } else {
       Gf[D][b] = 0.0;
       Gf[b][b] = 0.0;
@@ -286,5 +306,42 @@ FL_HD void visc_face(const double vel[3][4], const double T[4], const double gd[
   }
   Fd[3] = vf[0] * Fd[0] + vf[1] * Fd[1] + vf[2] * Fd[2] + lam * dT;
 }
+
+// Dissipative flux of the face a+1/2 along D from the primitives W and centre gradients G, with
+// the NP-point stencils; q holds the velocities already loaded for cells a-2 .. a+3 (q[1..3][o],
+// o = 0 .. 5).  F -= (0, tau_0D, tau_1D, tau_2D, energy).
+#ifdef __CUDACC__
+template <int D, int NP>
+__device__ __forceinline__ void add_visc_face(const double* __restrict__ W, const double* __restrict__ G, int cell, int s,
+                         int a, const Geo& g, const Phys& ph, const double q[5][6], double F[5]) {
+  constexpr int o0 = 3 - NP / 2;           // first stencil cell within q: a - NP/2 + 1
+  const int nc = g.ncell;
+  double vel[3][NP], T[NP], gd[3][NP], gb[3][NP];
+#pragma unroll
+  for (int o = 0; o < NP; ++o) {
+    vel[0][o] = q[1][o0 + o];
+    vel[1][o] = q[2][o0 + o];
+    vel[2][o] = q[3][o0 + o];
+    T[o] = __ldg(W + 5 * nc + cell + (o + o0 - 2) * s);
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (b == D || b >= g.ndim) continue;
+    const double* pd = G + (D * 3 + b) * nc + cell;   // d u_D / d x_b
+    const double* pb = G + (b * 3 + b) * nc + cell;   // d u_b / d x_b
+#pragma unroll
+    for (int o = 0; o < NP; ++o) {
+      gd[b][o] = __ldg(pd + (o + o0 - 2) * s);
+      gb[b][o] = __ldg(pb + (o + o0 - 2) * s);
+    }
+  }
+  double Fd[4];
+  visc_face<D, NP>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, Fd);
+  F[1] -= Fd[0];
+  F[2] -= Fd[1];
+  F[3] -= Fd[2];
+  F[4] -= Fd[3];
+}
+#endif
 
 }  // namespace fl

@@ -152,13 +152,17 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
 }
 
 // ------------------------------------------------------------------------------------------------
-// centre gradients: G[c*3+b] = d u_c / d x_b by ((f[-2] - f[+2]) + 8 (f[+1] - f[-1])) / 12 * mc,
-// only where the cell is interior along b (the only places the face fluxes read it)
+// centre gradients G[c*3+b] = d u_c / d x_b, only where the cell is interior along b (the only
+// places the face fluxes read it), for the cells the face stencils reach along the other axes:
+//   order 4: ((f[-2] - f[+2]) + 8 (f[+1] - f[-1])) / 12 * mc
+//   order 6: (45 (f[+1] - f[-1]) - 9 (f[+2] - f[-2]) + (f[+3] - f[-3])) / 60 * mc
 // ------------------------------------------------------------------------------------------------
+template <int ORDER>
 __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo g) {
+  constexpr int M = ORDER / 2;
   int lo[3], ext[3];
   for (int a = 0; a < 3; ++a) {
-    const int m = a < g.ndim ? 2 : 0;
+    const int m = a < g.ndim ? M : 0;
     lo[a] = g.h[a] - m;
     ext[a] = g.n[a] + 2 * m;
   }
@@ -178,7 +182,11 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
         double d = 0.0;
         if (inb) {
           const double* f = W + (1 + comp) * g.ncell + cell;
-          d = ((f[-2 * s] - f[2 * s]) + 8.0 * (f[s] - f[-s])) * kTwelfth * m;
+          if (ORDER == 4)
+            d = ((f[-2 * s] - f[2 * s]) + 8.0 * (f[s] - f[-s])) * kTwelfth * m;
+          else
+            d = (45.0 * (f[s] - f[-s]) - 9.0 * (f[2 * s] - f[-2 * s]) + (f[3 * s] - f[-3 * s])) *
+                (1.0 / 60.0) * m;
         }
         G[(comp * 3 + b) * g.ncell + cell] = d;
       }
@@ -189,7 +197,7 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
 // ------------------------------------------------------------------------------------------------
 // face flux F^c - F^d at face a+1/2 along D; `cell` is the padded index of cell a, s its stride
 // ------------------------------------------------------------------------------------------------
-template <int D, int SCHEME, bool VISC>
+template <int D, int SCHEME, int VORD>
 __device__ __forceinline__ void face_flux(const double* __restrict__ W, const double* __restrict__ G,
                                           int cell, int s, int a, const Geo& g, const Phys& ph,
                                           double F[5], double xl[5][3], double k0[5], double k1[5]) {
@@ -225,37 +233,10 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
     k1[v] = k2;
   }
   hllc<D>(wl, wr, ph, F);
-  if (!VISC) return;
-
-  // cells a-1 .. a+2 are q[.][1..4]
-  double vel[3][4], T[4], gd[3][4], gb[3][4];
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    vel[0][o] = q[1][1 + o];
-    vel[1][o] = q[2][1 + o];
-    vel[2][o] = q[3][1 + o];
-    T[o] = __ldg(W + 5 * nc + cell + (o - 1) * s);
-  }
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    if (b == D || b >= g.ndim) continue;
-    const double* pd = G + (D * 3 + b) * nc + cell;   // d u_D / d x_b
-    const double* pb = G + (b * 3 + b) * nc + cell;   // d u_b / d x_b
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      gd[b][o] = __ldg(pd + (o - 1) * s);
-      gb[b][o] = __ldg(pb + (o - 1) * s);
-    }
-  }
-  double Fd[4];
-  visc_face<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, Fd);
-  F[1] -= Fd[0];
-  F[2] -= Fd[1];
-  F[3] -= Fd[2];
-  F[4] -= Fd[3];
+  if (VORD) add_visc_face<D, VORD ? VORD : 4>(W, G, cell, s, a, g, ph, q, F);
 }
 
-template <int D, int SCHEME, bool VISC>
+template <int D, int SCHEME, int VORD>
 __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
                                               const double* __restrict__ G, double* __restrict__ R,
                                               Geo g, Phys ph, int accumulate, int seg) {
@@ -290,10 +271,10 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
       k0[v] = weno_k(qm1, q0, qp1);
       k1[v] = weno_k(q0, qp1, qp2);
     }
-    face_flux<D, SCHEME, VISC>(W, G, cell, s, a0 - 1, g, ph, Fp, xl, k0, k1);
+    face_flux<D, SCHEME, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, xl, k0, k1);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux<D, SCHEME, VISC>(W, G, cell, s, a, g, ph, F, xl, k0, k1);
+      face_flux<D, SCHEME, VORD>(W, G, cell, s, a, g, ph, F, xl, k0, k1);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -459,11 +440,38 @@ __global__ void k_wall_velocity(const double* __restrict__ phi, double* __restri
   }
 }
 
-template <int D, int SCHEME, bool VISC>
+template <int D, int SCHEME, int VORD>
 cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo& g,
                           const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  constexpr int A1 = (D == 0) ? 1 : 0;
-  constexpr int A2 = (D == 2) ? 1 : 2;
+  int grid;
+  face_shape(D, g, block, seg, grid);
+  k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
+  return cudaGetLastError();
+}
+
+template <int SCHEME, int VORD>
+cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, const Geo& g,
+                           const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  if (D == 0) return launch_face_t<0, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+  if (D == 1) return launch_face_t<1, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_face_t<2, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+}
+
+template <int SCHEME>
+cudaError_t launch_face_s(int D, const double* W, const double* G, double* R, const Geo& g,
+                          const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  if (ph.visc == FLUID_VISC_NONE)
+    return launch_face_sv<SCHEME, 0>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  if (ph.visc_order == 6)
+    return launch_face_sv<SCHEME, 6>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_face_sv<SCHEME, 4>(D, W, G, R, g, ph, accumulate, block, seg, st);
+}
+
+}  // namespace
+
+void face_shape(int D, const Geo& g, int& block, int& seg, int& grid) {
+  const int A1 = (D == 0) ? 1 : 0;
+  const int A2 = (D == 2) ? 1 : 2;
   const long long lines = (long long)g.n[A1] * g.n[A2];
   if (block <= 0) block = 128;
   if (seg <= 0) {
@@ -471,20 +479,8 @@ cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo
     seg = 64;
     while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
   }
-  const long long total = lines * ((g.n[D] + seg - 1) / seg);
-  k_face<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
-  return cudaGetLastError();
+  grid = grid_for(lines * ((g.n[D] + seg - 1) / seg), block);
 }
-
-template <int SCHEME, bool VISC>
-cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, const Geo& g,
-                           const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  if (D == 0) return launch_face_t<0, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
-  if (D == 1) return launch_face_t<1, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_face_t<2, SCHEME, VISC>(W, G, R, g, ph, accumulate, block, seg, st);
-}
-
-}  // namespace
 
 cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g, const Phys& ph,
                            const BC& bc, Ctl* ctl, cudaStream_t st) {
@@ -498,21 +494,21 @@ cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g,
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad(const double* W, double* G, const Geo& g, cudaStream_t st) {
+cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph, cudaStream_t st) {
+  const int m = ph.visc_order == 6 ? 3 : 2;
   long long total = 1;
-  for (int a = 0; a < 3; ++a) total *= g.n[a] + (a < g.ndim ? 4 : 0);
-  k_grad<<<grid_for(total, 256), 256, 0, st>>>(W, G, g);
+  for (int a = 0; a < 3; ++a) total *= g.n[a] + (a < g.ndim ? 2 * m : 0);
+  if (m == 3) k_grad<6><<<grid_for(total, 256), 256, 0, st>>>(W, G, g);
+  else k_grad<4><<<grid_for(total, 256), 256, 0, st>>>(W, G, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  const bool visc = ph.visc != FLUID_VISC_NONE;
+  if (ph.weno == FLUID_TENO6A) return launch_face_teno(D, W, G, R, g, ph, accumulate, block, seg, st);
   if (ph.weno == FLUID_WENO_JS)
-    return visc ? launch_face_sv<FLUID_WENO_JS, true>(D, W, G, R, g, ph, accumulate, block, seg, st)
-                : launch_face_sv<FLUID_WENO_JS, false>(D, W, G, R, g, ph, accumulate, block, seg, st);
-  return visc ? launch_face_sv<FLUID_WENO_Z, true>(D, W, G, R, g, ph, accumulate, block, seg, st)
-              : launch_face_sv<FLUID_WENO_Z, false>(D, W, G, R, g, ph, accumulate, block, seg, st);
+    return launch_face_s<FLUID_WENO_JS>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_face_s<FLUID_WENO_Z>(D, W, G, R, g, ph, accumulate, block, seg, st);
 }
 
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st) {

@@ -1,0 +1,135 @@
+// FP64 face kernels with the paper's channel-flow reconstruction (Sec. 3.1): TENO6-A on the
+// primitive variables with the interpolation limiter, the HLLC flux, and the dissipative flux by
+// central differences of order 4 or 6 (template VORD; 0 = inviscid).
+//
+// Interpolation limiter (reading of the paper's "interpolation limiter", its solver's
+// positivity-preserving limiting of reconstructed states): a face state with rho <= 0 or p <= 0
+// falls back, in all five primitives, to the cell on its side of the face.
+//
+// One thread marches along a segment of a grid line, as the WENO5 kernel does; each face is
+// computed once and serves the two cells that share it.  The scale sensors of the TENO-A cut-off
+// depend on single cells, so three of the four a face needs carry over from the previous face.
+#include <cuda_runtime.h>
+
+#include "fluid_internal.cuh"
+#include "teno_math.cuh"
+
+namespace fl {
+
+namespace {
+
+// face flux F^c - F^d at face a+1/2 along D; `cell` is the padded index of cell a, s its stride;
+// eta[v][0..2] carry the sensors of cells a-1, a, a+1 and are advanced by one cell
+template <int D, int VORD>
+__device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
+                                               int cell, int s, int a, const Geo& g, const Phys& ph,
+                                               double F[5], double eta[5][3]) {
+  const int nc = g.ncell;
+  double q[5][6];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int o = 0; o < 6; ++o) q[v][o] = __ldg(W + v * nc + cell + (o - 2) * s);
+  double wl[5], wr[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    // cells a-2 .. a+3 are q[v][0..5]; the sensor of cell a+2 is the new one
+    const double e3 = teno::sensor(q[v][4] - q[v][3], q[v][5] - q[v][4]);
+    const double ct = teno::cutoff(fmin(fmin(eta[v][0], eta[v][1]), fmin(eta[v][2], e3)));
+    wl[v] = teno::value(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], q[v][5], ct);
+    wr[v] = teno::value(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], q[v][0], ct);
+    eta[v][0] = eta[v][1];
+    eta[v][1] = eta[v][2];
+    eta[v][2] = e3;
+  }
+  // interpolation limiter
+  if (wl[0] <= 0.0 || wl[4] <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) wl[v] = q[v][2];
+  }
+  if (wr[0] <= 0.0 || wr[4] <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) wr[v] = q[v][3];
+  }
+  hllc<D>(wl, wr, ph, F);
+  if (VORD) add_visc_face<D, VORD ? VORD : 4>(W, G, cell, s, a, g, ph, q, F);
+}
+
+template <int D, int VORD>
+__global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
+                                                   const double* __restrict__ G, double* __restrict__ R,
+                                                   Geo g, Phys ph, int accumulate, int seg) {
+  constexpr int A1 = (D == 0) ? 1 : 0;
+  constexpr int A2 = (D == 2) ? 1 : 2;
+  const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
+  const int nseg = (nd + seg - 1) / seg;
+  const long long total = (long long)n1 * n2 * nseg;
+  const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
+  const int nc = g.ncell;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t % n1);
+    const long long r = t / n1;
+    const int i2 = (int)(r % n2);
+    const int sg = (int)(r / n2);
+    int c[3];
+    c[A1] = i1 + g.h[A1];
+    c[A2] = i2 + g.h[A2];
+    const int a0 = g.h[D] + sg * seg;
+    const int a1 = min(a0 + seg, g.h[D] + nd);
+    c[D] = a0 - 1;
+    int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
+    double Fp[5], F[5], eta[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      // sensors of cells a0-2, a0-1, a0 for the first face a0 - 1/2 (f points at cell a0 - 1)
+      const double* f = W + v * nc + cell;
+      const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
+                   qp2 = __ldg(f + 2 * s);
+      eta[v][0] = teno::sensor(qm1 - qm2, q0 - qm1);
+      eta[v][1] = teno::sensor(q0 - qm1, qp1 - q0);
+      eta[v][2] = teno::sensor(qp1 - q0, qp2 - qp1);
+    }
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta);
+    for (int a = a0; a < a1; ++a) {
+      cell += s;
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta);
+      const double id = g.idx[D][a];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double dF = F[v] - Fp[v];
+        double* dst = R + v * nc + cell;
+        *dst = accumulate ? fma(-id, dF, *dst) : -id * dF;
+        Fp[v] = F[v];
+      }
+    }
+  }
+}
+
+template <int D, int VORD>
+cudaError_t launch_d(const double* W, const double* G, double* R, const Geo& g, const Phys& ph,
+                     int accumulate, int block, int seg, cudaStream_t st) {
+  int grid;
+  face_shape(D, g, block, seg, grid);
+  k_face_teno<D, VORD><<<grid, block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
+  return cudaGetLastError();
+}
+
+template <int VORD>
+cudaError_t launch_v(int D, const double* W, const double* G, double* R, const Geo& g,
+                     const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  if (D == 0) return launch_d<0, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+  if (D == 1) return launch_d<1, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_d<2, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+}
+
+}  // namespace
+
+cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R, const Geo& g,
+                             const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+  if (ph.visc == FLUID_VISC_NONE) return launch_v<0>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  if (ph.visc_order == 6) return launch_v<6>(D, W, G, R, g, ph, accumulate, block, seg, st);
+  return launch_v<4>(D, W, G, R, g, ph, accumulate, block, seg, st);
+}
+
+}  // namespace fl

@@ -217,6 +217,7 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
   ph.suth_S = c.suth_S;
   ph.visc = c.visc_law;
   ph.weno = c.weno;
+  ph.visc_order = c.visc_order == 6 ? 6 : 4;
   ph.eps = c.weno_eps > 0 ? c.weno_eps : (c.weno == FLUID_WENO_JS ? 1e-6 : 1e-40);
   ph.has_force = 0;
   for (int a = 0; a < 3; ++a) {
@@ -276,7 +277,7 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = fl::launch_prim_bc(U_dev, W, nullptr, g, ph, bc, ctl, st);
-  if (e == cudaSuccess && visc) e = fl::launch_grad(W, G, g, st);
+  if (e == cudaSuccess && visc) e = fl::launch_grad(W, G, g, ph, st);
   for (int d = 0; e == cudaSuccess && d < g.ndim; ++d)
     e = fl::launch_face(d, W, G, R_dev, g, ph, d > 0, 0, 0, st);
   if (e == cudaSuccess && ph.has_force) e = fl::launch_source(R_dev, W, g, ph, st);

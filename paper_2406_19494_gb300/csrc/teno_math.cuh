@@ -1,0 +1,74 @@
+// TENO6-A reconstruction (the paper's channel scheme, Sec. 3.1), FP64.  The paper names the
+// scheme and cites its solver for it; the definition used here is the published one (Fu, Hu &
+// Adams 2016 for TENO6, 2017 for the adaptive cut-off):
+//   left-biased value at i+1/2 from q_{i-2} .. q_{i+3}; candidate stencils S0 = (i-1, i, i+1),
+//   S1 = (i, i+1, i+2), S2 = (i-2, i-1, i), S3 = (i, .., i+3) with the cell-average candidates
+//   p_k and the sixth-order linear weights d = (9/20, 3/10, 1/20, 1/5); Jiang-Shu smoothness
+//   measures beta_k and beta6 of the six-cell stencil, tau6 = |beta6 - (beta1 + beta2 + 4 beta0)/6|,
+//   gamma_k = (1 + tau6 / (beta_k + 1e-40))^6; a stencil is kept unless gamma_k / sum gamma < C_T,
+//   and the value is sum d_k p_k over the kept stencils divided by their sum of d_k.
+//   Adaptive C_T = 10^-floor(10.5 - 3.5 (1 - g(m))), g = (1 - m)^4 (1 + 4 m),
+//   m = 1 - min(1, eta / 0.25), eta the smallest scale sensor
+//   (2 |D+ D-| + e) / (D+^2 + D-^2 + e) (D+- the differences to the two neighbours,
+//   e = 0.9 * 0.25 * 1e-6 / 0.75) over the cells i-1 .. i+2.
+// The right-biased value at i+1/2 is the left-biased value of the mirrored stencil; both use the
+// same four cells for the sensor, so one cut-off serves both states of a face.
+#pragma once
+
+#include "flux_math.cuh"
+#include "teno_coeffs.cuh"
+
+namespace fl {
+namespace teno {
+
+constexpr double kEps = 1e-40;
+constexpr double kSensorE = 0.9 * 0.25 * 1e-6 / 0.75;
+
+// scale sensor of a cell from the differences to its two neighbours
+FL_HD double sensor(double dm, double dp) {
+  return (2.0 * fabs(dp * dm) + kSensorE) * fl_rcp(fma(dp, dp, fma(dm, dm, kSensorE)));
+}
+
+// cut-off C_T from the smallest sensor of the stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5)
+FL_HD double cutoff(double eta) {
+  const double m = 1.0 - fmin(1.0, 4.0 * eta);
+  const double t = 1.0 - m, t2 = t * t;
+  const double g = t2 * t2 * (1.0 + 4.0 * m);
+  const double bb = 10.5 - 3.5 * (1.0 - g);          // in [7, 10.5]
+  return bb >= 10.0 ? 1e-10 : (bb >= 9.0 ? 1e-9 : (bb >= 8.0 ? 1e-8 : 1e-7));
+}
+
+// left-biased value at i+1/2 from q0 .. q5 = q_{i-2} .. q_{i+3} with cut-off ct
+FL_HD double value(double q0, double q1, double q2, double q3, double q4, double q5, double ct) {
+  const double p0 = fma(2.0, q3, fma(5.0, q2, -q1)) * kSixth;
+  const double p1 = fma(-1.0, q4, fma(5.0, q3, 2.0 * q2)) * kSixth;
+  const double p2 = fma(11.0, q2, fma(-7.0, q1, 2.0 * q0)) * kSixth;
+  const double p3 = fma(1.0, q5, fma(-5.0, q4, fma(13.0, q3, 3.0 * q2))) * (1.0 / 12.0);
+  const double b0 = weno_B(q1, q2, q3);
+  const double b1 = weno_C(q2, q3, q4);
+  const double b2 = weno_A(q0, q1, q2);
+  const double e4[3] = {q3 - q2, q4 - q2, q5 - q2};
+  const double b3 = beta4_form(e4);
+  const double e6[5] = {q1 - q0, q2 - q0, q3 - q0, q4 - q0, q5 - q0};
+  const double b6 = beta6_form(e6);
+  const double tau = fabs(b6 - (b1 + b2 + 4.0 * b0) * kSixth);
+  double g[4];
+  const double bk[4] = {b0, b1, b2, b3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double x = 1.0 + tau * fl_rcp(bk[k] + kEps);
+    const double x2 = x * x;
+    g[k] = x2 * x2 * x2;
+  }
+  const double thr = ct * ((g[0] + g[1]) + (g[2] + g[3]));
+  // kept unless gamma_k / sum gamma < C_T
+  const double w0 = g[0] < thr ? 0.0 : 0.45;
+  const double w1 = g[1] < thr ? 0.0 : 0.3;
+  const double w2 = g[2] < thr ? 0.0 : 0.05;
+  const double w3 = g[3] < thr ? 0.0 : 0.2;
+  const double num = fma(w3, p3, fma(w2, p2, fma(w1, p1, w0 * p0)));
+  return num * fl_rcp((w0 + w1) + (w2 + w3));
+}
+
+}  // namespace teno
+}  // namespace fl

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "FLUID_OK", 1: "FLUID_EINVAL", 2: "FLUID_ENOMEM", 3: "FLUID_E
 BC = {"periodic": 0, "zero_gradient": 1, "wall": 2, "adiabatic": 3, "porous": 4, "inflow": 5}
 STRETCH = {"uniform": 0, "tanh2": 1, "tanh1": 2}
 VISC = {"none": 0, "constant": 1, "power": 2, "sutherland": 3}
-WENO = {"js": 0, "z": 1}
+WENO = {"js": 0, "z": 1, "teno6a": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 KERNELS = ("prim_bc", "grad", "face_x", "face_y", "face_z", "stage", "dt", "source", "adj_face", "adj_cell")
 
@@ -95,7 +95,7 @@ class FluidConfig(ctypes.Structure):
         ("porous_kappa", ctypes.c_double),
         ("porous_phi0", ctypes.c_double),
         ("adjoint", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("visc_order", ctypes.c_int32),
     ]
 
 
@@ -154,6 +154,7 @@ def config_from_case(case, precision="fp64", adjoint=False):
     c.dt_fixed = float(case.get("dt_fixed", 0.0))
     c.precision = PRECISION[precision]
     c.adjoint = 1 if adjoint else 0
+    c.visc_order = int(case.get("visc_order", 4))
     pz = case.get("porous", None)
     if pz:
         c.porous_axis, c.porous_side = int(pz["axis"]), int(pz["side"])

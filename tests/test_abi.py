@@ -54,7 +54,10 @@ def _create(lib, cfg):
     (lambda c: setattr(c, "gamma", 1.0), "gamma"),
     (lambda c: setattr(c, "struct_size", 8), "struct_size"),
     (lambda c: setattr(c, "precision", 7), "precision"),
-    (lambda c: setattr(c, "weno", 9), "WENO"),
+    (lambda c: setattr(c, "weno", 9), "reconstruction"),
+    (lambda c: setattr(c, "visc_order", 5), "visc_order"),
+    (lambda c: (setattr(c, "weno", 2), setattr(c, "precision", 1)), "FP64 only"),
+    (lambda c: (setattr(c, "visc_order", 6), setattr(c, "adjoint", 1)), "adjoint"),
     (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
 ])
 def test_invalid_configs_are_rejected_before_any_gpu_call(lib, mutate, needle):

@@ -242,7 +242,7 @@ def _patch_rhs(Ufilled, case, grid, cell):
     sub = dict(ndim=case.ndim, n=(1, 1, 1), lo=case.lo, hi=case.hi, bc=case.bc, gamma=case.gamma,
                R=case.R, Pr=case.Pr, visc=case.visc, mu_ref=case.mu_ref, T_ref=case.T_ref,
                visc_exp=case.visc_exp, suth_S=case.suth_S, weno=case.weno, weno_eps=case.weno_eps,
-               body_force=case.body_force, t_wall=case.t_wall)
+               body_force=case.body_force, t_wall=case.t_wall, visc_order=case.visc_order)
     sc = nf.Case(sub)
     axes = [_SubAxis(grid.axes[a], cell[a] - 3, cell[a] + 4) for a in range(3)]
     sl = (slice(None),) + tuple(slice(cell[a] - 3, cell[a] + 4) for a in (2, 1, 0))
