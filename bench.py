@@ -183,6 +183,9 @@ def run_fluid(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         mixed_ms = t.item()
 
+    # ---- the paper's channel scheme (TENO6-A + sixth-order central, FP64) ------------------------
+    teno = measure_teno(flush, stream, args) if not args.no_teno and ws == 1 else None
+
     # ---- adjoint / forward ratio (the metric's third part) -------------------------------------
     adjoint = measure_adjoint(flush, stream) if not args.no_adjoint else None
 
@@ -265,6 +268,7 @@ def run_fluid(args):
                 "flops32_per_cell_axis": accounting.mixed_cell_axis_flops32(case["weno"], case["visc"]),
                 "bytes_per_cell_axis": accounting.mixed_face_bytes()},
         },
+        "teno6a": teno,
         "adjoint": adjoint,
         "serving": serving,
         "clocks": clk.summary(),
@@ -277,6 +281,31 @@ def run_fluid(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measure_teno(flush, stream, args, steps=5):
+    """The scheme of the paper's channel computation (TENO6-A with the interpolation limiter, HLLC,
+    sixth-order central dissipative fluxes; FP64) on the channel workload, 192 x 128 x 128 cells:
+    cell-updates/s per RK3 step and the roofline of its face kernels."""
+    import torch
+    from paper_2406_19494_gb300.solver import Solver
+    c = dict(workloads.channel_case(192, 128, 128), weno="teno6a", visc_order=6)
+    s = Solver(c)
+    cen = [s.grid(a)[0][3:-3] for a in range(3)]
+    W = np.pad(workloads.channel_prims(c, *cen, seed=0), [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U = s.prim_to_cons(torch.from_numpy(W).cuda())
+    ncell = c["n"][0] * c["n"][1] * c["n"][2]
+    ms, prof, _ = timed_steps(s, U, steps, max(3, args.warmup), flush, stream)
+    f = {k: v for k, v in prof.items() if k.startswith("face_")}
+    t_face = sum(v[0] for v in f.values()) / max(1, sum(v[1] for v in f.values())) * 1e-3
+    per_axis = accounting.cell_axis_flops(3, "teno6a", c["visc"], 6)
+    achieved = per_axis * ncell / t_face / 1e12
+    peak64 = 152 * 2 * 2 * 2.07e9 / 1e12
+    return {"workload": "channel 192x128x128, TENO6-A + interpolation limiter + HLLC + 6th-order central",
+            "value": ncell * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "dtype": "f64", "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
+            "roofline_face": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                              "frac": achieved / peak64, "flops_per_cell_axis": per_axis}}
 
 
 def measure_adjoint(flush, stream, steps=5, warmup=3, grad_steps=400, K=20):
@@ -515,6 +544,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-teno", action="store_true", help="skip the TENO6-A channel-scheme measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "fluid":
         args.warmup = 3

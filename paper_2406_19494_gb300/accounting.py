@@ -8,43 +8,57 @@ Per face (one axis, one face, 3-D viscous WENO5-Z + HLLC):
   WENO5-Z reconstruction    73 per variable and side (JS: 69); 10 per face
   HLLC (one star branch)   115
   dissipative flux          90 (power-law mu; Sutherland 94; 1-D / 2-D fewer tangential terms)
+  TENO6-A reconstruction   165 per variable and side, plus the TENO-A scale sensor and cut-off
+                           (27 per variable, shared by both sides); 10 and 5 per face
+  sixth-order dissipative  the same terms with six-point interpolations (11) and derivatives (12)
 Per cell and axis: one face + the flux difference (3 per variable) = face + 15.
 Per cell and stage: primitives 15, centre gradients 6 per component, stage combination about 20.
 Per cell and RK3 step: 3 stages + the CFL reduction (about 28).
 """
 
 WENO = {"z": 73, "js": 69}
+TENO = 165
+TENO_SENSOR = 27
 HLLC = 115
 PRIM = 15
 STAGE = 20
 DT = 28
 
 
-def visc_face(ndim, visc):
+def visc_face(ndim, visc, order=4):
     if visc == "none":
         return 0
     tang = ndim - 1                       # tangential axes with derivative terms
     mu = {"constant": 0, "power": 3, "sutherland": 7}[visc]
+    if order == 6:
+        return 4 * 11 + 4 * 12 + 22 * tang + 2 + mu + 1 + 9 + 7 + 4
     return 20 + 24 + 10 * tang + 2 + mu + 1 + 9 + 7 + 4
 
 
-def face_flops(ndim, weno, visc):
-    return 10 * WENO[weno] + HLLC + visc_face(ndim, visc)
+def recon_flops(weno):
+    """Reconstruction work of one face (five primitives, both sides)."""
+    if weno == "teno6a":
+        return 10 * TENO + 5 * TENO_SENSOR
+    return 10 * WENO[weno]
 
 
-def cell_axis_flops(ndim, weno, visc):
+def face_flops(ndim, weno, visc, order=4):
+    return recon_flops(weno) + HLLC + visc_face(ndim, visc, order)
+
+
+def cell_axis_flops(ndim, weno, visc, order=4):
     """One face flux plus the flux difference of one cell along one axis (a face-kernel unit)."""
-    return face_flops(ndim, weno, visc) + 15
+    return face_flops(ndim, weno, visc, order) + 15
 
 
-def cell_stage_flops(ndim, weno, visc):
-    grad = 6 * 3 * ndim if visc != "none" else 0
-    return ndim * cell_axis_flops(ndim, weno, visc) + PRIM + grad + STAGE
+def cell_stage_flops(ndim, weno, visc, order=4):
+    grad = (8 if order == 6 else 6) * 3 * ndim if visc != "none" else 0
+    return ndim * cell_axis_flops(ndim, weno, visc, order) + PRIM + grad + STAGE
 
 
-def cell_update_flops(ndim, weno, visc):
+def cell_update_flops(ndim, weno, visc, order=4):
     """Algorithmic FP64 flops of one cell over one TVD-RK3 step."""
-    return 3 * cell_stage_flops(ndim, weno, visc) + DT
+    return 3 * cell_stage_flops(ndim, weno, visc, order) + DT
 
 
 def cell_update_bytes(nvar=5, word=8):

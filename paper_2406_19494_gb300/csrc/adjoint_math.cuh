@@ -34,21 +34,22 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   double a0, a1, a2, ge0, ge1, ge2, gb0 = 0.0, gb2 = 0.0;
   // face value = N / (6 S), N = sum a_k C_k, S = sum a_k
   double r0 = 0.0, r1 = 0.0, r2 = 0.0, sg = 1.0;
+  const double i0 = fl_rcp(e0), i1 = fl_rcp(e1), i2 = fl_rcp(e2);
   if (SCHEME == FLUID_WENO_JS) {
-    const double i0 = 1.0 / e0, i1 = 1.0 / e1, i2 = 1.0 / e2;
     a0 = 0.1 * i0 * i0; a1 = 0.6 * i1 * i1; a2 = 0.3 * i2 * i2;
     r0 = i0; r1 = i1; r2 = i2;
   } else {
     const double tau = b0 - b2 < 0.0 ? b2 - b0 : b0 - b2;
     sg = b0 - b2 < 0.0 ? -1.0 : 1.0;
-    r0 = tau / e0; r1 = tau / e1; r2 = tau / e2;
+    r0 = tau * i0; r1 = tau * i1; r2 = tau * i2;
     a0 = 0.1 * (1.0 + r0 * r0); a1 = 0.6 * (1.0 + r1 * r1); a2 = 0.3 * (1.0 + r2 * r2);
   }
   const double S = a0 + a1 + a2;
   const double N = a0 * C0 + a1 * C1 + a2 * C2;
-  const double out = N / (6.0 * S);
-  const double gN = g_out / (6.0 * S);
-  const double gS = -g_out * out / S;
+  const double iS6 = fl_rcp(6.0 * S);
+  const double out = N * iS6;
+  const double gN = g_out * iS6;
+  const double gS = -6.0 * out * gN;                 // -g_out out / S
   const double ga0 = gN * C0 + gS, ga1 = gN * C1 + gS, ga2 = gN * C2 + gS;
   const double gC0 = gN * a0, gC1 = gN * a1, gC2 = gN * a2;
   if (SCHEME == FLUID_WENO_JS) {
@@ -59,10 +60,10 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   } else {
     // a_k = d_k (1 + r_k^2), r_k = tau / e_k
     const double gr0 = ga0 * 0.2 * r0, gr1 = ga1 * 1.2 * r1, gr2 = ga2 * 0.6 * r2;
-    const double gtau = gr0 / e0 + gr1 / e1 + gr2 / e2;
-    ge0 = -gr0 * r0 / e0;
-    ge1 = -gr1 * r1 / e1;
-    ge2 = -gr2 * r2 / e2;
+    const double gtau = gr0 * i0 + gr1 * i1 + gr2 * i2;
+    ge0 = -gr0 * r0 * i0;
+    ge1 = -gr1 * r1 * i1;
+    ge2 = -gr2 * r2 * i2;
     gb0 += sg * gtau;
     gb2 -= sg * gtau;
   }
@@ -95,13 +96,13 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   const double qL = fl_rsqrt(rL), qR = fl_rsqrt(rR);
   const double sL = rL * qL, sR = rR * qR;
   const double irL = qL * qL, irR = qR * qR;
-  const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
-  const double isum = 1.0 / (sL + sR);
+  const double cL = fl_sqrt(ph.gamma * pL * irL), cR = fl_sqrt(ph.gamma * pR * irR);
+  const double isum = fl_rcp(sL + sR);
   double ut[3];
   for (int c = 0; c < 3; ++c) ut[c] = (sL * wl[1 + c] + sR * wr[1 + c]) * isum;
   const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   const double Ht = (sL * HL + sR * HR) * isum;
-  const double ct = sqrt(ph.gm1 * (Ht - 0.5 * (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2])));
+  const double ct = fl_sqrt(ph.gm1 * (Ht - 0.5 * (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2])));
   const double utn = ut[D];
   const double aL = unL - cL, bL = utn - ct;
   const bool selL = aL <= bL;
@@ -112,7 +113,8 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   const double mL = rL * (SL - unL), mR = rR * (SR - unR);
   const double Nn = pR - pL + unL * mL - unR * mR;
   const double Dd = mL - mR;
-  const double Ss = Nn / Dd;
+  const double iDd = fl_rcp(Dd);
+  const double Ss = Nn * iDd;
   const bool left = (SL >= 0.0) || (Ss >= 0.0);
   const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
   const double r = left ? rL : rR, p = left ? pL : pR, E = left ? EL : ER;
@@ -138,7 +140,7 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   g_p += gF[4] * un;
   if (star) {
     const double d = S - Ss;
-    const double q = 1.0 / d;
+    const double q = fl_rcp(d);
     const double fac = m * q;
     const double A = E * ir, B = Ss - un, Cc = fac * Ss + p * q;
     const double Es = fac * A + B * Cc;
@@ -203,7 +205,7 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
     gER += g_E; gSR += g_S; gmR += g_m; girR += g_ir;
   }
   // Ss = Nn / Dd
-  const double gNn = g_Ss / Dd, gDd = -g_Ss * Ss / Dd;
+  const double gNn = g_Ss * iDd, gDd = -g_Ss * Ss * iDd;
   gwr[4] += gNn;
   gwl[4] -= gNn;
   gwl[1 + D] += gNn * mL;
@@ -224,7 +226,7 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   // ct = sqrt(gm1 (Ht - |ut|^2 / 2))
   double gut[3] = {0.0, 0.0, 0.0};
   gut[D] += gutn;
-  const double gX = ct > 0.0 ? gct / (2.0 * ct) : 0.0;
+  const double gX = ct > 0.0 ? 0.5 * gct * fl_rcp(ct) : 0.0;
   const double gHt = ph.gm1 * gX;
   for (int c = 0; c < 3; ++c) gut[c] -= ph.gm1 * gX * ut[c];
   // Ht = (sL HL + sR HR) isum
@@ -251,7 +253,7 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   gsL += gsum;
   gsR += gsum;
   // c = sqrt(gamma p ir)
-  const double gYL = gcL / (2.0 * cL), gYR = gcR / (2.0 * cR);
+  const double gYL = 0.5 * gcL * fl_rcp(cL), gYR = 0.5 * gcR * fl_rcp(cR);
   gwl[4] += gYL * ph.gamma * irL;
   girL += gYL * ph.gamma * pL;
   gwr[4] += gYR * ph.gamma * irR;
@@ -341,7 +343,7 @@ FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double
 // ------------------------------------------------------------------------------------------------
 FL_HD void prim_vjp(const double U[5], const Phys& ph, const double gW[6], double gU[5]) {
   const double r = U[0];
-  const double ir = 1.0 / r;
+  const double ir = fl_rcp(r);
   const double u[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
   const double p = ph.gm1 * (U[4] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
   // T = p / (rho R)

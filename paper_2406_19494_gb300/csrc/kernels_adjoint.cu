@@ -48,10 +48,19 @@ __global__ void __launch_bounds__(128) k_adj_face(const double* __restrict__ W,
   const int nc = g.ncell;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int af = (int)(t % (nd + 1));          // face a + 1/2 with a = h - 1 + af
-    const long long r = t / (nd + 1);
-    const int i1 = (int)(r % n1);
-    const int i2 = (int)(r / n1);
+    // consecutive threads take consecutive x: faces for D = x, columns of faces otherwise
+    int af, i1, i2;                              // face a + 1/2 with a = h - 1 + af
+    if (D == 0) {
+      af = (int)(t % (nd + 1));
+      const long long r = t / (nd + 1);
+      i1 = (int)(r % n1);
+      i2 = (int)(r / n1);
+    } else {
+      i1 = (int)(t % n1);
+      const long long r = t / n1;
+      af = (int)(r % (nd + 1));
+      i2 = (int)(r / (nd + 1));
+    }
     int c[3];
     c[A1] = i1 + g.h[A1];
     c[A2] = i2 + g.h[A2];
@@ -159,10 +168,18 @@ __global__ void k_adj_gather(const double* __restrict__ CW, const double* __rest
   const int amin = g.h[D] - 1, amax = g.h[D] + g.n[D] - 1;   // faces a + 1/2
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(t % pd);
-    const long long r = t / pd;
-    const int i1 = (int)(r % n1);
-    const int i2 = (int)(r / n1);
+    int x, i1, i2;                               // consecutive threads take consecutive x
+    if (D == 0) {
+      x = (int)(t % pd);
+      const long long r = t / pd;
+      i1 = (int)(r % n1);
+      i2 = (int)(r / n1);
+    } else {
+      i1 = (int)(t % n1);
+      const long long r = t / n1;
+      x = (int)(r % pd);
+      i2 = (int)(r / pd);
+    }
     int c[3];
     c[A1] = i1 + g.h[A1];
     c[A2] = i2 + g.h[A2];
