@@ -285,11 +285,13 @@ def run_fluid(args):
 
 def measure_teno(flush, stream, args, steps=5):
     """The scheme of the paper's channel computation (TENO6-A with the interpolation limiter, HLLC,
-    sixth-order central dissipative fluxes; FP64) on the channel workload, 192 x 128 x 128 cells:
-    cell-updates/s per RK3 step and the roofline of its face kernels."""
+    sixth-order central dissipative fluxes; FP64) on the channel workload, 192 x 128 x 128 cells
+    (96 x 64 x 64 with the small --workload tgv64): cell-updates/s per RK3 step and the roofline of
+    its face kernels."""
     import torch
     from paper_2406_19494_gb300.solver import Solver
-    c = dict(workloads.channel_case(192, 128, 128), weno="teno6a", visc_order=6)
+    n = (96, 64, 64) if args.workload == "tgv64" else (192, 128, 128)
+    c = dict(workloads.channel_case(*n), weno="teno6a", visc_order=6)
     s = Solver(c)
     cen = [s.grid(a)[0][3:-3] for a in range(3)]
     W = np.pad(workloads.channel_prims(c, *cen, seed=0), [(0, 0)] + [(3, 3)] * 3, mode="edge")
@@ -301,7 +303,7 @@ def measure_teno(flush, stream, args, steps=5):
     per_axis = accounting.cell_axis_flops(3, "teno6a", c["visc"], 6)
     achieved = per_axis * ncell / t_face / 1e12
     peak64 = 152 * 2 * 2 * 2.07e9 / 1e12
-    return {"workload": "channel 192x128x128, TENO6-A + interpolation limiter + HLLC + 6th-order central",
+    return {"workload": "channel %dx%dx%d, TENO6-A + interpolation limiter + HLLC + 6th-order central" % n,
             "value": ncell * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "dtype": "f64", "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
             "roofline_face": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
@@ -457,7 +459,8 @@ def face_traffic(ncell):
     except (OSError, ValueError):
         return None
     csrc = os.path.join(ROOT, "paper_2406_19494_gb300", "csrc")
-    src = open(os.path.join(csrc, "kernels_fp64.cu"), "rb").read() + open(os.path.join(csrc, "fluid_internal.cuh"), "rb").read()
+    src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                   for f in ("kernels_fp64.cu", "fluid_internal.cuh", "flux_math.cuh"))
     if hashlib.sha256(src).hexdigest()[:16] != info.get("source_sha256_16"):
         return None
     per = sum(info["dram_bytes_per_launch"]) / len(info["dram_bytes_per_launch"])
