@@ -62,6 +62,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device):
+    """The largest of the ranks' times (ms); every rank returns the same value.  One rank: ms."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(cells, steps, ranks, ms):
+    """Cell-updates/s of the whole job: every rank advances its own replica of `cells` cells by
+    `steps` steps; the job takes the slowest rank's time `ms`."""
+    return cells * steps * ranks / (ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -169,19 +186,14 @@ def run_fluid(args):
     total_ms, prof, clk = timed_steps(s, U, args.steps, args.warmup, flush, stream, clock_gpu=local)
     if ws > 1:
         dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, "cuda")
     launches = sum(n for _, n in prof.values())
 
     # ---- the mixed FP32-flux / FP64-state path on the same workload ------------------------------
     sm = Solver(case, precision="mixed")
     Um = U0.clone()
     mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
-    if ws > 1:
-        t = torch.tensor([mixed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mixed_ms = t.item()
+    mixed_ms = max_over_ranks(mixed_ms, "cuda")
 
     # ---- the paper's channel scheme (TENO6-A + sixth-order central, FP64) ------------------------
     teno = measure_teno(flush, stream, args) if not args.no_teno and ws == 1 else None
@@ -209,10 +221,7 @@ def run_fluid(args):
         if k > 0:
             e_ms.append(a.elapsed_time(b))
     e2e_ms = sum(e_ms) / len(e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = max_over_ranks(e2e_ms, "cuda")
 
     # ---- rooflines of the dominant kernel class (the face kernels) ----------------------------
     def face_time(p):
@@ -235,7 +244,7 @@ def run_fluid(args):
     m32 = accounting.mixed_cell_axis_flops32(case["weno"], case["visc"]) * ncell / tm_face / 1e12
     mbytes = accounting.mixed_face_bytes() * ncell / tm_face / 1e9
 
-    value = ncell * args.steps * ws / (total_ms * 1e-3)
+    value = whole_job_rate(ncell, args.steps, ws, total_ms)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -255,7 +264,7 @@ def run_fluid(args):
                      "flops_per_cell_update": accounting.cell_update_flops(3, case["weno"], case["visc"])},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "mixed": {
-            "value": ncell * args.steps * ws / (mixed_ms * 1e-3), "unit": UNIT,
+            "value": whole_job_rate(ncell, args.steps, ws, mixed_ms), "unit": UNIT,
             "ms_per_step": mixed_ms / args.steps, "speedup_vs_fp64": total_ms / mixed_ms,
             "dtype": "f32 fluxes / f64 state",
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items() if v[1]},
