@@ -260,6 +260,7 @@ int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int
 int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev, double* ieee_dev,
                      int n, void* stream);
 
+
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as
  * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is
  * owned by its own pool or arena and which forbids allocations behind its back, or a

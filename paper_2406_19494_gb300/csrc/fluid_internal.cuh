@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/fluid.h"
+#include "fast_math.cuh"
 
 namespace fl {
 
@@ -65,7 +66,7 @@ __host__ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   const double r = T * ph.iT_ref;
   if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * exp(ph.visc_exp * log(r));
   // Sutherland
-  return ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
+  return ph.mu_ref * (r * fl_sqrt(r)) * (ph.T_ref + ph.suth_S) * fl_rcp(T + ph.suth_S);
 }
 
 // d mu / d T of the same laws
