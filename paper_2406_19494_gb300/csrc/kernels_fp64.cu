@@ -64,7 +64,14 @@ __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a
 }
 
 // primitives of padded cell own[] (interior: from U; halo: composed boundary maps); E receives the
-// total energy per volume of interior cells (halo cells leave it unset)
+// total energy per volume of interior cells (halo cells leave it unset).
+//
+// The halo passes x -> y -> z compose: the pass of axis a sees own indices on the axes before it
+// and source indices on the axes after it, so a halo cell starts from the cell at the source index
+// on every axis and then takes the maps of its halo axes in order (an inflow axis replaces the
+// state by its profile).  Every cell therefore converts exactly one cell's U -- its own or its
+// source -- and only wall halos run map arithmetic, so warps that straddle the x halo do not run
+// the conversion twice.
 __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const int own[3], int cell,
                                           const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
                                           double w[NW], double& E) {
@@ -77,30 +84,22 @@ __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const in
     src[a] = ghost[a] ? bc_source(bc.kind[a][side[a]], side[a], own[a], g.n[a], g.h[a]) : own[a];
     any |= ghost[a];
   }
+  const int scell = any ? src[0] + src[1] * g.sy + src[2] * g.sz : cell;
+  prim_of(U, scell, g.ncell, ph, w);
   if (!any) {
-    prim_of(U, cell, g.ncell, ph, w);
     E = U[4 * g.ncell + cell];
     return false;
   }
-  // Sequential halo passes x -> y -> z, composed: the pass of axis a sees own indices on the
-  // axes before it and source indices on the axes after it.
-  bool have = false;
   for (int a = 0; a < 3; ++a) {
     if (!ghost[a]) continue;
     const int kind = bc.kind[a][side[a]];
+    if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) continue;
     int c[3];
     for (int b = 0; b < 3; ++b) c[b] = b < a ? own[b] : src[b];
     if (kind == FLUID_BC_INFLOW) {
       inflow_at(bc.inflow[a][side[a]], a, c, g, ph, w);
-      have = true;
       continue;
     }
-    if (!have) {
-      c[a] = src[a];
-      prim_of(U, c[0] + c[1] * g.sy + c[2] * g.sz, g.ncell, ph, w);
-      have = true;
-    }
-    if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) continue;
     double vw = 0.0;
     if (kind == FLUID_BC_POROUS) vw = bc.vw[c[bc.porous_t1]];
     wall_map(w, kind, bc.Tw[a][side[a]], vw, a, ph, &ctl->flags);
