@@ -59,6 +59,8 @@ def _create(lib, cfg):
     (lambda c: (setattr(c, "weno", 2), setattr(c, "precision", 1)), "FP64 only"),
     (lambda c: (setattr(c, "visc_order", 6), setattr(c, "adjoint", 1)), "adjoint"),
     (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
+    (lambda c: c.n.__setitem__(0, (1 << 20) + 1), "3 <= n"),
+    (lambda c: (c.n.__setitem__(0, 20000), c.n.__setitem__(1, 20000)), "32-bit"),
 ])
 def test_invalid_configs_are_rejected_before_any_gpu_call(lib, mutate, needle):
     cfg = native.config_from_case(wl.random_box(2, (8, 8, 1)))

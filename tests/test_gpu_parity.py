@@ -372,3 +372,36 @@ def test_channel_full_size_sampled():
     xs = [grid.axes[a].xc[3:-3] for a in range(3)]
     W = wl.channel_prims(c, *xs, seed=0)
     _sampled_rhs_check(c, W, margin=0)
+
+
+@pytest.mark.slow
+def test_longest_axis_one_dimensional():
+    """The longest axis the configuration admits (2^20 cells, 1-D Sod-type data repeated along x):
+    sampled cells of one right-hand side and of one step against the oracle on 7-cell patches."""
+    n = 1 << 20
+    c = dict(wl.sod_case(200), n=(n, 1, 1), hi=(float(n) / 200.0, 1.0, 1.0))
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xc = grid.axes[0].xc
+    # a Sod state every 200 cells (discontinuities all along the axis)
+    W = wl.sod_prims((xc % 1.0))[:, None, None, :]
+    U = nf.prim_to_cons(W, case)
+    s = Solver(c)
+    Rg = s.rhs(torch.from_numpy(U).cuda())
+    s.check()
+    Rg = Rg.cpu().numpy()
+    Uf = nf.fill_halos(U.copy(), case, grid)
+    rng = np.random.default_rng(1)
+    cells = [int(v) for v in rng.integers(3, 3 + n, 40)] + [3, 3 + n - 1, 3 + n // 2]
+    sub = dict(c, n=(1, 1, 1))
+    sc = nf.Case(sub)
+    ref, got = [], []
+    for x in cells:
+        axes = [_SubAxis(grid.axes[0], x - 3, x + 4), _SubAxis(grid.axes[1], 0, 1), _SubAxis(grid.axes[2], 0, 1)]
+        R = nf.rhs_filled(Uf[:, :, :, x - 3:x + 4].copy(), sc, _SubGrid(axes))
+        ref.append(R[:, 0, 0, 3])
+        got.append(Rg[:, 0, 0, x])
+    ref, got = np.array(ref), np.array(got)
+    scale = np.max(np.abs(ref), axis=0)
+    scale = np.where(scale > 0, scale, 1.0)
+    assert np.all(np.max(np.abs(got - ref), axis=0) / scale <= TOL)
