@@ -19,11 +19,12 @@ namespace fl {
 namespace {
 
 // face flux F^c - F^d at face a+1/2 along D; `cell` is the padded index of cell a, s its stride;
-// eta[v][0..2] carry the sensors of cells a-1, a, a+1 and are advanced by one cell
+// eta[v][0..2] carry the sensors of cells a-1, a, a+1 and b3[v] the three-cell smoothness
+// measures of the left state (see teno::face_states); both advance by one cell
 template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
-                                               double F[5], double eta[5][3]) {
+                                               double F[5], double eta[5][3], double b3[5][3]) {
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -36,8 +37,7 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
     // cells a-2 .. a+3 are q[v][0..5]; the sensor of cell a+2 is the new one
     const double e3 = teno::sensor(q[v][4] - q[v][3], q[v][5] - q[v][4]);
     const double ct = teno::cutoff(fmin(fmin(eta[v][0], eta[v][1]), fmin(eta[v][2], e3)));
-    wl[v] = teno::value(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], q[v][5], ct);
-    wr[v] = teno::value(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], q[v][0], ct);
+    teno::face_states(q[v], ct, b3[v], wl[v], wr[v]);
     eta[v][0] = eta[v][1];
     eta[v][1] = eta[v][2];
     eta[v][2] = e3;
@@ -79,21 +79,25 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], eta[5][3];
+    double Fp[5], F[5], eta[5][3], b3[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      // sensors of cells a0-2, a0-1, a0 for the first face a0 - 1/2 (f points at cell a0 - 1)
+      // sensors of cells a0-2, a0-1, a0 and the left-state three-cell measures of the first face
+      // a0 - 1/2 (f points at cell a0 - 1)
       const double* f = W + v * nc + cell;
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
       eta[v][0] = teno::sensor(qm1 - qm2, q0 - qm1);
       eta[v][1] = teno::sensor(q0 - qm1, qp1 - q0);
       eta[v][2] = teno::sensor(qp1 - q0, qp2 - qp1);
+      b3[v][0] = weno_B(qm1, q0, qp1);
+      b3[v][1] = weno_C(q0, qp1, qp2);
+      b3[v][2] = weno_A(qm2, qm1, q0);
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

@@ -38,19 +38,9 @@ FL_HD double cutoff(double eta) {
   return bb >= 10.0 ? 1e-10 : (bb >= 9.0 ? 1e-9 : (bb >= 8.0 ? 1e-8 : 1e-7));
 }
 
-// left-biased value at i+1/2 from q0 .. q5 = q_{i-2} .. q_{i+3} with cut-off ct
-FL_HD double value(double q0, double q1, double q2, double q3, double q4, double q5, double ct) {
-  const double p0 = fma(2.0, q3, fma(5.0, q2, -q1)) * kSixth;
-  const double p1 = fma(-1.0, q4, fma(5.0, q3, 2.0 * q2)) * kSixth;
-  const double p2 = fma(11.0, q2, fma(-7.0, q1, 2.0 * q0)) * kSixth;
-  const double p3 = fma(1.0, q5, fma(-5.0, q4, fma(13.0, q3, 3.0 * q2))) * (1.0 / 12.0);
-  const double b0 = weno_B(q1, q2, q3);
-  const double b1 = weno_C(q2, q3, q4);
-  const double b2 = weno_A(q0, q1, q2);
-  const double e4[3] = {q3 - q2, q4 - q2, q5 - q2};
-  const double b3 = beta4_form(e4);
-  const double e6[5] = {q1 - q0, q2 - q0, q3 - q0, q4 - q0, q5 - q0};
-  const double b6 = beta6_form(e6);
+// TENO6 weights and value from the candidates p_k and smoothness measures b_k (beta6 = b6)
+FL_HD double combine(double p0, double p1, double p2, double p3, double b0, double b1, double b2,
+                     double b3, double b6, double ct) {
   const double tau = fabs(b6 - (b1 + b2 + 4.0 * b0) * kSixth);
   double g[4];
   const double bk[4] = {b0, b1, b2, b3};
@@ -68,6 +58,48 @@ FL_HD double value(double q0, double q1, double q2, double q3, double q4, double
   const double w3 = g[3] < thr ? 0.0 : 0.2;
   const double num = fma(w3, p3, fma(w2, p2, fma(w1, p1, w0 * p0)));
   return num * fl_rcp((w0 + w1) + (w2 + w3));
+}
+
+// left-biased value at i+1/2 from q0 .. q5 = q_{i-2} .. q_{i+3} with cut-off ct
+FL_HD double value(double q0, double q1, double q2, double q3, double q4, double q5, double ct) {
+  const double p0 = fma(2.0, q3, fma(5.0, q2, -q1)) * kSixth;
+  const double p1 = fma(-1.0, q4, fma(5.0, q3, 2.0 * q2)) * kSixth;
+  const double p2 = fma(11.0, q2, fma(-7.0, q1, 2.0 * q0)) * kSixth;
+  const double p3 = fma(1.0, q5, fma(-5.0, q4, fma(13.0, q3, 3.0 * q2))) * (1.0 / 12.0);
+  const double e4[3] = {q3 - q2, q4 - q2, q5 - q2};
+  const double e6[5] = {q1 - q0, q2 - q0, q3 - q0, q4 - q0, q5 - q0};
+  return combine(p0, p1, p2, p3, weno_B(q1, q2, q3), weno_C(q2, q3, q4), weno_A(q0, q1, q2),
+                 beta4_form(e4), beta6_form(e6), ct);
+}
+
+// Both states of the face a+1/2 from q[0..5] = q_{a-2} .. q_{a+3} while marching along +D.
+//   * the left state's central and downwind candidates are the right state's downwind and central
+//     ones (the same quadratics through cells a-1..a+1 and a..a+2, at the same point);
+//   * the right state's three-cell measures (B of the stencil centred at a+1, A at a, C at a+2) are
+//     the next face's left-state measures (B at a+1, C at a+2, A at a): b3c carries them as
+//     (beta0, beta1, beta2) of that next left state.
+// On entry b3c holds this face's left-state (beta0, beta1, beta2); on exit the next face's.
+FL_HD void face_states(const double q[6], double ct, double b3c[3], double& wl, double& wr) {
+  const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1])) * kSixth;       // cells a-1..a+1
+  const double pd = fma(-1.0, q[4], fma(5.0, q[3], 2.0 * q[2])) * kSixth;  // cells a..a+2
+  const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0])) * kSixth;
+  const double p4 = fma(1.0, q[5], fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]))) * (1.0 / 12.0);
+  const double e4[3] = {q[3] - q[2], q[4] - q[2], q[5] - q[2]};
+  const double e6[5] = {q[1] - q[0], q[2] - q[0], q[3] - q[0], q[4] - q[0], q[5] - q[0]};
+  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), beta6_form(e6), ct);
+  // right state: the mirrored stencil q'_j = q[5 - j]
+  const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5])) * kSixth;
+  const double r4 = fma(1.0, q[0], fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]))) * (1.0 / 12.0);
+  const double f4[3] = {q[2] - q[3], q[1] - q[3], q[0] - q[3]};
+  const double f6[5] = {q[4] - q[5], q[3] - q[5], q[2] - q[5], q[1] - q[5], q[0] - q[5]};
+  const double rb0 = weno_B(q[4], q[3], q[2]);
+  const double rb1 = weno_C(q[3], q[2], q[1]);
+  const double rb2 = weno_A(q[5], q[4], q[3]);
+  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, beta4_form(f4), beta6_form(f6), ct);
+  // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at a (rb1's)
+  b3c[0] = rb0;
+  b3c[1] = rb2;
+  b3c[2] = rb1;
 }
 
 }  // namespace teno
