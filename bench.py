@@ -194,6 +194,7 @@ def run_fluid(args):
     Um = U0.clone()
     mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
     mixed_ms = max_over_ranks(mixed_ms, "cuda")
+    mixed_err = mixed_vs_fp64(s, sm, U, Um, case, args.warmup + args.steps)
 
     # ---- the paper's channel scheme (TENO6-A + sixth-order central, FP64) ------------------------
     teno = measure_teno(flush, stream, args) if not args.no_teno and ws == 1 else None
@@ -267,6 +268,7 @@ def run_fluid(args):
             "value": whole_job_rate(ncell, args.steps, ws, mixed_ms), "unit": UNIT,
             "ms_per_step": mixed_ms / args.steps, "speedup_vs_fp64": total_ms / mixed_ms,
             "dtype": "f32 fluxes / f64 state",
+            "error_vs_fp64": mixed_err,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items() if v[1]},
             "roofline_face": {
                 "fp64": {"achieved": m64, "peak": peak64, "unit": "TFLOP/s", "frac": m64 / peak64},
@@ -290,6 +292,35 @@ def run_fluid(args):
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def mixed_vs_fp64(s64, s32, U64, U32, case, steps):
+    """Differences between the FP64 and the mixed solutions after the same `steps` RK3 steps from
+    the same state (both timed runs): the state per variable (max |dU| / max |U|), the kinetic
+    energy and its rate of change (the TGV dissipation rate), with the rate from each solver's own
+    right-hand side.  Plain host arithmetic on copies; diagnostics, not part of the solver."""
+    import torch
+    inner = (slice(None),) + tuple(slice(3, 3 + case["n"][a]) for a in (2, 1, 0))
+    a = U64.cpu().numpy()[inner]
+    b = U32.cpu().numpy()[inner]
+    ra = s64.rhs(U64).cpu().numpy()[inner]
+    rb = s32.rhs(U32).cpu().numpy()[inner]
+    torch.cuda.synchronize()
+
+    def ke_and_rate(u, r):
+        m2 = u[1] ** 2 + u[2] ** 2 + u[3] ** 2
+        ke = 0.5 * m2 / u[0]
+        # d/dt (|m|^2 / 2 rho) = (m . dm/dt) / rho - |m|^2 / (2 rho^2) drho/dt
+        rate = (u[1] * r[1] + u[2] * r[2] + u[3] * r[3]) / u[0] - 0.5 * m2 / u[0] ** 2 * r[0]
+        return float(ke.sum()), float(rate.sum())
+    ke_a, rate_a = ke_and_rate(a, ra)
+    ke_b, rate_b = ke_and_rate(b, rb)
+    scale = np.max(np.abs(a.reshape(5, -1)), axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return {"steps": steps,
+            "state_max_rel": [float(v) for v in np.max(np.abs((a - b).reshape(5, -1)), axis=1) / scale],
+            "kinetic_energy_rel": abs(ke_b - ke_a) / abs(ke_a),
+            "kinetic_energy_rate_rel": abs(rate_b - rate_a) / abs(rate_a)}
 
 
 def measure_teno(flush, stream, args, steps=5):
