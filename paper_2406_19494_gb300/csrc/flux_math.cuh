@@ -72,8 +72,9 @@ FL_HD double weno5_beta(double qm2, double qm1, double q0, double qp1, double qp
 // right-biased value at face a+1/2 is, with the roles of its outer members exchanged, the set of
 // the left-biased value at a+3/2; weno_x gives the scaled weights of a set (X_k = alpha_k / d_k
 // times the common factor of weno5_beta, which is symmetric under that exchange) so that one set
-// serves both faces, and weno_x_value forms the value from the stencil and the X's with the
-// linear weights d_k and 1/6 folded into the candidate coefficients.
+// serves both faces, and weno_x_value forms the value from the stencil's centre and cell
+// differences and the X's, with the linear weights d_k and 1/6 folded into the candidate
+// coefficients.
 template <int SCHEME>
 FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
   const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
@@ -90,14 +91,18 @@ FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
   }
 }
 
-FL_HD double weno_x_value(double qm2, double qm1, double q0, double qp1, double qp2, const double X[3]) {
-  // d_k / 6 times the candidate values: d = (1/10, 6/10, 3/10)
-  const double C0 = fma(11.0 / 60.0, q0, fma(-7.0 / 60.0, qm1, (1.0 / 30.0) * qm2));
-  const double C1 = fma(0.2, qp1, fma(0.5, q0, -0.1 * qm1));
-  const double C2 = fma(-0.05, qp2, fma(0.25, qp1, 0.1 * q0));
+// The value from the stencil centre q0 and the four cell differences of the stencil,
+// dm2 = q_{i-1} - q_{i-2}, dm1 = q_i - q_{i-1}, dp0 = q_{i+1} - q_i, dp1 = q_{i+2} - q_{i+1}:
+// with the candidates as offsets from q_i, p0 - q_i = (5 dm1 - 2 dm2) / 6,
+// p1 - q_i = (dm1 + 2 dp0) / 6, p2 - q_i = (4 dp0 - dp1) / 6 (d_k / 6 folded in).
+FL_HD double weno_x_value(double q0, double dm2, double dm1, double dp0, double dp1, const double X[3]) {
+  // d = (1/10, 6/10, 3/10)
+  const double C0 = fma(5.0 / 60.0, dm1, (-2.0 / 60.0) * dm2);
+  const double C1 = fma(0.2, dp0, 0.1 * dm1);
+  const double C2 = fma(-0.05, dp1, 0.2 * dp0);
   const double num = fma(X[2], C2, fma(X[1], C1, X[0] * C0));
   const double den = fma(0.3, X[2], fma(0.6, X[1], 0.1 * X[0]));
-  return num * fl_rcp(den);
+  return fma(num, fl_rcp(den), q0);
 }
 
 // 13/12 t^2 with t the second difference of a three-cell stencil: the part the three indicator

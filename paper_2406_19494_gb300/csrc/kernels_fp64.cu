@@ -213,18 +213,22 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
   double wl[5], wr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    // cells a-2 .. a+3 are q[v][0..5]
-    const double k2 = weno_k(q[v][3], q[v][4], q[v][5]);
-    const double sA = fma(3.0, q[v][3], fma(-4.0, q[v][2], q[v][1]));
-    const double sB = q[v][2] - q[v][4];
-    const double sC = fma(3.0, q[v][3], fma(-4.0, q[v][4], q[v][5]));
+    // cells a-2 .. a+3 are q[v][0..5]; d_j = q[v][j+1] - q[v][j]
+    const double d0 = q[v][1] - q[v][0], d1 = q[v][2] - q[v][1], d2 = q[v][3] - q[v][2];
+    const double d3 = q[v][4] - q[v][3], d4 = q[v][5] - q[v][4];
+    const double t2 = d4 - d3;
+    const double k2 = k1312 * t2 * t2;                     // weno_k of cells a+1 .. a+3
+    const double sA = fma(3.0, d2, -d1);                   // q_{a-1} - 4 q_a + 3 q_{a+1}
+    const double sB = d2 + d3;                             // -(q_a - q_{a+2})
+    const double sC = fma(-3.0, d3, d4);                   // 3 q_{a+1} - 4 q_{a+2} + q_{a+3}
     const double An = fma(0.25 * sA, sA, k0[v]);
     const double Bn = fma(0.25 * sB, sB, k1[v]);
     const double Cn = fma(0.25 * sC, sC, k2);
-    wl[v] = weno_x_value(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], xl[v]);
+    wl[v] = weno_x_value(q[v][2], d0, d1, d2, d3, xl[v]);
     double xr[3];
     weno_x<SCHEME>(Cn, Bn, An, ph.eps, xr);
-    wr[v] = weno_x_value(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], xr);
+    // mirrored stencil: centre q_{a+1}, differences -d4, -d3, -d2, -d1
+    wr[v] = weno_x_value(q[v][3], -d4, -d3, -d2, -d1, xr);
     xl[v][0] = xr[2];
     xl[v][1] = xr[1];
     xl[v][2] = xr[0];
