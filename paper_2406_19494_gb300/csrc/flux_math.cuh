@@ -130,18 +130,19 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const double unL = wl[1 + D], unR = wr[1 + D];
   const double q2L = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
   const double q2R = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-  const double EL = pL * ph.igm1 + 0.5 * rL * q2L;
-  const double ER = pR * ph.igm1 + 0.5 * rR * q2R;
   // 1/sqrt(rho) gives both sqrt(rho) (Roe weights) and 1/rho
   const double qL = fl_rsqrt(rL), qR = fl_rsqrt(rR);
   const double sL = rL * qL, sR = rR * qR;
   const double irL = qL * qL, irR = qR * qR;
-  const double cL = fl_sqrt(ph.gamma * pL * irL), cR = fl_sqrt(ph.gamma * pR * irR);
+  // p / rho and the total enthalpy H = (E + p) / rho = gamma/(gamma-1) p/rho + |u|^2 / 2
+  const double gg = ph.gamma * ph.igm1;
+  const double pirL = pL * irL, pirR = pR * irR;
+  const double HL = fma(pirL, gg, 0.5 * q2L), HR = fma(pirR, gg, 0.5 * q2R);
+  const double cL = fl_sqrt(ph.gamma * pirL), cR = fl_sqrt(ph.gamma * pirR);
   const double isum = fl_rcp(sL + sR);
   const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
   const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
   const double ut2 = (sL * wl[3] + sR * wr[3]) * isum;
-  const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   const double Ht = (sL * HL + sR * HR) * isum;
   const double ct = fl_sqrt(ph.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
   const double utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
@@ -154,35 +155,36 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
   const double r = left ? rL : rR;
   const double p = left ? pL : pR;
-  const double E = left ? EL : ER;
+  const double H = left ? HL : HR;
   const double un = left ? unL : unR;
   const double S = left ? SL : SR;
   const double m = left ? mL : mR;
   const double u0 = left ? wl[1] : wr[1];
   const double u1 = left ? wl[2] : wr[2];
   const double u2 = left ? wl[3] : wr[3];
-  // Euler flux of the selected side
+  // Euler flux of the selected side: (rho u_n, rho u_n u + p n, rho u_n H)
   const double mn = r * un;
   F[0] = mn;
   F[1] = mn * u0;
   F[2] = mn * u1;
   F[3] = mn * u2;
   F[1 + D] += p;
-  F[4] = un * (E + p);
+  F[4] = mn * H;
   if (star) {
     // U*_K = m/(S - S*) [1, S* (normal), tangential u, E/rho + (S* - un)(S* + p/m)]
     const double q = fl_rcp(S - Ss);
     const double fac = m * q;
-    const double ir = left ? irL : irR;
+    const double pir = left ? pirL : pirR;
+    const double eir = H - pir;                       // E / rho
     const double dU0 = fac - r;
-    double dU[3] = {fac * u0 - r * u0, fac * u1 - r * u1, fac * u2 - r * u2};
+    double dU[3] = {dU0 * u0, dU0 * u1, dU0 * u2};
     dU[D] = fac * Ss - r * un;
-    const double Es = fac * (E * ir) + (Ss - un) * (fac * Ss + p * q);
+    const double Es = fac * eir + (Ss - un) * (fac * Ss + p * q);
     F[0] += S * dU0;
     F[1] += S * dU[0];
     F[2] += S * dU[1];
     F[3] += S * dU[2];
-    F[4] += S * (Es - E);
+    F[4] += S * (Es - r * eir);
   }
 }
 
