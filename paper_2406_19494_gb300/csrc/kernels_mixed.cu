@@ -394,22 +394,22 @@ __global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(MixedIn in, double
 }
 
 // y / z variant: lanes map to 32 consecutive x columns (coalesced loads); a block of NWARP warps
-// covers 4 NWARP - 1 cells along the face axis D (4 NWARP faces) of those columns at one index of
-// the remaining axis.  The cell differences along D are staged in shared memory; warp w computes
-// the four consecutive faces 4w .. 4w+3, keeps the previous face flux in registers for the
-// divergence of the cells between them and takes the flux of face 4w+4 from the next warp
-// through shared memory.  Registers are capped at 64 so that 32 / NWARP blocks (32 warps) fit an SM.
-constexpr int kTFaces = 4;                                   // faces per warp
-
-template <int NWARP>
+// covers FPW NWARP - 1 cells along the face axis D (FPW NWARP faces) of those columns at one index
+// of the remaining axis.  The cell differences along D are staged in shared memory; warp w computes
+// the FPW consecutive faces FPW w .. FPW w + FPW - 1, keeps the previous face flux in registers for
+// the divergence of the cells between them and takes the flux of face FPW (w + 1) from the next
+// warp through shared memory.  Registers are capped at 64 so that 32 / NWARP blocks (32 warps)
+// fit an SM.
+template <int NWARP, int FPW>
 constexpr size_t t_smem() {
-  return sizeof(float) * 6 * (kTFaces * NWARP + 4) * 32 + sizeof(double) * NWARP * 5 * 32;
+  return sizeof(float) * 6 * (FPW * NWARP + 4) * 32 + sizeof(double) * NWARP * 5 * 32;
 }
 
-template <int D, int SCHEME, bool VISC, int NWARP>
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW>
 __global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn in, double* __restrict__ R,
                                                                        Geo g, PhysF pf, int accumulate) {
   static_assert(D == 1 || D == 2, "tiles along y or z");
+  constexpr int kTFaces = FPW;
   constexpr int kTCells = kTFaces * NWARP - 1;
   constexpr int kTWarps = NWARP;
   constexpr int NVW = VISC ? 6 : 5;
@@ -557,24 +557,24 @@ cudaError_t launch_t(const MixedIn& in, double* R, const Geo& g, const PhysF& pf
   return cudaGetLastError();
 }
 
-template <int SCHEME, bool VISC, int NWARP>
+template <int SCHEME, bool VISC, int NWARP, int FPW>
 cudaError_t launch_tile(int D, const MixedIn& in, double* R, const Geo& g, const PhysF& pf,
                         int accumulate, cudaStream_t st) {
-  constexpr int cells = kTFaces * NWARP - 1;
-  constexpr size_t smem = t_smem<NWARP>();
+  constexpr int cells = FPW * NWARP - 1;
+  constexpr size_t smem = t_smem<NWARP, FPW>();
   const int other = D == 1 ? 2 : 1;
   const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + cells - 1) / cells, g.n[other]);
   // a tile may need more than the default 48 KB of dynamic shared memory (attribute is per device)
   if (D == 1) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC, NWARP>,
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC, NWARP, FPW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_face_mixed_t<1, SCHEME, VISC, NWARP><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+    k_face_mixed_t<1, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC, NWARP>,
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC, NWARP, FPW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_face_mixed_t<2, SCHEME, VISC, NWARP><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+    k_face_mixed_t<2, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
   }
   return cudaGetLastError();
 }
@@ -594,9 +594,10 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
     if (D == 1) return launch_t<1, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
     return launch_t<2, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
   }
-  // warps per tile: block 64 -> 2, otherwise 4
-  if (block == 64) return launch_tile<SCHEME, VISC, 2>(D, in, R, g, pf, accumulate, st);
-  return launch_tile<SCHEME, VISC, 4>(D, in, R, g, pf, accumulate, st);
+  // tile shape (warps x faces per warp): block 64 -> 2 x 4, otherwise 4 x 4 (on TGV 128^3 the
+  // 4 x 4 tile was the fastest of 16 x 1, 8 x 2, 4 x 4 and 2 x 4)
+  if (block == 64) return launch_tile<SCHEME, VISC, 2, 4>(D, in, R, g, pf, accumulate, st);
+  return launch_tile<SCHEME, VISC, 4, 4>(D, in, R, g, pf, accumulate, st);
 }
 
 }  // namespace
