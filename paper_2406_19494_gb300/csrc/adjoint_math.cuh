@@ -13,8 +13,11 @@ namespace fl {
 // ------------------------------------------------------------------------------------------------
 // WENO5: cotangent of the five stencil values q_{i-2..i+2} given the cotangent of the face value
 // ------------------------------------------------------------------------------------------------
+// With out != nullptr the face value itself (the forward result, q_i plus the offset form) is
+// returned too; with g_out = 1 gq is the gradient of the face value.
 template <int SCHEME>
-FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]) {
+FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5],
+                     double* out_value = nullptr) {
   // WENO5 is translation-equivariant (f(q - c) = f(q) - c), so its Jacobian is that of the data
   // shifted by the centre value.  Working on the shifted data keeps every intermediate -- in
   // particular the weight cotangents, proportional to C_k - 6 f -- free of the cancellation of
@@ -48,6 +51,7 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   const double N = a0 * C0 + a1 * C1 + a2 * C2;
   const double iS6 = fl_rcp(6.0 * S);
   const double out = N * iS6;
+  if (out_value) *out_value = out + qin[2];
   const double gN = g_out * iS6;
   const double gS = -6.0 * out * gN;                 // -g_out out / S
   const double ga0 = gN * C0 + gS, ga1 = gN * C1 + gS, ga2 = gN * C2 + gS;

@@ -34,8 +34,10 @@ constexpr int kGComp = 4;     // tangential gradient components read by one face
 
 __device__ __forceinline__ int stride_of(const Geo& g, int d) { return d == 0 ? 1 : (d == 1 ? g.sy : g.sz); }
 
+constexpr int kAdjBlock = 64;   // threads per block of k_adj_face (its WENO gradients sit in shared memory)
+
 template <int D, int SCHEME, bool VISC>
-__global__ void __launch_bounds__(128) k_adj_face(const double* __restrict__ W,
+__global__ void __launch_bounds__(kAdjBlock) k_adj_face(const double* __restrict__ W,
                                                   const double* __restrict__ G,
                                                   const double* __restrict__ mu,
                                                   double* __restrict__ CW, double* __restrict__ CG,
@@ -77,7 +79,10 @@ __global__ void __launch_bounds__(128) k_adj_face(const double* __restrict__ W,
       const double mR = inR ? mu[v * nc + cell + s] : 0.0;
       gF[v] = mR * iR - mL * iL;
     }
-    // forward recompute of the reconstruction
+    // the ten reconstructions and their gradients in one pass (the reverse form with a unit
+    // cotangent); the gradients wait in shared memory for the HLLC cotangents
+    __shared__ double sJ[10][5][kAdjBlock];
+    const int tid = threadIdx.x;
     double q[5][6];
 #pragma unroll
     for (int v = 0; v < 5; ++v)
@@ -86,8 +91,15 @@ __global__ void __launch_bounds__(128) k_adj_face(const double* __restrict__ W,
     double wl[5], wr[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      wl[v] = weno5<SCHEME>(q[v][0], q[v][1], q[v][2], q[v][3], q[v][4], ph.eps);
-      wr[v] = weno5<SCHEME>(q[v][5], q[v][4], q[v][3], q[v][2], q[v][1], ph.eps);
+      double J[5];
+      const double ql[5] = {q[v][0], q[v][1], q[v][2], q[v][3], q[v][4]};
+      weno5_vjp<SCHEME>(ql, ph.eps, 1.0, J, &wl[v]);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sJ[2 * v][k][tid] = J[k];
+      const double qr[5] = {q[v][5], q[v][4], q[v][3], q[v][2], q[v][1]};
+      weno5_vjp<SCHEME>(qr, ph.eps, 1.0, J, &wr[v]);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sJ[2 * v + 1][k][tid] = J[k];
     }
     double gwl[5], gwr[5];
     hllc_vjp<D>(wl, wr, ph, gF, gwl, gwr);
@@ -98,15 +110,11 @@ __global__ void __launch_bounds__(128) k_adj_face(const double* __restrict__ W,
       for (int k = 0; k < kSlots; ++k) gcell[v][k] = 0.0;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double gq[5];
-      const double ql[5] = {q[v][0], q[v][1], q[v][2], q[v][3], q[v][4]};
-      weno5_vjp<SCHEME>(ql, ph.eps, gwl[v], gq);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) gcell[v][k] += gq[k];
-      const double qr[5] = {q[v][5], q[v][4], q[v][3], q[v][2], q[v][1]};
-      weno5_vjp<SCHEME>(qr, ph.eps, gwr[v], gq);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) gcell[v][5 - k] += gq[k];
+      for (int k = 0; k < 5; ++k) {
+        gcell[v][k] += gwl[v] * sJ[2 * v][k][tid];
+        gcell[v][5 - k] += gwr[v] * sJ[2 * v + 1][k][tid];
+      }
     }
     if (VISC) {
       double vel[3][4], T[4], gd[3][4], gb[3][4];
@@ -450,7 +458,7 @@ cudaError_t adj_face_t(const double* W, const double* G, const double* mu, doubl
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const long long total = (long long)g.n[A1] * g.n[A2] * (g.n[D] + 1);
-  k_adj_face<D, SCHEME, VISC><<<grid_for(total, 128), 128, 0, st>>>(W, G, mu, CW, CG, g, ph);
+  k_adj_face<D, SCHEME, VISC><<<grid_for(total, kAdjBlock), kAdjBlock, 0, st>>>(W, G, mu, CW, CG, g, ph);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaSuccess;
