@@ -96,3 +96,20 @@ def test_serve_footprint_grows_with_the_grid(lib):
     big = native.config_from_case(wl.tgv_case(64))
     fs, fb = lib.fluid_serve_footprint(ctypes.byref(small)), lib.fluid_serve_footprint(ctypes.byref(big))
     assert 0 < fs < fb and fb > 8 * 38 ** 3 * 30
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the binding raises instead of computing."""
+    monkeypatch.setattr(native, "LIB_PATH", str(tmp_path / "missing" / "libfluid.so"))
+    monkeypatch.setattr(native, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        native.lib()
+
+
+def test_solver_needs_a_cuda_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2406_19494_gb300.solver import Solver
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        Solver(wl.random_box(2, (8, 8, 1)))
