@@ -202,9 +202,12 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
                                           double F[5], double xl[5][3], double k0[5], double k1[5]) {
   // Carried along the march, per primitive: xl, the scaled weights (weno_x) of the left-biased
   // value at this face, whose indicator set (A_{a-1}, B_a, C_{a+1}) was the right-biased set of
-  // the previous face; k0, k1 = weno_k of the stencils centred at a and a+1.  The right-biased
+  // the previous face; k0, k1 = 4 weno_k of the stencils centred at a and a+1.  The right-biased
   // value needs C_{a+2}, B_{a+1}, A_a: one new stencil (centred at a+2) per face.
+  // The indicators are taken times 4 (13/3 t^2 + s^2) with epsilon times 4: the weights of
+  // either scheme are homogeneous in (beta + eps, tau), so the normalised weights are unchanged.
   const int nc = g.ncell;
+  const double eps4 = 4.0 * ph.eps;
   double q[5][6];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
@@ -217,16 +220,16 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
     const double d0 = q[v][1] - q[v][0], d1 = q[v][2] - q[v][1], d2 = q[v][3] - q[v][2];
     const double d3 = q[v][4] - q[v][3], d4 = q[v][5] - q[v][4];
     const double t2 = d4 - d3;
-    const double k2 = k1312 * t2 * t2;                     // weno_k of cells a+1 .. a+3
+    const double k2 = (4.0 * k1312) * t2 * t2;             // 4 weno_k of cells a+1 .. a+3
     const double sA = fma(3.0, d2, -d1);                   // q_{a-1} - 4 q_a + 3 q_{a+1}
     const double sB = d2 + d3;                             // -(q_a - q_{a+2})
     const double sC = fma(-3.0, d3, d4);                   // 3 q_{a+1} - 4 q_{a+2} + q_{a+3}
-    const double An = fma(0.25 * sA, sA, k0[v]);
-    const double Bn = fma(0.25 * sB, sB, k1[v]);
-    const double Cn = fma(0.25 * sC, sC, k2);
+    const double An = fma(sA, sA, k0[v]);                  // 4 A_a
+    const double Bn = fma(sB, sB, k1[v]);                  // 4 B_{a+1}
+    const double Cn = fma(sC, sC, k2);                     // 4 C_{a+2}
     wl[v] = weno_x_value(q[v][2], d0, d1, d2, d3, xl[v]);
     double xr[3];
-    weno_x<SCHEME>(Cn, Bn, An, ph.eps, xr);
+    weno_x<SCHEME>(Cn, Bn, An, eps4, xr);
     // mirrored stencil: centre q_{a+1}, differences -d4, -d3, -d2, -d1
     wr[v] = weno_x_value(q[v][3], -d4, -d3, -d2, -d1, xr);
     xl[v][0] = xr[2];
@@ -270,9 +273,10 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
       const double* f = W + v * nc + cell;
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
-      weno_x<SCHEME>(weno_A(qm2, qm1, q0), weno_B(qm1, q0, qp1), weno_C(q0, qp1, qp2), ph.eps, xl[v]);
-      k0[v] = weno_k(qm1, q0, qp1);
-      k1[v] = weno_k(q0, qp1, qp2);
+      weno_x<SCHEME>(4.0 * weno_A(qm2, qm1, q0), 4.0 * weno_B(qm1, q0, qp1), 4.0 * weno_C(q0, qp1, qp2),
+                     4.0 * ph.eps, xl[v]);
+      k0[v] = 4.0 * weno_k(qm1, q0, qp1);
+      k1[v] = 4.0 * weno_k(q0, qp1, qp2);
     }
     face_flux<D, SCHEME, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, xl, k0, k1);
     for (int a = a0; a < a1; ++a) {
