@@ -84,24 +84,26 @@ FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
   } else {
     const double tau = fabs(b0 - b2);
     const double P = e0 * Q0;
-    const double PP = P * P, tt = tau * tau;
-    X[0] = fma(tt, Q0 * Q0, PP);
-    X[1] = fma(tt, Q1 * Q1, PP);
-    X[2] = fma(tt, Q2 * Q2, PP);
+    const double PP = P * P;
+    const double T0 = tau * Q0, T1 = tau * Q1, T2 = tau * Q2;
+    X[0] = fma(T0, T0, PP);
+    X[1] = fma(T1, T1, PP);
+    X[2] = fma(T2, T2, PP);
   }
 }
 
 // The value from the stencil centre q0 and the four cell differences of the stencil,
 // dm2 = q_{i-1} - q_{i-2}, dm1 = q_i - q_{i-1}, dp0 = q_{i+1} - q_i, dp1 = q_{i+2} - q_{i+1}:
 // with the candidates as offsets from q_i, p0 - q_i = (5 dm1 - 2 dm2) / 6,
-// p1 - q_i = (dm1 + 2 dp0) / 6, p2 - q_i = (4 dp0 - dp1) / 6 (d_k / 6 folded in).
+// p1 - q_i = (dm1 + 2 dp0) / 6, p2 - q_i = (4 dp0 - dp1) / 6 (d_k / 6 folded in, and both sums
+// scaled by 10 so that two coefficients are 1).
 FL_HD double weno_x_value(double q0, double dm2, double dm1, double dp0, double dp1, const double X[3]) {
-  // d = (1/10, 6/10, 3/10)
-  const double C0 = fma(5.0 / 60.0, dm1, (-2.0 / 60.0) * dm2);
-  const double C1 = fma(0.2, dp0, 0.1 * dm1);
-  const double C2 = fma(-0.05, dp1, 0.2 * dp0);
+  // d = (1/10, 6/10, 3/10); numerator and denominator both taken times 10
+  const double C0 = fma(5.0 / 6.0, dm1, (-1.0 / 3.0) * dm2);
+  const double C1 = fma(2.0, dp0, dm1);
+  const double C2 = fma(-0.5, dp1, 2.0 * dp0);
   const double num = fma(X[2], C2, fma(X[1], C1, X[0] * C0));
-  const double den = fma(0.3, X[2], fma(0.6, X[1], 0.1 * X[0]));
+  const double den = fma(3.0, X[2], fma(6.0, X[1], X[0]));
   return fma(num, fl_rcp(den), q0);
 }
 
