@@ -290,10 +290,10 @@ FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double
   double vf[3], Gf[3][3];
   for (int c = 0; c < 3; ++c) {
     vf[c] = interp4(vel[c]);
-    Gf[c][D] = dnorm4(vel[c], mfa);
+    Gf[c][D] = dnorm4(vel[c], mfa * k24th);
   }
   const double Tf = interp4(T);
-  const double dT = dnorm4(T, mfa);
+  const double dT = dnorm4(T, mfa * k24th);
   bool act[3];
   for (int b = 0; b < 3; ++b) {
     act[b] = b != D && b < ndim;

@@ -141,11 +141,13 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const double pirL = pL * irL, pirR = pR * irR;
   const double HL = fma(pirL, gg, 0.5 * q2L), HR = fma(pirR, gg, 0.5 * q2R);
   const double cL = fl_sqrt(ph.gamma * pirL), cR = fl_sqrt(ph.gamma * pirR);
+  // Roe weights sqrt(rho_K) / (sqrt(rho_L) + sqrt(rho_R))
   const double isum = fl_rcp(sL + sR);
-  const double ut0 = (sL * wl[1] + sR * wr[1]) * isum;
-  const double ut1 = (sL * wl[2] + sR * wr[2]) * isum;
-  const double ut2 = (sL * wl[3] + sR * wr[3]) * isum;
-  const double Ht = (sL * HL + sR * HR) * isum;
+  const double aL = sL * isum, aR = sR * isum;
+  const double ut0 = fma(aL, wl[1], aR * wr[1]);
+  const double ut1 = fma(aL, wl[2], aR * wr[2]);
+  const double ut2 = fma(aL, wl[3], aR * wr[3]);
+  const double Ht = fma(aL, HL, aR * HR);
   const double ct = fl_sqrt(ph.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
   const double utn = D == 0 ? ut0 : (D == 1 ? ut1 : ut2);
   const double SL = fmin(unL - cL, utn - ct);
@@ -225,13 +227,14 @@ FL_HD bool wall_map_prim(double w[6], int kind, double Tw, double vw, int a, con
 //   6 points: value (150 (f2 + f3) - 25 (f1 + f4) + 3 (f0 + f5)) / 256,
 //             derivative (2250 (f3 - f2) - 125 (f4 - f1) + 9 (f5 - f0)) / 1920
 // ------------------------------------------------------------------------------------------------
+// the derivatives take m = mfa / 24 (order 4) or mfa / 1920 (order 6), formed once per face
 FL_HD double interp4(const double f[4]) { return (9.0 * (f[1] + f[2]) - (f[0] + f[3])) * k16th; }
-FL_HD double dnorm4(const double f[4], double mfa) { return ((f[0] - f[3]) + 27.0 * (f[2] - f[1])) * k24th * mfa; }
+FL_HD double dnorm4(const double f[4], double m) { return ((f[0] - f[3]) + 27.0 * (f[2] - f[1])) * m; }
 FL_HD double interp6(const double f[6]) {
   return (150.0 * (f[2] + f[3]) - 25.0 * (f[1] + f[4]) + 3.0 * (f[0] + f[5])) * (1.0 / 256.0);
 }
-FL_HD double dnorm6(const double f[6], double mfa) {
-  return (2250.0 * (f[3] - f[2]) - 125.0 * (f[4] - f[1]) + 9.0 * (f[5] - f[0])) * (1.0 / 1920.0) * mfa;
+FL_HD double dnorm6(const double f[6], double m) {
+  return (2250.0 * (f[3] - f[2]) - 125.0 * (f[4] - f[1]) + 9.0 * (f[5] - f[0])) * m;
 }
 template <int NP>
 FL_HD double interp_np(const double f[NP]) {
@@ -247,13 +250,14 @@ FL_HD double dnorm_np(const double f[NP], double mfa) {
 template <int D, int NP = 4>
 FL_HD void visc_face(const double vel[3][NP], const double T[NP], const double gd[3][NP],
                      const double gb[3][NP], int ndim, double mfa, const Phys& ph, double Fd[4]) {
+  const double m = mfa * (NP == 4 ? k24th : 1.0 / 1920.0);
   double vf[3], Gf[3][3];
   for (int c = 0; c < 3; ++c) {
     vf[c] = interp_np<NP>(vel[c]);
-    Gf[c][D] = dnorm_np<NP>(vel[c], mfa);
+    Gf[c][D] = dnorm_np<NP>(vel[c], m);
   }
   const double Tf = interp_np<NP>(T);
-  const double dT = dnorm_np<NP>(T, mfa);
+  const double dT = dnorm_np<NP>(T, m);
   for (int b = 0; b < 3; ++b) {
     if (b == D) continue;
     if (b < ndim) {
