@@ -56,10 +56,10 @@ struct Slot {
 };
 
 struct BucketKey {
-  int ndim, n0, n1, n2, precision, visc, weno;
+  int ndim, n0, n1, n2, precision, visc, weno, visc_order;
   bool operator<(const BucketKey& o) const {
-    return std::tie(ndim, n0, n1, n2, precision, visc, weno) <
-           std::tie(o.ndim, o.n0, o.n1, o.n2, o.precision, o.visc, o.weno);
+    return std::tie(ndim, n0, n1, n2, precision, visc, weno, visc_order) <
+           std::tie(o.ndim, o.n0, o.n1, o.n2, o.precision, o.visc, o.weno, o.visc_order);
   }
 };
 
@@ -125,7 +125,8 @@ struct fluid_server {
   // time the candidate launch shapes of the face kernels on a scratch copy of the state
   void autotune(Slot& s) {
     const fluid_config& c = s.job->cfg;
-    const BucketKey key{c.ndim, c.n[0], c.n[1], c.n[2], c.precision, c.visc_law, c.weno};
+    const BucketKey key{c.ndim, c.n[0], c.n[1], c.n[2], c.precision, c.visc_law, c.weno,
+                        c.visc_order == 6 ? 6 : 4};
     auto it = tuned.find(key);
     if (it == tuned.end()) {
       std::vector<std::pair<int, int>> cand = {{0, 0}, {32, 64}, {64, 16}, {128, 32}};

@@ -73,6 +73,28 @@ def test_results_equal_alone_and_in_the_mix(precision):
         assert np.array_equal(U, ref), (r, np.max(np.abs(U - ref)))
 
 
+def test_channel_scheme_requests_equal_alone_and_in_the_mix():
+    """Requests with the paper's channel scheme (TENO6-A, sixth-order dissipative fluxes, FP64) in
+    a mix with WENO5 requests: each result equals the same solve alone."""
+    from paper_2406_19494_gb300.serve import Server
+    mix = _mix()[:4]
+    teno = []
+    for r, case, U0 in mix:
+        if case["visc"] == "none":
+            case = dict(case, weno="teno6a")
+        else:
+            case = dict(case, weno="teno6a", visc_order=6)
+        teno.append((r, case, U0))
+    jobs = mix[:2] + teno
+    srv = Server(budget_bytes=8e9, max_active=4, chunk_steps=5, graphs=True, autotune=True)
+    tickets = [srv.submit(case, U0, r["nsteps"], precision="fp64") for r, case, U0 in jobs]
+    outs = [srv.poll(t, timeout_ms=120000) for t in tickets]
+    srv.close()
+    for (r, case, U0), (res, U) in zip(jobs, outs):
+        assert res["status"] == 0 and res["steps_done"] == r["nsteps"]
+        assert np.array_equal(U, _alone(case, U0, r["nsteps"], "fp64")), r
+
+
 def test_admission_respects_the_budget():
     from paper_2406_19494_gb300.serve import Server
     mix = _mix()
