@@ -51,6 +51,11 @@ CASES = {
                                          visc="sutherland", t_wall=((1, 1), (2.5, 1), (1, 1)),
                                          porous=dict(axis=1, side=0, begin=4, count=12, A=0.05,
                                                      kappa=3.0, phi0=0.1)),
+    # several x tiles (31 cells) and ragged y / z tiles (15 cells): 40 = 31 + 9, 33 = 2 x 15 + 3
+    "ragged3d_tiles": lambda: wl.random_box(3, (40, 33, 17), visc="sutherland"),
+    "euler3d_minimal_n3": lambda: wl.random_box(3, (3, 3, 3), visc="none"),
+    "ragged2d_xwall": lambda: wl.random_box(2, (37, 5, 1), bc=(("wall", "wall"), P, P),
+                                            t_wall=((2.5, 2.6), (1, 1), (1, 1))),
 }
 
 
