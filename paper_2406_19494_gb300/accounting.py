@@ -68,11 +68,14 @@ def cell_update_bytes(nvar=5, word=8):
 
 
 # ---- mixed FP32-flux / FP64-state face kernel (FLUID_PREC_MIXED) ------------------------------
-# FP64 per cell and axis: 6 cell differences (5 primitives + T), the cell-centre Euler flux (15),
-# adding the FP32 increment (5) and the flux difference (15).  FP32: the WENO5 reconstructions,
-# the HLLC increment in jump form (about 150) and the dissipative flux (90).
+# FP64 per cell and axis: the cell-centre Euler flux from the primitives and the stored
+# H = E + p (rho u_n 1, adding the increment to the mass flux 1, three momentum FMAs 6, the
+# pressure 1, the energy FMA 2) and the flux difference with its scaling and accumulation (15).
+# The cell differences come from the exact FP32 split of the primitives and cost no FP64 work.
+# FP32: the WENO5 reconstructions, the HLLC increment in jump form (about 150) and the
+# dissipative flux (90).
 def mixed_cell_axis_flops64():
-    return 6 + 15 + 5 + 15
+    return 1 + 1 + 6 + 1 + 2 + 15
 
 
 def mixed_cell_axis_flops32(weno="z", visc="power"):
@@ -80,6 +83,7 @@ def mixed_cell_axis_flops32(weno="z", visc="power"):
 
 
 def mixed_face_bytes():
-    """Compulsory bytes of one face-kernel launch per cell: FP64 primitives 6 x 8 read, FP32
-    primitives 6 x 4 read, FP32 tangential gradients 4 x 4 read, R read and written 2 x 40."""
-    return 48 + 24 + 16 + 80
+    """Compulsory bytes of one face-kernel launch per cell: FP64 primitives and H 6 x 8 read, the
+    FP32 (hi, lo) split of 6 primitives 12 x 4 read, FP32 tangential gradients 4 x 4 read, R read
+    and written 2 x 40."""
+    return 48 + 48 + 16 + 80
