@@ -12,6 +12,7 @@ by torch.distributed.run) every rank advances its own independent replica of the
 `--impl reference` times the CPU oracle on a bounded sample of the same workload instead.
 """
 import argparse
+import datetime
 import json
 import math
 import os
@@ -80,23 +81,33 @@ def whole_job_rate(cells, steps, ranks, ms):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the warm-up (the tool
+    takes longer to start than a short timed region lasts); the summary keeps the samples whose
+    timestamps fall inside the host-side window of the timed region (mark_start / mark_end)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
+        self.t0 = self.t1 = None
+        self.out = ""
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
         self.out = ""
@@ -108,22 +119,43 @@ class ClockSampler:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
 
-    def summary(self):
+    def _rows(self):
         rows = []
         for line in (self.out or "").strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                rows.append(f)
-        if not rows:
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                continue
+            rows.append((ts, f[1:]))
+        return rows
+
+    def summary(self):
+        rows = self._rows()
+        window = "timed region"
+        if self.t0 is not None and self.t1 is not None:
+            slack = datetime.timedelta(milliseconds=60)
+            inside = [r for ts, r in rows if self.t0 - slack <= ts <= self.t1 + slack]
+        else:
+            inside = [r for _, r in rows]
+        if not inside and rows:
+            # a region shorter than the sampling interval: the samples nearest to it
+            mid = self.t0 + (self.t1 - self.t0) / 2 if self.t0 and self.t1 else rows[-1][0]
+            inside = [min(rows, key=lambda tr: abs(tr[0] - mid))[1]]
+            window = "nearest sample to the timed region"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = [float(r[1]) for r in inside if num(r[1])]
+        mx = [float(r[2]) for r in inside if num(r[2])]
+        pw = [float(r[3]) for r in inside if num(r[3])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
-                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+                "reasons": reasons, "samples": len(inside), "window": window,
+                "power_w_max": max(pw) if pw else None}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -131,6 +163,9 @@ def timed_steps(s, U, steps, warmup, flush, stream, clock_gpu=None):
     """Warm up, then time `steps` RK3 steps with CUDA events (L2 flushed before each) while the
     library's event profiler records every kernel; returns (total ms, per-kernel profile, clocks)."""
     import torch
+    clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
+    if clk:
+        clk.__enter__()
     for _ in range(warmup):
         s.step(U, 1)
     s.check()
@@ -139,9 +174,8 @@ def timed_steps(s, U, steps, warmup, flush, stream, clock_gpu=None):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     s.profile(True)
     s.profile_read(reset=True)
-    clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
     if clk:
-        clk.__enter__()
+        clk.mark_start()
     for k in range(steps):
         flush.fill_(float(k))
         starts[k].record(stream)
@@ -149,11 +183,29 @@ def timed_steps(s, U, steps, warmup, flush, stream, clock_gpu=None):
         ends[k].record(stream)
     torch.cuda.synchronize()
     if clk:
+        clk.mark_end()
         clk.__exit__(None, None, None)
     prof = s.profile_read(reset=True)
     s.profile(False)
     s.check()
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), prof, clk
+
+
+def one_call_ms(s, U, steps, flush, stream):
+    """ms per step of one fluid_step call of `steps` steps (the way a run advances), after one
+    warm-up call; L2 flushed once before the timed call (the working set of a step exceeds L2)."""
+    import torch
+    s.step(U, steps)
+    s.check()
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.step(U, steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    s.check()
+    return a.elapsed_time(b) / steps
 
 
 def run_fluid(args):
@@ -195,6 +247,15 @@ def run_fluid(args):
     mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
     mixed_ms = max_over_ranks(mixed_ms, "cuda")
     mixed_err = mixed_vs_fp64(s, sm, U, Um, case, args.warmup + args.steps)
+    one_call = None
+    if ws == 1:
+        Uc = U0.clone()
+        one_call = {"fp64_ms_per_step": one_call_ms(s, Uc, args.steps, flush, stream)}
+        Uc.copy_(U0)
+        one_call["mixed_ms_per_step"] = one_call_ms(sm, Uc, args.steps, flush, stream)
+        one_call["note"] = ("K steps in one fluid_step call after a warm-up call of K; L2 flushed "
+                            "once before the call, the working set of a step (~0.5 GB) exceeds L2")
+        del Uc
 
     # ---- the paper's channel scheme (TENO6-A + sixth-order central, FP64) ------------------------
     teno = measure_teno(flush, stream, args) if not args.no_teno and ws == 1 else None
@@ -283,6 +344,7 @@ def run_fluid(args):
         "adjoint": adjoint,
         "serving": serving,
         "clocks": clk.summary(),
+        "steps_in_one_call": one_call,
         "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
                   "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
     }

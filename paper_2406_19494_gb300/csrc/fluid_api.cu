@@ -285,6 +285,15 @@ int stage_into(fluid_solver* s, int stage, const double* Un, const double* Us, d
   return FLUID_OK;
 }
 
+// stage_into followed by the primitives of Ud (what rhs_into(Ud) computes first)
+int stage_prim_into(fluid_solver* s, int stage, const double* Un, const double* Us, double* Ud,
+                    double t_end, cudaStream_t st) {
+  FL_TIMED(s, FLUID_KERNEL_STAGE, st,
+           fl::launch_stage_prim(stage, Un, Us, s->R, Ud, s->W, s->W32, s->geo, s->ph, s->bc,
+                                 s->ctl, t_end, st));
+  return FLUID_OK;
+}
+
 // (dR/dX)^T mu on the interior into gX; (dR/dphi)^T mu added to gphi when given
 int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, double* gphi,
             cudaStream_t st) {
@@ -623,18 +632,26 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
   if (int r = check_ptr(s, U_dev, "U_dev")) return r;
   if (nsteps < 0) return fail(s, FLUID_EINVAL, "nsteps < 0");
   cudaStream_t st = as_stream(stream);
+  // Each stage's combination also writes the primitives of its result (stage_prim_into), so the
+  // next right-hand side starts at its gradients; only the first step of a call converts U here,
+  // and the call's last stage, whose primitives nothing reads, is the plain combination.
+  if (nsteps > 0)
+    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
   for (int k = 0; k < nsteps; ++k) {
     // stage 1: U1 = Un + dt R(Un) into A; dt from the primitives of Un
-    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
     if (int r = dt_into(s, nullptr, 1, t_end, st)) return r;
     if (int r = grad_faces(s, s->R, st)) return r;
-    if (int r = stage_into(s, 1, U_dev, U_dev, s->A, t_end, st)) return r;
+    if (int r = stage_prim_into(s, 1, U_dev, U_dev, s->A, t_end, st)) return r;
     // stage 2: U2 = 3/4 Un + 1/4 (U1 + dt R(U1)) into A
-    if (int r = rhs_into(s, s->A, s->R, st)) return r;
-    if (int r = stage_into(s, 2, U_dev, s->A, s->A, t_end, st)) return r;
+    if (int r = grad_faces(s, s->R, st)) return r;
+    if (int r = stage_prim_into(s, 2, U_dev, s->A, s->A, t_end, st)) return r;
     // stage 3: Un+1 = 1/3 Un + 2/3 (U2 + dt R(U2)) into U
-    if (int r = rhs_into(s, s->A, s->R, st)) return r;
-    if (int r = stage_into(s, 3, U_dev, s->A, U_dev, t_end, st)) return r;
+    if (int r = grad_faces(s, s->R, st)) return r;
+    if (k + 1 < nsteps) {
+      if (int r = stage_prim_into(s, 3, U_dev, s->A, U_dev, t_end, st)) return r;
+    } else if (int r = stage_into(s, 3, U_dev, s->A, U_dev, t_end, st)) {
+      return r;
+    }
   }
   return FLUID_OK;
 }

@@ -97,6 +97,11 @@ cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& 
 cudaError_t launch_stage(int stage, const double* Un, const double* Us, const double* R, double* Ud,
                          const double* W, const Geo& g, const Phys& ph, Ctl* ctl, double t_end,
                          cudaStream_t st, double dt_arg = 0.0);
+// stage `stage` of RK3 into Ud with the solver's dt, then the primitives of Ud into W (and W32 / H
+// when W32 is given) for every padded cell, equal to launch_prim_bc(Ud, ...) on the result
+cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, const double* R,
+                              double* Ud, double* W, float* W32, const Geo& g, const Phys& ph,
+                              const BC& bc, Ctl* ctl, double t_end, cudaStream_t st);
 cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, double* partial,
                               int nparts, cudaStream_t st);
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,

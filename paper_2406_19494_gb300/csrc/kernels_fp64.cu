@@ -12,6 +12,9 @@
 //               One thread marches along a segment of a grid line so each face is computed once
 //               and reused by the two cells that share it.
 //   k_source / k_stage   body-force source, RK3 stage combination, non-finite check
+//   k_stage_prim / k_halo_prim   the stage combination fused with the primitives of its result
+//               (interior cells), then the halo cells from those; fluid_step uses this pair in
+//               place of k_stage followed by the next right-hand side's k_prim_bc
 //   k_dt_*      CFL time step: per-block minimum, then one block reduces (deterministic)
 //
 // The state is FP64 structure-of-arrays U[v][z][y][x]; primitives and gradients live in solver
@@ -72,11 +75,10 @@ __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a
 // state by its profile).  Every cell therefore converts exactly one cell's U -- its own or its
 // source -- and only wall halos run map arithmetic, so warps that straddle the x halo do not run
 // the conversion twice.
-__device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const int own[3], int cell,
-                                          const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
-                                          double w[NW], double& E) {
-  bool ghost[3];
-  int side[3], src[3];
+// Source cell of padded cell own[]: ghost[a] / side[a] / src[a] per axis; returns whether any axis
+// is a halo axis (then src[] is the interior cell the halo maps start from).
+__device__ __forceinline__ bool halo_source(const int own[3], const Geo& g, const BC& bc,
+                                            bool ghost[3], int side[3], int src[3]) {
   bool any = false;
   for (int a = 0; a < 3; ++a) {
     ghost[a] = own[a] < g.h[a] || own[a] >= g.h[a] + g.n[a];
@@ -84,12 +86,13 @@ __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const in
     src[a] = ghost[a] ? bc_source(bc.kind[a][side[a]], side[a], own[a], g.n[a], g.h[a]) : own[a];
     any |= ghost[a];
   }
-  const int scell = any ? src[0] + src[1] * g.sy + src[2] * g.sz : cell;
-  prim_of(U, scell, g.ncell, ph, w);
-  if (!any) {
-    E = U[4 * g.ncell + cell];
-    return false;
-  }
+  return any;
+}
+
+// the maps of the halo axes of a cell, in axis order, applied to the primitives w of its source
+__device__ __forceinline__ void halo_maps(const int own[3], const bool ghost[3], const int side[3],
+                                          const int src[3], const Geo& g, const Phys& ph,
+                                          const BC& bc, Ctl* ctl, double w[NW]) {
   for (int a = 0; a < 3; ++a) {
     if (!ghost[a]) continue;
     const int kind = bc.kind[a][side[a]];
@@ -104,6 +107,30 @@ __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const in
     if (kind == FLUID_BC_POROUS) vw = bc.vw[c[bc.porous_t1]];
     wall_map(w, kind, bc.Tw[a][side[a]], vw, a, ph, &ctl->flags);
   }
+}
+
+// primitives of padded cell own[] (interior: from U; halo: composed boundary maps); E receives the
+// total energy per volume of interior cells (halo cells leave it unset).
+//
+// The halo passes x -> y -> z compose: the pass of axis a sees own indices on the axes before it
+// and source indices on the axes after it, so a halo cell starts from the cell at the source index
+// on every axis and then takes the maps of its halo axes in order (an inflow axis replaces the
+// state by its profile).  Every cell therefore converts exactly one cell's U -- its own or its
+// source -- and only wall halos run map arithmetic, so warps that straddle the x halo do not run
+// the conversion twice.
+__device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const int own[3], int cell,
+                                          const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
+                                          double w[NW], double& E) {
+  bool ghost[3];
+  int side[3], src[3];
+  const bool any = halo_source(own, g, bc, ghost, side, src);
+  const int scell = any ? src[0] + src[1] * g.sy + src[2] * g.sz : cell;
+  prim_of(U, scell, g.ncell, ph, w);
+  if (!any) {
+    E = U[4 * g.ncell + cell];
+    return false;
+  }
+  halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
   return true;
 }
 
@@ -361,6 +388,125 @@ __global__ void k_stage(int stage, const double* Un, const double* Us, const dou
   if (bad) atomicOr(&ctl->flags, FLAG_NONFINITE);
 }
 
+// One RK3 stage fused with the primitives of its result (the next right-hand side's first pass):
+// interior cell c gets Ud = the stage combination of k_stage, and W (and for MIXED the W32 split and
+// H) from Ud by the same conversion k_prim_bc applies, so the halo cells (k_halo_prim, next) and
+// the following kernels see exactly what k_prim_bc would have produced.  W is read (body-force
+// velocities of the stage's input state) and rewritten only at the thread's own cell.  A third
+// stage with dt <= 0 leaves Un unwritten and converts it as it is.
+template <bool MIXED>
+__global__ void k_stage_prim(int stage, const double* Un, const double* Us, const double* __restrict__ R,
+                             double* Ud, double* W, float* __restrict__ W32, Geo g, Phys ph, Ctl* ctl,
+                             double t_end) {
+  const double dt = ctl->dt;
+  const bool hold = stage == 3 && !(dt > 0.0);
+  if (stage == 3 && !hold && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+    const double tn = ctl->t + dt;
+    ctl->t = (t_end > 0.0 && !(tn < t_end)) ? t_end : tn;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n[0]) return;
+  const int nc = g.ncell;
+  bool bad = false;
+  for (int k = blockIdx.z; k < g.n[2]; k += gridDim.z)
+    for (int j = blockIdx.y; j < g.n[1]; j += gridDim.y) {
+      const int c = (i + g.h[0]) + (j + g.h[1]) * g.sy + (k + g.h[2]) * g.sz;
+      double u[5];
+      if (hold) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = Un[v * nc + c];
+      } else {
+        double r[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) r[v] = R[v * nc + c];
+        if (ph.has_force) {
+          const double uu = W[nc + c], vv = W[2 * nc + c], ww = W[3 * nc + c];
+          r[1] += ph.f[0];
+          r[2] += ph.f[1];
+          r[3] += ph.f[2];
+          r[4] += ph.f[0] * uu + ph.f[1] * vv + ph.f[2] * ww;
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double un = Un[v * nc + c];
+          double out;
+          if (stage == 1) {
+            out = un + dt * r[v];
+          } else {
+            const double us = Us[v * nc + c];
+            out = stage == 2 ? 0.75 * un + 0.25 * (us + dt * r[v])
+                             : (1.0 / 3.0) * un + (2.0 / 3.0) * (us + dt * r[v]);
+          }
+          bad |= !finite_bits(out);
+          Ud[v * nc + c] = out;
+          u[v] = out;
+        }
+      }
+      double w[NW];
+      prim_from_cons(u, ph, w);
+#pragma unroll
+      for (int v = 0; v < NW; ++v) W[v * nc + c] = w[v];
+      if (MIXED) {
+#pragma unroll
+        for (int v = 0; v < NW; ++v) split_hi_lo(w[v], W32[v * nc + c], W32[(NW + v) * nc + c]);
+        W[NW * nc + c] = u[4] + w[4];
+      }
+    }
+  if (bad) atomicOr(&ctl->flags, FLAG_NONFINITE);
+}
+
+// Halo cells only, from the interior primitives already in W: the maps of k_prim_bc applied to the
+// source cell's primitives.  Cells are enumerated by their highest halo axis a: axes above a
+// interior, axis a one of its 2 h[a] halo layers, axes below a anywhere in the padded range.
+template <bool MIXED>
+__global__ void k_halo_prim(double* __restrict__ W, float* __restrict__ W32, Geo g, Phys ph, BC bc,
+                            Ctl* ctl, long long total) {
+  const int nc = g.ncell;
+  for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < total;
+       t0 += (long long)gridDim.x * blockDim.x) {
+    long long t = t0;
+    int own[3] = {0, 0, 0};
+    for (int a = 2; a >= 0; --a) {
+      long long cnt = 2LL * g.h[a];
+      for (int b = 0; b < 3; ++b)
+        if (b != a) cnt *= b < a ? g.p[b] : g.n[b];
+      if (t >= cnt) {
+        t -= cnt;
+        continue;
+      }
+      for (int b = 0; b < a; ++b) {
+        own[b] = (int)(t % g.p[b]);
+        t /= g.p[b];
+      }
+      const int l = (int)(t % (2 * g.h[a]));
+      t /= 2 * g.h[a];
+      own[a] = l < g.h[a] ? l : g.n[a] + l;
+      for (int b = a + 1; b < 3; ++b) {
+        own[b] = g.h[b] + (int)(t % g.n[b]);
+        t /= g.n[b];
+      }
+      break;
+    }
+    bool ghost[3];
+    int side[3], src[3];
+    halo_source(own, g, bc, ghost, side, src);
+    const int scell = src[0] + src[1] * g.sy + src[2] * g.sz;
+    const int cell = own[0] + own[1] * g.sy + own[2] * g.sz;
+    double w[NW];
+#pragma unroll
+    for (int v = 0; v < NW; ++v) w[v] = W[v * nc + scell];
+    halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
+#pragma unroll
+    for (int v = 0; v < NW; ++v) W[v * nc + cell] = w[v];
+    if (MIXED) {
+#pragma unroll
+      for (int v = 0; v < NW; ++v) split_hi_lo(w[v], W32[v * nc + cell], W32[(NW + v) * nc + cell]);
+      const double E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+      W[NW * nc + cell] = E + w[4];
+    }
+  }
+}
+
 constexpr int kDtBlock = 256;
 
 // CFL: dt = cfl * min over cells and axes of dx / (|u| + c) and dx^2 / (k nu), taken as
@@ -529,6 +675,25 @@ cudaError_t launch_stage(int stage, const double* Un, const double* Us, const do
                          cudaStream_t st, double dt_arg) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
   k_stage<<<grid_for(total, 256), 256, 0, st>>>(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end, dt_arg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, const double* R,
+                              double* Ud, double* W, float* W32, const Geo& g, const Phys& ph,
+                              const BC& bc, Ctl* ctl, double t_end, cudaStream_t st) {
+  // interior rows in nb near-equal chunks of whole warps, at most 256 threads each
+  const int nb = (g.n[0] + 255) / 256;
+  const int block = ((g.n[0] + nb - 1) / nb + 31) / 32 * 32;
+  const dim3 grid((g.n[0] + block - 1) / block, g.n[1] < 65535 ? g.n[1] : 65535,
+                  g.n[2] < 65535 ? g.n[2] : 65535);
+  if (W32) k_stage_prim<true><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
+  else k_stage_prim<false><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)g.p[0] * g.p[1] * g.p[2] - (long long)g.n[0] * g.n[1] * g.n[2];
+  if (total <= 0) return cudaSuccess;
+  if (W32) k_halo_prim<true><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total);
+  else k_halo_prim<false><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total);
   return cudaGetLastError();
 }
 

@@ -155,6 +155,49 @@ def test_step_parity(name):
     assert max(rel_err(Ud.cpu().numpy()[inner], U2[inner])) <= TOL
 
 
+def _solver_with_bcs(c, phi, inflow, precision):
+    from paper_2406_19494_gb300.solver import Solver as S
+    s = S(c, precision=precision)
+    if phi is not None:
+        s.set_wall_params(torch.from_numpy(phi).cuda())
+    for (a, side), prof in inflow.items():
+        s.set_inflow(a, side, torch.from_numpy(np.ascontiguousarray(prof)).cuda())
+    return s
+
+
+def steps_in_one_call_vs_single_calls(c, U, phi, inflow, nsteps, precision="fp64", t_end=0.0):
+    """(state, time) after one fluid_step call of nsteps and after nsteps calls of one step."""
+    out = []
+    for calls, per_call in ((1, nsteps), (nsteps, 1)):
+        s = _solver_with_bcs(c, phi, inflow, precision)
+        Ud = torch.from_numpy(U).cuda()
+        for _ in range(calls):
+            s.step(Ud, per_call, t_end=t_end)
+        s.check()
+        out.append((Ud.cpu().numpy(), s.time()))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", [n for n in CASES if n != "sod1d"])
+def test_multi_step_call_equals_single_step_calls(name, precision):
+    """Within one fluid_step call each RK3 stage writes the primitives of its result together with
+    the result, and the next right-hand side starts from them; a single-step call converts U with
+    the primitive kernel instead.  Both must give the same bits, halo cells and all boundary kinds
+    included."""
+    c, case, grid, U, phi, inflow = setup_case(name, seed=5)
+    (Ua, ta), (Ub, tb) = steps_in_one_call_vs_single_calls(c, U, phi, inflow, 3, precision)
+    assert np.array_equal(Ua, Ub) and ta == tb
+
+
+def test_multi_step_call_past_t_end_equals_single_step_calls():
+    """Sod past t = 0.2 in one call and in single-step calls: the steps after the clipped one have
+    dt = 0 and leave the state as it is, in both."""
+    c, case, grid, U, _, _ = setup_case("sod1d")
+    (Ua, ta), (Ub, tb) = steps_in_one_call_vs_single_calls(c, U, None, {}, 180, t_end=0.2)
+    assert np.array_equal(Ua, Ub) and ta == tb and ta[0] == 0.2
+
+
 def test_sod_run_to_t02():
     """Whole Sod run to t = 0.2 (175 steps, last step clipped): same number of steps, same final
     time, and per-step parity at several points of the trajectory."""

@@ -164,3 +164,13 @@ def test_channel_full_size_teno_sampled():
     xs = [grid.axes[a].xc[3:-3] for a in range(3)]
     W = wl.channel_prims(c, *xs, seed=5)
     _sampled_rhs_check(c, W, margin=0)
+
+
+@pytest.mark.parametrize("name", ["channel3d_teno_visc6", "bl2d_teno_visc6_porous_inflow"])
+def test_multi_step_call_equals_single_step_calls(name):
+    """The fused stage-and-primitives pass of a multi-step call gives the bits of single-step calls
+    with the channel scheme too."""
+    from test_gpu_parity import steps_in_one_call_vs_single_calls
+    c, case, grid, U, phi, inflow = setup_case(name, seed=4)
+    (Ua, ta), (Ub, tb) = steps_in_one_call_vs_single_calls(c, U, phi, inflow, 3)
+    assert np.array_equal(Ua, Ub) and ta == tb
