@@ -24,7 +24,8 @@ namespace {
 template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
-                                               double F[5], double eta[5][3], double b3[5][3]) {
+                                               double F[5], double eta[5][3], double b3[5][3],
+                                               const double (*omega)[16]) {
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -37,7 +38,7 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
     // cells a-2 .. a+3 are q[v][0..5]; the sensor of cell a+2 is the new one
     const double e3 = teno::sensor(q[v][4] - q[v][3], q[v][5] - q[v][4]);
     const double ct = teno::cutoff(fmin(fmin(eta[v][0], eta[v][1]), fmin(eta[v][2], e3)));
-    teno::face_states(q[v], ct, b3[v], wl[v], wr[v]);
+    teno::face_states(q[v], ct, b3[v], omega, wl[v], wr[v]);
     eta[v][0] = eta[v][1];
     eta[v][1] = eta[v][2];
     eta[v][2] = e3;
@@ -66,6 +67,11 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
   const long long total = (long long)n1 * n2 * nseg;
   const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
   const int nc = g.ncell;
+  // normalised weights per keep mask, k-major: for each k the 16 masks' weights sit in distinct
+  // pairs of banks, so lanes reading different masks do not conflict
+  __shared__ double omega[4][16];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) teno::weight_entry(i, omega);
+  __syncthreads();
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i1 = (int)(t % n1);
@@ -94,10 +100,10 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       b3[v][1] = weno_C(q0, qp1, qp2);
       b3[v][2] = weno_A(qm2, qm1, q0);
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3, omega);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3, omega);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

@@ -29,18 +29,32 @@ FL_HD double sensor(double dm, double dp) {
   return (2.0 * fabs(dp * dm) + kSensorE) * fl_rcp(fma(dp, dp, fma(dm, dm, kSensorE)));
 }
 
-// cut-off C_T from the smallest sensor of the stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5)
+// cut-off C_T from the smallest sensor of the stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5):
+// 10^-floor(alpha1 - alpha2 (1 - g(m))) is a step function of eta with the thresholds kCutEta*
+// (teno_coeffs.cuh), since g grows with eta
 FL_HD double cutoff(double eta) {
-  const double m = 1.0 - fmin(1.0, 4.0 * eta);
-  const double t = 1.0 - m, t2 = t * t;
-  const double g = t2 * t2 * (1.0 + 4.0 * m);
-  const double bb = 10.5 - 3.5 * (1.0 - g);          // in [7, 10.5]
-  return bb >= 10.0 ? 1e-10 : (bb >= 9.0 ? 1e-9 : (bb >= 8.0 ? 1e-8 : 1e-7));
+  return eta >= kCutEta10 ? 1e-10 : (eta >= kCutEta9 ? 1e-9 : (eta >= kCutEta8 ? 1e-8 : 1e-7));
 }
 
-// TENO6 weights and value from the candidates p_k and smoothness measures b_k (beta6 = b6)
+// linear weights d_k = (9/20, 3/10, 1/20, 1/5) (sixth-order combination of the four candidates)
+FL_HD double lin_weight(int k) { return k == 0 ? 0.45 : (k == 1 ? 0.3 : (k == 2 ? 0.05 : 0.2)); }
+
+// Normalised weights of the kept stencils for each keep mask (bit k set: stencil k kept):
+// omega[k][mask] = d_k / sum of the kept d_j, 0 for a cut stencil (mask 0 cannot occur: the
+// largest gamma_k / sum gamma is at least 1/4).  Entry i of the 64 is written by call i.
+FL_HD void weight_entry(int i, double omega[4][16]) {
+  const int k = i >> 4, mask = i & 15;
+  double den = 0.0;
+  for (int j = 0; j < 4; ++j)
+    if ((mask >> j) & 1) den += lin_weight(j);
+  omega[k][mask] = ((mask >> k) & 1) ? lin_weight(k) / den : 0.0;
+}
+
+// TENO6 value from the candidates p_k and smoothness measures b_k (beta6 = b6): stencil k is kept
+// unless gamma_k / sum gamma < C_T, and the value is the kept candidates' combination with the
+// normalised weights of omega (weight_entry)
 FL_HD double combine(double p0, double p1, double p2, double p3, double b0, double b1, double b2,
-                     double b3, double b6, double ct) {
+                     double b3, double b6, double ct, const double (*omega)[16]) {
   const double tau = fabs(b6 - (b1 + b2 + 4.0 * b0) * kSixth);
   double g[4];
   const double bk[4] = {b0, b1, b2, b3};
@@ -51,25 +65,8 @@ FL_HD double combine(double p0, double p1, double p2, double p3, double b0, doub
     g[k] = x2 * x2 * x2;
   }
   const double thr = ct * ((g[0] + g[1]) + (g[2] + g[3]));
-  // kept unless gamma_k / sum gamma < C_T
-  const double w0 = g[0] < thr ? 0.0 : 0.45;
-  const double w1 = g[1] < thr ? 0.0 : 0.3;
-  const double w2 = g[2] < thr ? 0.0 : 0.05;
-  const double w3 = g[3] < thr ? 0.0 : 0.2;
-  const double num = fma(w3, p3, fma(w2, p2, fma(w1, p1, w0 * p0)));
-  return num * fl_rcp((w0 + w1) + (w2 + w3));
-}
-
-// left-biased value at i+1/2 from q0 .. q5 = q_{i-2} .. q_{i+3} with cut-off ct
-FL_HD double value(double q0, double q1, double q2, double q3, double q4, double q5, double ct) {
-  const double p0 = fma(2.0, q3, fma(5.0, q2, -q1)) * kSixth;
-  const double p1 = fma(-1.0, q4, fma(5.0, q3, 2.0 * q2)) * kSixth;
-  const double p2 = fma(11.0, q2, fma(-7.0, q1, 2.0 * q0)) * kSixth;
-  const double p3 = fma(1.0, q5, fma(-5.0, q4, fma(13.0, q3, 3.0 * q2))) * (1.0 / 12.0);
-  const double e4[3] = {q3 - q2, q4 - q2, q5 - q2};
-  const double e6[5] = {q1 - q0, q2 - q0, q3 - q0, q4 - q0, q5 - q0};
-  return combine(p0, p1, p2, p3, weno_B(q1, q2, q3), weno_C(q2, q3, q4), weno_A(q0, q1, q2),
-                 beta4_form(e4), beta6_form(e6), ct);
+  const int mask = (g[0] < thr ? 0 : 1) | (g[1] < thr ? 0 : 2) | (g[2] < thr ? 0 : 4) | (g[3] < thr ? 0 : 8);
+  return fma(omega[3][mask], p3, fma(omega[2][mask], p2, fma(omega[1][mask], p1, omega[0][mask] * p0)));
 }
 
 // Both states of the face a+1/2 from q[0..5] = q_{a-2} .. q_{a+3} while marching along +D.
@@ -79,23 +76,25 @@ FL_HD double value(double q0, double q1, double q2, double q3, double q4, double
 //     the next face's left-state measures (B at a+1, C at a+2, A at a): b3c carries them as
 //     (beta0, beta1, beta2) of that next left state.
 // On entry b3c holds this face's left-state (beta0, beta1, beta2); on exit the next face's.
-FL_HD void face_states(const double q[6], double ct, double b3c[3], double& wl, double& wr) {
+FL_HD void face_states(const double q[6], double ct, double b3c[3], const double (*omega)[16],
+                       double& wl, double& wr) {
   const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1])) * kSixth;       // cells a-1..a+1
   const double pd = fma(-1.0, q[4], fma(5.0, q[3], 2.0 * q[2])) * kSixth;  // cells a..a+2
   const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0])) * kSixth;
   const double p4 = fma(1.0, q[5], fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]))) * (1.0 / 12.0);
   const double e4[3] = {q[3] - q[2], q[4] - q[2], q[5] - q[2]};
-  const double e6[5] = {q[1] - q[0], q[2] - q[0], q[3] - q[0], q[4] - q[0], q[5] - q[0]};
-  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), beta6_form(e6), ct);
+  // beta6 of the window and of its mirror image together (the reversal negates the odd part)
+  double b6l, b6r;
+  beta6_pair(q, b6l, b6r);
+  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), b6l, ct, omega);
   // right state: the mirrored stencil q'_j = q[5 - j]
   const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5])) * kSixth;
   const double r4 = fma(1.0, q[0], fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]))) * (1.0 / 12.0);
   const double f4[3] = {q[2] - q[3], q[1] - q[3], q[0] - q[3]};
-  const double f6[5] = {q[4] - q[5], q[3] - q[5], q[2] - q[5], q[1] - q[5], q[0] - q[5]};
   const double rb0 = weno_B(q[4], q[3], q[2]);
   const double rb1 = weno_C(q[3], q[2], q[1]);
   const double rb2 = weno_A(q[5], q[4], q[3]);
-  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, beta4_form(f4), beta6_form(f6), ct);
+  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, beta4_form(f4), b6r, ct, omega);
   // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at a (rb1's)
   b3c[0] = rb0;
   b3c[1] = rb2;

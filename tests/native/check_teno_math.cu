@@ -1,0 +1,24 @@
+// Host build of the TENO6-A face arithmetic of the FP64 kernels (teno_math.cuh and the generated
+// teno_coeffs.cuh), for a CPU check against the oracle: reads six-cell windows q[0..5] from stdin,
+// forms the cut-off from the sensors of cells 1..4 as the face kernel does, and prints the left-
+// and right-biased states of the face between cells 2 and 3.
+#include <cmath>
+#include <cstdio>
+
+#include "../../paper_2406_19494_gb300/csrc/teno_math.cuh"
+
+int main() {
+  double omega[4][16];
+  for (int i = 0; i < 64; ++i) fl::teno::weight_entry(i, omega);
+  double q[6];
+  while (std::scanf("%lf %lf %lf %lf %lf %lf", q, q + 1, q + 2, q + 3, q + 4, q + 5) == 6) {
+    double eta = HUGE_VAL;
+    for (int j = 1; j <= 4; ++j) eta = std::fmin(eta, fl::teno::sensor(q[j] - q[j - 1], q[j + 1] - q[j]));
+    const double ct = fl::teno::cutoff(eta);
+    double b3c[3] = {fl::weno_B(q[1], q[2], q[3]), fl::weno_C(q[2], q[3], q[4]), fl::weno_A(q[0], q[1], q[2])};
+    double wl, wr;
+    fl::teno::face_states(q, ct, b3c, omega, wl, wr);
+    std::printf("%.17g %.17g %.17g\n", wl, wr, ct);
+  }
+  return 0;
+}
