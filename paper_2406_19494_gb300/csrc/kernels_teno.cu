@@ -25,7 +25,7 @@ template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
                                                double F[5], double eta[5][3], double b3[5][3],
-                                               const double (*omega)[16]) {
+                                               double kk[5][2], const double (*omega)[16]) {
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -38,7 +38,7 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
     // cells a-2 .. a+3 are q[v][0..5]; the sensor of cell a+2 is the new one
     const double e3 = teno::sensor(q[v][4] - q[v][3], q[v][5] - q[v][4]);
     const double ct = teno::cutoff(fmin(fmin(eta[v][0], eta[v][1]), fmin(eta[v][2], e3)));
-    teno::face_states(q[v], ct, b3[v], omega, wl[v], wr[v]);
+    teno::face_states(q[v], ct, b3[v], kk[v], omega, wl[v], wr[v]);
     eta[v][0] = eta[v][1];
     eta[v][1] = eta[v][2];
     eta[v][2] = e3;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], eta[5][3], b3[5][3];
+    double Fp[5], F[5], eta[5][3], b3[5][3], kk[5][2];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       // sensors of cells a0-2, a0-1, a0 and the left-state three-cell measures of the first face
@@ -99,11 +99,15 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       b3[v][0] = weno_B(qm1, q0, qp1);
       b3[v][1] = weno_C(q0, qp1, qp2);
       b3[v][2] = weno_A(qm2, qm1, q0);
+      // 13/12 t^2 of the three-cell stencils centred at a0-1 and a0
+      const double ta = fma(-2.0, q0, qm1) + qp1, tb = fma(-2.0, qp1, q0) + qp2;
+      kk[v][0] = k1312 * ta * ta;
+      kk[v][1] = k1312 * tb * tb;
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3, omega);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3, kk, omega);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3, omega);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3, kk, omega);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

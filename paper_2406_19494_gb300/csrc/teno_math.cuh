@@ -24,9 +24,24 @@ namespace teno {
 constexpr double kEps = 1e-40;
 constexpr double kSensorE = 0.9 * 0.25 * 1e-6 / 0.75;
 
+// 1/y for the quantities that only decide the cut-off (the sensors and gamma_k): one
+// second-order Newton step from the hardware estimate of rcp.approx.ftz.f64, relative error the
+// square of the estimate's (about 2^-34 or smaller; the third-order fl_rcp squares it once more).
+// A decision can differ from exact division only where its quantity is within about 1e-10
+// relative of the threshold.
+FL_HD double rcp_decide(double y) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  return fma(r, fma(-y, r, 1.0), r);
+#else
+  return 1.0 / y;
+#endif
+}
+
 // scale sensor of a cell from the differences to its two neighbours
 FL_HD double sensor(double dm, double dp) {
-  return (2.0 * fabs(dp * dm) + kSensorE) * fl_rcp(fma(dp, dp, fma(dm, dm, kSensorE)));
+  return (2.0 * fabs(dp * dm) + kSensorE) * rcp_decide(fma(dp, dp, fma(dm, dm, kSensorE)));
 }
 
 // cut-off C_T from the smallest sensor of the stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5):
@@ -41,16 +56,19 @@ FL_HD double lin_weight(int k) { return k == 0 ? 0.45 : (k == 1 ? 0.3 : (k == 2 
 
 // Normalised weights of the kept stencils for each keep mask (bit k set: stencil k kept):
 // omega[k][mask] = d_k / sum of the kept d_j, 0 for a cut stencil (mask 0 cannot occur: the
-// largest gamma_k / sum gamma is at least 1/4).  Entry i of the 64 is written by call i.
+// largest gamma_k / sum gamma is at least 1/4), times the common factor of candidate k's
+// coefficients (1/6 for the three-cell candidates, 1/12 for the four-cell one), which the
+// candidates below leave out.  Entry i of the 64 is written by call i.
 FL_HD void weight_entry(int i, double omega[4][16]) {
   const int k = i >> 4, mask = i & 15;
   double den = 0.0;
   for (int j = 0; j < 4; ++j)
     if ((mask >> j) & 1) den += lin_weight(j);
-  omega[k][mask] = ((mask >> k) & 1) ? lin_weight(k) / den : 0.0;
+  omega[k][mask] = ((mask >> k) & 1) ? lin_weight(k) / (den * (k < 3 ? 6.0 : 12.0)) : 0.0;
 }
 
-// TENO6 value from the candidates p_k and smoothness measures b_k (beta6 = b6): stencil k is kept
+// TENO6 value from the candidates p_k (times 6, the four-cell one times 12) and smoothness measures
+// b_k (beta6 = b6): stencil k is kept
 // unless gamma_k / sum gamma < C_T, and the value is the kept candidates' combination with the
 // normalised weights of omega (weight_entry)
 FL_HD double combine(double p0, double p1, double p2, double p3, double b0, double b1, double b2,
@@ -60,7 +78,7 @@ FL_HD double combine(double p0, double p1, double p2, double p3, double b0, doub
   const double bk[4] = {b0, b1, b2, b3};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double x = 1.0 + tau * fl_rcp(bk[k] + kEps);
+    const double x = fma(tau, rcp_decide(bk[k] + kEps), 1.0);
     const double x2 = x * x;
     g[k] = x2 * x2 * x2;
   }
@@ -76,24 +94,32 @@ FL_HD double combine(double p0, double p1, double p2, double p3, double b0, doub
 //     the next face's left-state measures (B at a+1, C at a+2, A at a): b3c carries them as
 //     (beta0, beta1, beta2) of that next left state.
 // On entry b3c holds this face's left-state (beta0, beta1, beta2); on exit the next face's.
-FL_HD void face_states(const double q[6], double ct, double b3c[3], const double (*omega)[16],
-                       double& wl, double& wr) {
-  const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1])) * kSixth;       // cells a-1..a+1
-  const double pd = fma(-1.0, q[4], fma(5.0, q[3], 2.0 * q[2])) * kSixth;  // cells a..a+2
-  const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0])) * kSixth;
-  const double p4 = fma(1.0, q[5], fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]))) * (1.0 / 12.0);
+FL_HD void face_states(const double q[6], double ct, double b3c[3], double kk[2],
+                       const double (*omega)[16], double& wl, double& wr) {
+  // candidates times 6 (three cells) and 12 (four cells); the factors are in omega
+  const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1]));       // cells a-1..a+1
+  const double pd = fma(-1.0, q[4], fma(5.0, q[3], 2.0 * q[2]));  // cells a..a+2
+  const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0]));
+  const double p4 = q[5] + fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]));
   const double e4[3] = {q[3] - q[2], q[4] - q[2], q[5] - q[2]};
   // beta6 of the window and of its mirror image together (the reversal negates the odd part)
   double b6l, b6r;
   beta6_pair(q, b6l, b6r);
   wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), b6l, ct, omega);
   // right state: the mirrored stencil q'_j = q[5 - j]
-  const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5])) * kSixth;
-  const double r4 = fma(1.0, q[0], fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]))) * (1.0 / 12.0);
+  const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5]));
+  const double r4 = q[0] + fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]));
   const double f4[3] = {q[2] - q[3], q[1] - q[3], q[0] - q[3]};
-  const double rb0 = weno_B(q[4], q[3], q[2]);
-  const double rb1 = weno_C(q[3], q[2], q[1]);
-  const double rb2 = weno_A(q[5], q[4], q[3]);
+  // three-cell measures K + s^2 / 4 with K = 13/12 t^2 of the stencil: K of the stencils centred at
+  // a and a+1 carry over from the previous face (kk), the one centred at a+2 is new
+  const double t2 = fma(-2.0, q[4], q[3]) + q[5];
+  const double K2 = k1312 * t2 * t2;
+  const double sB = q[4] - q[2], sC = fma(-4.0, q[2], 3.0 * q[3]) + q[1], sA = fma(-4.0, q[4], q[5]) + 3.0 * q[3];
+  const double rb0 = fma(0.25 * sB, sB, kk[1]);             // B of (q2, q3, q4)
+  const double rb1 = fma(0.25 * sC, sC, kk[0]);             // C of (q1, q2, q3)
+  const double rb2 = fma(0.25 * sA, sA, K2);                // A of (q3, q4, q5)
+  kk[0] = kk[1];
+  kk[1] = K2;
   wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, beta4_form(f4), b6r, ct, omega);
   // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at a (rb1's)
   b3c[0] = rb0;

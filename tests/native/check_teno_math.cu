@@ -16,8 +16,11 @@ int main() {
     for (int j = 1; j <= 4; ++j) eta = std::fmin(eta, fl::teno::sensor(q[j] - q[j - 1], q[j + 1] - q[j]));
     const double ct = fl::teno::cutoff(eta);
     double b3c[3] = {fl::weno_B(q[1], q[2], q[3]), fl::weno_C(q[2], q[3], q[4]), fl::weno_A(q[0], q[1], q[2])};
+    // 13/12 t^2 of the three-cell stencils centred at cells 2 and 3, as the march carries them
+    const double ta = std::fma(-2.0, q[2], q[1]) + q[3], tb = std::fma(-2.0, q[3], q[2]) + q[4];
+    double kk[2] = {fl::k1312 * ta * ta, fl::k1312 * tb * tb};
     double wl, wr;
-    fl::teno::face_states(q, ct, b3c, omega, wl, wr);
+    fl::teno::face_states(q, ct, b3c, kk, omega, wl, wr);
     std::printf("%.17g %.17g %.17g\n", wl, wr, ct);
   }
   return 0;
