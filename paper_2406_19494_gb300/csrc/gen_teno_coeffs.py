@@ -46,20 +46,23 @@ def emit(name, offsets):
     n = len(offsets) - 1
     print("// %s: cells %s (offsets from the target cell), e[j-1] = q_{s_j} - q_{s_0}, j = 1 .. %d:"
           % (name, offsets, n))
-    print("// beta = sum_{j<=k} c_jk e_j e_k / %d, grouped by rows: sum_j e_j (sum_{k>=j} c_jk e_k)." % den)
+    print("// beta = sum_{j<=k} c_jk e_j e_k / %d, grouped by rows: sum_j e_j (sum_{k>=j} c_jk e_k / %d)"
+          % (den, den))
+    print("// (the coefficients c_jk / %d rounded to FP64)." % den)
     print("FL_HD double %s(const double e[%d]) {" % (name, n))
     rows = []
+    f = lambda c: "%r" % (float(sp.Rational(c, den)))
     for j in range(n):
         row = [(k, c) for (jj, k, c) in terms if jj == j]
-        expr = "%d.0 * e[%d]" % (row[0][1], row[0][0])
+        expr = "%s * e[%d]" % (f(row[0][1]), row[0][0])
         for k, c in row[1:]:
-            expr = "fma(%d.0, e[%d], %s)" % (c, k, expr)
+            expr = "fma(%s, e[%d], %s)" % (f(c), k, expr)
         print("  const double r%d = %s;" % (j, expr))
         rows.append(j)
     acc = "e[0] * r0"
     for j in rows[1:]:
         acc = "fma(e[%d], r%d, %s)" % (j, j, acc)
-    print("  return (%s) * (1.0 / %d.0);" % (acc, den))
+    print("  return %s;" % acc)
     print("}")
     print()
 
@@ -80,7 +83,7 @@ def beta_matrix(offsets):
     return sp.Matrix(n, n, lambda i, j: sp.Rational(1, 2) * sp.diff(beta, q[i], q[j])), q, beta
 
 
-def emit_pair(name, offsets):
+def emit_pair(name, offsets, scale=6):
     """Both smoothness measures of a six-cell window and of its mirror image, the form evaluated on
     q and on (q5, .., q0).  With u_j = q_j + q_{5-j} and v_j = q_j - q_{5-j} (j = 0, 1, 2), the
     reversal leaves u and negates v, so beta(q) = S + T + 2 X and beta(Jq) = S + T - 2 X with S a
@@ -129,10 +132,12 @@ def emit_pair(name, offsets):
     bL = beta.subs(dict(zip(q, qs)), simultaneous=True)
     bR = beta.subs(dict(zip(q, reversed(qs))), simultaneous=True)
     assert sp.expand(Sv + Tv + 2 * Xv - bL) == 0 and sp.expand(Sv + Tv - 2 * Xv - bR) == 0
-    f = lambda c: "%r" % float(c)
-    print("// %s: the TENO6 measure of the window q[0..5] (cells %s around the target cell)" % (name, offsets))
+    f = lambda c: "%r" % float(scale * c)
+    print("// %s: %d times the TENO6 measure of the window q[0..5] (cells %s around the target cell)"
+          % (name, scale, offsets))
     print("// and of its mirror image (q[5..0]): bL = S + T + 2 X, bR = S + T - 2 X with u_j = q_j + q_{5-j},")
-    print("// v_j = q_j - q_{5-j}, a_k = u_k - u_0; coefficients are the exact rationals rounded to FP64.")
+    print("// v_j = q_j - q_{5-j}, a_k = u_k - u_0; coefficients are %d times the exact rationals, rounded" % scale)
+    print("// to FP64 (the factor is the 6 of tau6 = |beta6 - (beta1 + beta2 + 4 beta0) / 6|).")
     print("FL_HD void %s(const double q[6], double& bL, double& bR) {" % name)
     print("  // a_k from differences of neighbouring values, exact for close values, never from the sums u_k")
     print("  const double a1 = (q[1] - q[0]) + (q[4] - q[5]), a2 = (q[2] - q[0]) + (q[3] - q[5]);")
@@ -178,7 +183,6 @@ print("#endif")
 print("namespace fl {")
 print("namespace teno {")
 emit("beta4_form", (0, 1, 2, 3))
-emit("beta6_form", (-2, -1, 0, 1, 2, 3))
 emit_pair("beta6_pair", (-2, -1, 0, 1, 2, 3))
 emit_cutoff_thresholds()
 print("}  // namespace teno")

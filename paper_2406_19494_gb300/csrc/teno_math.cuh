@@ -68,17 +68,18 @@ FL_HD void weight_entry(int i, double omega[4][16]) {
 }
 
 // TENO6 value from the candidates p_k (times 6, the four-cell one times 12) and smoothness measures
-// b_k (beta6 = b6): stencil k is kept
+// b_k (b6 = 6 beta6): stencil k is kept
 // unless gamma_k / sum gamma < C_T, and the value is the kept candidates' combination with the
 // normalised weights of omega (weight_entry)
 FL_HD double combine(double p0, double p1, double p2, double p3, double b0, double b1, double b2,
                      double b3, double b6, double ct, const double (*omega)[16]) {
-  const double tau = fabs(b6 - (b1 + b2 + 4.0 * b0) * kSixth);
+  // b6 is 6 beta6 (beta6_pair), so tau = 6 tau6 and gamma_k = (1 + tau / (6 (beta_k + eps)))^6
+  const double tau = fabs(b6 - fma(4.0, b0, b1 + b2));
   double g[4];
   const double bk[4] = {b0, b1, b2, b3};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double x = fma(tau, rcp_decide(bk[k] + kEps), 1.0);
+    const double x = fma(tau, rcp_decide(fma(6.0, bk[k], 6.0 * kEps)), 1.0);
     const double x2 = x * x;
     g[k] = x2 * x2 * x2;
   }
@@ -102,7 +103,7 @@ FL_HD void face_states(const double q[6], double ct, double b3c[3], double kk[2]
   const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0]));
   const double p4 = q[5] + fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]));
   const double e4[3] = {q[3] - q[2], q[4] - q[2], q[5] - q[2]};
-  // beta6 of the window and of its mirror image together (the reversal negates the odd part)
+  // 6 beta6 of the window and of its mirror image together (the reversal negates the odd part)
   double b6l, b6r;
   beta6_pair(q, b6l, b6r);
   wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), b6l, ct, omega);
