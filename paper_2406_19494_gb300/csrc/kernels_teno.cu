@@ -19,12 +19,12 @@ namespace fl {
 namespace {
 
 // face flux F^c - F^d at face a+1/2 along D; `cell` is the padded index of cell a, s its stride;
-// eta[v][0..2] carry the sensors of cells a-1, a, a+1 and b3[v] the three-cell smoothness
+// lev[v][0..2] carry the cut-off levels of cells a-1, a, a+1 and b3[v] the three-cell smoothness
 // measures of the left state (see teno::face_states); both advance by one cell
 template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
-                                               double F[5], double eta[5][3], double b3[5][3],
+                                               double F[5], int lev[5][3], double b3[5][3],
                                                double kk[5][2], const double (*omega)[16]) {
   const int nc = g.ncell;
   double q[5][6];
@@ -35,13 +35,13 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
   double wl[5], wr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    // cells a-2 .. a+3 are q[v][0..5]; the sensor of cell a+2 is the new one
-    const double e3 = teno::sensor(q[v][4] - q[v][3], q[v][5] - q[v][4]);
-    const double ct = teno::cutoff(fmin(fmin(eta[v][0], eta[v][1]), fmin(eta[v][2], e3)));
+    // cells a-2 .. a+3 are q[v][0..5]; the sensor level of cell a+2 is the new one
+    const int l3 = teno::sensor_level(q[v][4] - q[v][3], q[v][5] - q[v][4]);
+    const double ct = teno::cutoff_of_level(min(min(lev[v][0], lev[v][1]), min(lev[v][2], l3)));
     teno::face_states(q[v], ct, b3[v], kk[v], omega, wl[v], wr[v]);
-    eta[v][0] = eta[v][1];
-    eta[v][1] = eta[v][2];
-    eta[v][2] = e3;
+    lev[v][0] = lev[v][1];
+    lev[v][1] = lev[v][2];
+    lev[v][2] = l3;
   }
   // interpolation limiter
   if (wl[0] <= 0.0 || wl[4] <= 0.0) {
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], eta[5][3], b3[5][3], kk[5][2];
+    double Fp[5], F[5], b3[5][3], kk[5][2];
+    int lev[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       // sensors of cells a0-2, a0-1, a0 and the left-state three-cell measures of the first face
@@ -93,9 +94,9 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       const double* f = W + v * nc + cell;
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
-      eta[v][0] = teno::sensor(qm1 - qm2, q0 - qm1);
-      eta[v][1] = teno::sensor(q0 - qm1, qp1 - q0);
-      eta[v][2] = teno::sensor(qp1 - q0, qp2 - qp1);
+      lev[v][0] = teno::sensor_level(qm1 - qm2, q0 - qm1);
+      lev[v][1] = teno::sensor_level(q0 - qm1, qp1 - q0);
+      lev[v][2] = teno::sensor_level(qp1 - q0, qp2 - qp1);
       b3[v][0] = weno_B(qm1, q0, qp1);
       b3[v][1] = weno_C(q0, qp1, qp2);
       b3[v][2] = weno_A(qm2, qm1, q0);
@@ -104,10 +105,10 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       kk[v][0] = k1312 * ta * ta;
       kk[v][1] = k1312 * tb * tb;
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, eta, b3, kk, omega);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, kk, omega);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, eta, b3, kk, omega);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, kk, omega);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

@@ -24,11 +24,10 @@ namespace teno {
 constexpr double kEps = 1e-40;
 constexpr double kSensorE = 0.9 * 0.25 * 1e-6 / 0.75;
 
-// 1/y for the quantities that only decide the cut-off (the sensors and gamma_k): one
-// second-order Newton step from the hardware estimate of rcp.approx.ftz.f64, relative error the
-// square of the estimate's (about 2^-34 or smaller; the third-order fl_rcp squares it once more).
-// A decision can differ from exact division only where its quantity is within about 1e-10
-// relative of the threshold.
+// 1/y for gamma_k, which only decides the cut-off: one second-order Newton step from the hardware
+// estimate of rcp.approx.ftz.f64, relative error the square of the estimate's (about 2^-34 or
+// smaller; the third-order fl_rcp squares it once more).  A keep decision can differ from exact
+// division only where gamma_k / sum gamma is within about 1e-10 relative of C_T.
 FL_HD double rcp_decide(double y) {
 #ifdef __CUDA_ARCH__
   double r;
@@ -39,16 +38,22 @@ FL_HD double rcp_decide(double y) {
 #endif
 }
 
-// scale sensor of a cell from the differences to its two neighbours
-FL_HD double sensor(double dm, double dp) {
-  return (2.0 * fabs(dp * dm) + kSensorE) * rcp_decide(fma(dp, dp, fma(dm, dm, kSensorE)));
+// Cut-off level of a cell from the differences dm, dp to its two neighbours: how many of the
+// thresholds kCutEta8 < kCutEta9 < kCutEta10 (teno_coeffs.cuh) its scale sensor
+// eta = N / D = (2 |dp dm| + e) / (dp^2 + dm^2 + e) reaches, decided as N >= eta_k D (D > 0)
+// without forming the quotient.  The adaptive C_T = 10^-floor(alpha1 - alpha2 (1 - g(m))) of a
+// stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5) is a step function of its smallest sensor,
+// since g grows with eta, so it follows from the smallest level of the stencil's cells.
+FL_HD int sensor_level(double dm, double dp) {
+  const double N = fma(2.0, fabs(dp * dm), kSensorE);
+  const double Dn = fma(dp, dp, fma(dm, dm, kSensorE));
+  return (fma(-kCutEta8, Dn, N) >= 0.0 ? 1 : 0) + (fma(-kCutEta9, Dn, N) >= 0.0 ? 1 : 0) +
+         (fma(-kCutEta10, Dn, N) >= 0.0 ? 1 : 0);
 }
 
-// cut-off C_T from the smallest sensor of the stencil (C_r = 0.25, alpha1 = 10.5, alpha2 = 3.5):
-// 10^-floor(alpha1 - alpha2 (1 - g(m))) is a step function of eta with the thresholds kCutEta*
-// (teno_coeffs.cuh), since g grows with eta
-FL_HD double cutoff(double eta) {
-  return eta >= kCutEta10 ? 1e-10 : (eta >= kCutEta9 ? 1e-9 : (eta >= kCutEta8 ? 1e-8 : 1e-7));
+// C_T of a level: 1e-7, 1e-8, 1e-9, 1e-10
+FL_HD double cutoff_of_level(int level) {
+  return level >= 3 ? 1e-10 : (level == 2 ? 1e-9 : (level == 1 ? 1e-8 : 1e-7));
 }
 
 // linear weights d_k = (9/20, 3/10, 1/20, 1/5) (sixth-order combination of the four candidates)
