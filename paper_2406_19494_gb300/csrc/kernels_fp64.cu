@@ -407,49 +407,72 @@ __global__ void k_stage_prim(int stage, const double* Un, const double* Us, cons
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n[0]) return;
   const int nc = g.ncell;
+  // two cells per thread, rows j and j + J2, with every load of both issued before any store, so
+  // that the two conversions' FP64 chains overlap
+  const int J2 = (g.n[1] + 1) >> 1;
   bool bad = false;
   for (int k = blockIdx.z; k < g.n[2]; k += gridDim.z)
-    for (int j = blockIdx.y; j < g.n[1]; j += gridDim.y) {
-      const int c = (i + g.h[0]) + (j + g.h[1]) * g.sy + (k + g.h[2]) * g.sz;
-      double u[5];
-      if (hold) {
+    for (int j = blockIdx.y; j < J2; j += gridDim.y) {
+      const int base = (i + g.h[0]) + (k + g.h[2]) * g.sz;
+      const bool two = j + J2 < g.n[1];
+      const int c[2] = {base + (j + g.h[1]) * g.sy, base + (j + J2 + g.h[1]) * g.sy};
+      double un[2][5], rs[2][5], us[2][5], vel[2][3];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = Un[v * nc + c];
-      } else {
-        double r[5];
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) r[v] = R[v * nc + c];
-        if (ph.has_force) {
-          const double uu = W[nc + c], vv = W[2 * nc + c], ww = W[3 * nc + c];
-          r[1] += ph.f[0];
-          r[2] += ph.f[1];
-          r[3] += ph.f[2];
-          r[4] += ph.f[0] * uu + ph.f[1] * vv + ph.f[2] * ww;
-        }
+        for (int v = 0; v < 5; ++v) un[q][v] = Un[v * nc + c[q]];
+        if (!hold) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const double un = Un[v * nc + c];
-          double out;
-          if (stage == 1) {
-            out = un + dt * r[v];
-          } else {
-            const double us = Us[v * nc + c];
-            out = stage == 2 ? 0.75 * un + 0.25 * (us + dt * r[v])
-                             : (1.0 / 3.0) * un + (2.0 / 3.0) * (us + dt * r[v]);
+          for (int v = 0; v < 5; ++v) rs[q][v] = R[v * nc + c[q]];
+          if (stage != 1) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) us[q][v] = Us[v * nc + c[q]];
           }
-          bad |= !finite_bits(out);
-          Ud[v * nc + c] = out;
-          u[v] = out;
+          if (ph.has_force) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vel[q][b] = W[(1 + b) * nc + c[q]];
+          }
         }
       }
-      double w[NW];
-      prim_from_cons(u, ph, w);
 #pragma unroll
-      for (int v = 0; v < NW; ++v) W[v * nc + c] = w[v];
-      if (MIXED) {
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
+        double u[5];
+        if (hold) {
 #pragma unroll
-        for (int v = 0; v < NW; ++v) split_hi_lo(w[v], W32[v * nc + c], W32[(NW + v) * nc + c]);
-        W[NW * nc + c] = u[4] + w[4];
+          for (int v = 0; v < 5; ++v) u[v] = un[q][v];
+        } else {
+          double* r = rs[q];
+          if (ph.has_force) {
+            r[1] += ph.f[0];
+            r[2] += ph.f[1];
+            r[3] += ph.f[2];
+            r[4] += ph.f[0] * vel[q][0] + ph.f[1] * vel[q][1] + ph.f[2] * vel[q][2];
+          }
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            double out;
+            if (stage == 1) {
+              out = un[q][v] + dt * r[v];
+            } else {
+              out = stage == 2 ? 0.75 * un[q][v] + 0.25 * (us[q][v] + dt * r[v])
+                               : (1.0 / 3.0) * un[q][v] + (2.0 / 3.0) * (us[q][v] + dt * r[v]);
+            }
+            bad |= !finite_bits(out);
+            Ud[v * nc + c[q]] = out;
+            u[v] = out;
+          }
+        }
+        double w[NW];
+        prim_from_cons(u, ph, w);
+#pragma unroll
+        for (int v = 0; v < NW; ++v) W[v * nc + c[q]] = w[v];
+        if (MIXED) {
+#pragma unroll
+          for (int v = 0; v < NW; ++v) split_hi_lo(w[v], W32[v * nc + c[q]], W32[(NW + v) * nc + c[q]]);
+          W[NW * nc + c[q]] = u[4] + w[4];
+        }
       }
     }
   if (bad) atomicOr(&ctl->flags, FLAG_NONFINITE);
@@ -684,8 +707,8 @@ cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, con
   // interior rows in nb near-equal chunks of whole warps, at most 256 threads each
   const int nb = (g.n[0] + 255) / 256;
   const int block = ((g.n[0] + nb - 1) / nb + 31) / 32 * 32;
-  const dim3 grid((g.n[0] + block - 1) / block, g.n[1] < 65535 ? g.n[1] : 65535,
-                  g.n[2] < 65535 ? g.n[2] : 65535);
+  const int j2 = (g.n[1] + 1) / 2;                                     // row pairs
+  const dim3 grid((g.n[0] + block - 1) / block, j2 < 65535 ? j2 : 65535, g.n[2] < 65535 ? g.n[2] : 65535);
   if (W32) k_stage_prim<true><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
   else k_stage_prim<false><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
   cudaError_t e = cudaGetLastError();
