@@ -260,6 +260,13 @@ int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int
 int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev, double* ieee_dev,
                      int n, void* stream);
 
+/* Accuracy check of the power-law viscosity ratio (T / T_ref)^e as the kernels compute it: for an
+ * exponent that is a ratio p / q of small integers (0.7 = 7 / 10) one Halley step for y^q = x^p
+ * from an FP32 estimate, otherwise the library exp(e log x).  fast[i] = that value of x[i],
+ * lib[i] = exp(e log x[i]) (CUDA's library), for n device values.  For tests. */
+int fluid_check_pow(const double* x_dev, double* fast_dev, double* lib_dev, int n, double e,
+                    void* stream);
+
 
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as
  * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is

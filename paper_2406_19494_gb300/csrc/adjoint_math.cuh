@@ -330,7 +330,7 @@ FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double
     }
   }
   for (int c = 0; c < 3; ++c) gG[c][c] += gdiv;
-  const double gTf = gmu * viscosity_dT(Tf, ph);
+  const double gTf = gmu * viscosity_dT(Tf, mu, ph);
   for (int k = 0; k < 4; ++k) {
     gT[k] = gTf * ci[k] + gdT * cn[k];
     for (int c = 0; c < 3; ++c) gvel[c][k] = gvf[c] * ci[k] + gG[c][D] * cn[k];

@@ -55,5 +55,45 @@ FL_HD double fl_rcp(double y) {
 #endif
 }
 
+// x^n for a small positive integer n by binary powering (n - 1 + number of bits of n multiplies at
+// most; x^7 and x^10 take four).
+FL_HD double fl_ipow(double x, int n) {
+  double r = x, b = x;
+  bool have = false;
+  while (true) {
+    if (n & 1) {
+      r = have ? r * b : b;
+      have = true;
+    }
+    n >>= 1;
+    if (!n) break;
+    b = b * b;
+  }
+  return r;
+}
+
+// x^(p/q) for 0 < p, q <= 16 and x in (1e-15, 1e15) (so that x^p and y^q stay normal and
+// finite): y = x^(p/q) is the positive root of y^q = a, a = x^p.  An FP32 estimate
+// y0 = 2^(e log2 x) from the hardware approximations (ex2.approx, lg2.approx; relative error below
+// about 3e-6 on this range) takes one step of Halley's method for that equation,
+// y1 = y0 ((q + 1) a + (q - 1) y0^q) / ((q - 1) a + (q + 1) y0^q), whose error is about
+// (q^2 - 1) / 12 times the cube of y0's, below FP64 rounding.  The step is written as the
+// correction y1 = y0 + 2 y0 (a - y0^q) / ((q + 1) y0^q + (q - 1) a), of relative size about 1e-6,
+// so that its own rounding stays far below an ulp of y1.  Other x take the library
+// exp(e log x).  e32 is p/q in FP32.  Checked on the GPU against x^(p/q) (fluid_check_pow).
+FL_HD double fl_pow_rational(double x, int p, int q, float e32) {
+#ifdef __CUDA_ARCH__
+  if (x > 1e-15 && x < 1e15) {
+    float l, y32;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"((float)x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y32) : "f"(e32 * l));
+    const double y0 = (double)y32;
+    const double a = fl_ipow(x, p), yq = fl_ipow(y0, q);
+    const double den = fma(0.5 * (double)(q + 1), yq, (0.5 * (double)(q - 1)) * a);
+    return fma(y0 * (a - yq), fl_rcp(den), y0);
+  }
+#endif
+  return exp(((double)p / (double)q) * log(x));
+}
 
 }  // namespace fl

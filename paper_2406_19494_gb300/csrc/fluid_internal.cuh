@@ -34,6 +34,8 @@ struct Geo {
 struct Phys {
   double gamma, gm1, igm1, R, iR, cp, Pr, lam_fac;
   double mu_ref, T_ref, iT_ref, visc_exp, suth_S;
+  int visc_p, visc_q;  // power law: visc_exp = visc_p / visc_q (small integers), else visc_q = 0
+  float visc_e32;      // visc_exp in FP32
   int visc, weno;
   int visc_order;     // central differences of the dissipative fluxes: 4 or 6
   double eps;
@@ -64,19 +66,37 @@ __device__ __forceinline__ bool finite_bits(double x) {
 __host__ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return ph.mu_ref;
   const double r = T * ph.iT_ref;
-  if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * exp(ph.visc_exp * log(r));
+  if (ph.visc == FLUID_VISC_POWER) {
+    if (ph.visc_q > 0) return ph.mu_ref * fl_pow_rational(r, ph.visc_p, ph.visc_q, ph.visc_e32);
+    return ph.mu_ref * exp(ph.visc_exp * log(r));
+  }
   // Sutherland
   return ph.mu_ref * (r * fl_sqrt(r)) * (ph.T_ref + ph.suth_S) * fl_rcp(T + ph.suth_S);
 }
 
-// d mu / d T of the same laws
-__host__ __device__ __forceinline__ double viscosity_dT(double T, const Phys& ph) {
+// d mu / d T of the same laws, given mu = viscosity(T, ph): power law e mu / T; Sutherland
+// (mu = C r^{3/2} / (T + S), C = mu_ref (T_ref + S)) mu (1.5 / T - 1 / (T + S))
+__host__ __device__ __forceinline__ double viscosity_dT(double T, double mu, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return 0.0;
-  const double r = T * ph.iT_ref;
-  if (ph.visc == FLUID_VISC_POWER) return ph.mu_ref * ph.visc_exp * exp((ph.visc_exp - 1.0) * log(r)) * ph.iT_ref;
-  // mu = C r^{3/2} / (T + S) with C = mu_ref (T_ref + S): dmu/dT = mu (1.5 / T - 1 / (T + S))
-  const double mu = ph.mu_ref * (r * sqrt(r)) * (ph.T_ref + ph.suth_S) / (T + ph.suth_S);
-  return mu * (1.5 / T - 1.0 / (T + ph.suth_S));
+  if (ph.visc == FLUID_VISC_POWER) return ph.visc_exp * mu * fl_rcp(T);
+  return mu * (1.5 * fl_rcp(T) - fl_rcp(T + ph.suth_S));
+}
+
+// The power-law exponent as p / q with 0 < p, q <= 16 when it is one to within a few ulp (0.7 is
+// 7/10), for fl_pow_rational; q = 0 otherwise.  Also sets the FP32 copy.
+inline void set_power_law(Phys& ph, double e) {
+  ph.visc_exp = e;
+  ph.visc_e32 = (float)e;
+  ph.visc_p = ph.visc_q = 0;
+  for (int q = 1; q <= 16; ++q) {
+    const double pq = e * q;
+    const int p = (int)(pq + 0.5);
+    if (p >= 1 && p <= 16 && fabs((double)p / q - e) <= 4.0 * 2.220446049250313e-16 * fabs(e)) {
+      ph.visc_p = p;
+      ph.visc_q = q;
+      return;
+    }
+  }
 }
 
 // Configuration check shared by the entry points: NULL if valid, else a static message.

@@ -213,7 +213,7 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
   ph.mu_ref = c.mu_ref;
   ph.T_ref = c.T_ref;
   ph.iT_ref = c.T_ref > 0 ? 1.0 / c.T_ref : 1.0;
-  ph.visc_exp = c.visc_exp;
+  set_power_law(ph, c.visc_exp);
   ph.suth_S = c.suth_S;
   ph.visc = c.visc_law;
   ph.weno = c.weno;

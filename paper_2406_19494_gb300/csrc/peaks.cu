@@ -72,6 +72,29 @@ __global__ void k_check_sqrt(const double* __restrict__ y, double* __restrict__ 
 }
 }  // namespace
 
+__global__ void k_check_pow(const double* __restrict__ x, double* __restrict__ fast,
+                            double* __restrict__ lib, int n, fl::Phys ph) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    fast[i] = fl::viscosity(x[i] * ph.T_ref, ph) / ph.mu_ref;
+    lib[i] = exp(ph.visc_exp * log(x[i]));
+  }
+}
+
+extern "C" int fluid_check_pow(const double* x_dev, double* fast_dev, double* lib_dev, int n,
+                               double e, void* stream) {
+  if (!x_dev || !fast_dev || !lib_dev || n < 0) return FLUID_EINVAL;
+  if (n == 0) return FLUID_OK;
+  fl::Phys ph{};
+  ph.visc = FLUID_VISC_POWER;
+  ph.mu_ref = 1.0;
+  ph.T_ref = 1.0;
+  ph.iT_ref = 1.0;
+  fl::set_power_law(ph, e);
+  k_check_pow<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0,
+                reinterpret_cast<cudaStream_t>(stream)>>>(x_dev, fast_dev, lib_dev, n, ph);
+  return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
+}
+
 extern "C" int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev,
                                 double* ieee_dev, int n, void* stream) {
   if (!y_dev || !rsqrt_dev || !sqrt_dev || !ieee_dev || n < 0) return FLUID_EINVAL;
