@@ -218,8 +218,9 @@ int fluid_check(fluid_solver* s, void* stream);
  * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8
  * that still fills the GPU).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
  * tiles of 2 warps (block 64) or 4 warps (otherwise) by default; seg < 0 selects the register-window
- * marching kernels with |seg| cells per segment and `block` threads instead.  Results do not
- * depend on the shape. */
+ * marching kernels with |seg| cells per segment and `block` threads instead.  FP64 results and
+ * those of the two mixed tiles are bitwise the same for every shape; the mixed register-window
+ * kernels agree with the tiles to FP32 rounding. */
 int fluid_tune_faces(fluid_solver* s, int block, int seg);
 
 /* Kernel classes reported by the profiler. */

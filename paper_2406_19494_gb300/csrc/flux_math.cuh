@@ -92,6 +92,24 @@ FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
   }
 }
 
+// weno_x for indicators that already include epsilon: e_k = beta_k + eps (so that
+// tau = |e0 - e2| = |beta0 - beta2|)
+template <int SCHEME>
+FL_HD void weno_x_e(double e0, double e1, double e2, double X[3]) {
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  if (SCHEME == FLUID_WENO_JS) {
+    X[0] = Q0 * Q0; X[1] = Q1 * Q1; X[2] = Q2 * Q2;
+  } else {
+    const double tau = fabs(e0 - e2);
+    const double P = e0 * Q0;
+    const double PP = P * P;
+    const double T0 = tau * Q0, T1 = tau * Q1, T2 = tau * Q2;
+    X[0] = fma(T0, T0, PP);
+    X[1] = fma(T1, T1, PP);
+    X[2] = fma(T2, T2, PP);
+  }
+}
+
 // The value from the stencil centre q0 and the four cell differences of the stencil,
 // dm2 = q_{i-1} - q_{i-2}, dm1 = q_i - q_{i-1}, dp0 = q_{i+1} - q_i, dp1 = q_{i+2} - q_{i+1}:
 // with the candidates as offsets from q_i, p0 - q_i = (5 dm1 - 2 dm2) / 6,

@@ -97,13 +97,18 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       lev[v][0] = teno::sensor_level(qm1 - qm2, q0 - qm1);
       lev[v][1] = teno::sensor_level(q0 - qm1, qp1 - q0);
       lev[v][2] = teno::sensor_level(qp1 - q0, qp2 - qp1);
-      b3[v][0] = weno_B(qm1, q0, qp1);
-      b3[v][1] = weno_C(q0, qp1, qp2);
-      b3[v][2] = weno_A(qm2, qm1, q0);
-      // 13/12 t^2 of the three-cell stencils centred at a0-1 and a0
-      const double ta = fma(-2.0, q0, qm1) + qp1, tb = fma(-2.0, qp1, q0) + qp2;
-      kk[v][0] = k1312 * ta * ta;
-      kk[v][1] = k1312 * tb * tb;
+      // the three-cell measures and 13/12 t^2 terms the march carries into the first face, formed
+      // by the march's own operations (teno::face_states at the face before), so that a segment
+      // start continues bit for bit: K of the stencils centred at a-1, a, a+1 (a = a0 - 1), then
+      // B centred at a, A centred at a+1 and C centred at a-1
+      const double tm = fma(-2.0, qm1, qm2) + q0, ta = fma(-2.0, q0, qm1) + qp1, tb = fma(-2.0, qp1, q0) + qp2;
+      const double Km = k1312 * tm * tm, Ka = k1312 * ta * ta, Kb = k1312 * tb * tb;
+      const double sB = qp1 - qm1, sA = fma(-4.0, qp1, qp2) + 3.0 * q0, sC = fma(-4.0, qm1, 3.0 * q0) + qm2;
+      b3[v][0] = fma(0.25 * sB, sB, Ka);
+      b3[v][1] = fma(0.25 * sA, sA, Kb);
+      b3[v][2] = fma(0.25 * sC, sC, Km);
+      kk[v][0] = Ka;
+      kk[v][1] = Kb;
     }
     face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, kk, omega);
     for (int a = a0; a < a1; ++a) {

@@ -1,0 +1,65 @@
+"""The face kernels' launch shape (fluid_tune_faces: threads per block, cells per marching
+segment, the mixed path's tile or register-window kernels) is a performance choice only: the
+right-hand side is the same to rounding for every shape.  The mixed path's y / z tiles of either
+size compute each face with the same code from the same cell differences, so they agree bitwise;
+its register-window kernels compile the same face arithmetic in another kernel, where the compiler
+may fuse a different pair of FP32 operations into one multiply-add, so they agree to FP32
+rounding.  The FP64 marches (WENO5-JS, WENO5-Z, TENO6-A) start every segment with the terms the
+march would have carried there, formed by the march's own operations, so every segment length
+gives bitwise the same right-hand side."""
+import numpy as np
+import pytest
+
+from helpers import padded_state, rel_err
+from paper_2406_19494_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = ("periodic", "periodic")
+WALL = ("wall", "wall")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19494_gb300 import build
+    build.build()
+
+
+def _rhs(c, U, precision, block, seg):
+    from paper_2406_19494_gb300.solver import Solver
+    s = Solver(c, precision=precision)
+    s.tune_faces(block, seg)
+    R = s.rhs(torch.from_numpy(U).cuda())
+    s.check()
+    return R.cpu().numpy()
+
+
+CASE = lambda: wl.random_box(3, (37, 29, 21), bc=(P, WALL, P), stretch=("uniform", "tanh2", "uniform"),
+                             beta=(0.0, 2.0, 0.0), t_wall=((1, 1), (2.5, 2.2), (1, 1)))
+
+
+@pytest.mark.parametrize("scheme", [dict(), dict(weno="js"), dict(weno="teno6a", visc_order=6)])
+def test_fp64_shapes_agree_bitwise(scheme):
+    c = dict(CASE(), **scheme)
+    case, grid, U = padded_state(c, seed=8)
+    inner = (slice(None),) + case.interior()
+    base = _rhs(c, U, "fp64", 0, 0)[inner]
+    for block, seg in ((64, 8), (96, 5), (128, 64), (32, 3), (128, 1)):
+        R = _rhs(c, U, "fp64", block, seg)[inner]
+        assert np.array_equal(R, base), (block, seg)
+
+
+def test_mixed_shapes_agree():
+    c = CASE()
+    case, grid, U = padded_state(c, seed=9)
+    inner = (slice(None),) + case.interior()
+    base = _rhs(c, U, "mixed", 0, 0)[inner]
+    for block, seg in ((64, 0), (128, 0)):
+        R = _rhs(c, U, "mixed", block, seg)[inner]
+        assert np.array_equal(R, base), (block, seg)
+    for block, seg in ((64, -8), (128, -5), (32, -3)):
+        R = _rhs(c, U, "mixed", block, seg)[inner]
+        assert max(rel_err(R, base)) <= 1e-6, (block, seg)
