@@ -30,10 +30,14 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   const double t0 = q[0] - 2.0 * q[1] + q[2], s0 = q[0] - 4.0 * q[1] + 3.0 * q[2];
   const double t1 = q[1] - 2.0 * q[2] + q[3], s1 = q[1] - q[3];
   const double t2 = q[2] - 2.0 * q[3] + q[4], s2 = 3.0 * q[2] - 4.0 * q[3] + q[4];
-  const double b0 = k1312 * t0 * t0 + 0.25 * s0 * s0;
-  const double b1 = k1312 * t1 * t1 + 0.25 * s1 * s1;
-  const double b2 = k1312 * t2 * t2 + 0.25 * s2 * s2;
-  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
+  // indicators and epsilon taken times 4 (4 beta = 13/3 t^2 + s^2): the weights of either scheme
+  // are homogeneous in (beta + eps, tau), so the value and its gradient are unchanged
+  constexpr double K4 = 4.0 * k1312;
+  const double b0 = fma(K4 * t0, t0, s0 * s0);
+  const double b1 = fma(K4 * t1, t1, s1 * s1);
+  const double b2 = fma(K4 * t2, t2, s2 * s2);
+  const double eps4 = 4.0 * eps;
+  const double e0 = b0 + eps4, e1 = b1 + eps4, e2 = b2 + eps4;
   double a0, a1, a2, ge0, ge1, ge2, gb0 = 0.0, gb2 = 0.0;
   // face value = N / (6 S), N = sum a_k C_k, S = sum a_k
   double r0 = 0.0, r1 = 0.0, r2 = 0.0, sg = 1.0;
@@ -45,7 +49,7 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
     const double tau = b0 - b2 < 0.0 ? b2 - b0 : b0 - b2;
     sg = b0 - b2 < 0.0 ? -1.0 : 1.0;
     r0 = tau * i0; r1 = tau * i1; r2 = tau * i2;
-    a0 = 0.1 * (1.0 + r0 * r0); a1 = 0.6 * (1.0 + r1 * r1); a2 = 0.3 * (1.0 + r2 * r2);
+    a0 = 0.1 * fma(r0, r0, 1.0); a1 = 0.6 * fma(r1, r1, 1.0); a2 = 0.3 * fma(r2, r2, 1.0);
   }
   const double S = a0 + a1 + a2;
   const double N = a0 * C0 + a1 * C1 + a2 * C2;
@@ -54,7 +58,7 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   if (out_value) *out_value = out + qin[2];
   const double gN = g_out * iS6;
   const double gS = -6.0 * out * gN;                 // -g_out out / S
-  const double ga0 = gN * C0 + gS, ga1 = gN * C1 + gS, ga2 = gN * C2 + gS;
+  const double ga0 = fma(gN, C0, gS), ga1 = fma(gN, C1, gS), ga2 = fma(gN, C2, gS);
   const double gC0 = gN * a0, gC1 = gN * a1, gC2 = gN * a2;
   if (SCHEME == FLUID_WENO_JS) {
     // a_k = d_k / e_k^2: da/de = -2 a / e
@@ -64,24 +68,29 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
   } else {
     // a_k = d_k (1 + r_k^2), r_k = tau / e_k
     const double gr0 = ga0 * 0.2 * r0, gr1 = ga1 * 1.2 * r1, gr2 = ga2 * 0.6 * r2;
-    const double gtau = gr0 * i0 + gr1 * i1 + gr2 * i2;
+    const double gtau = fma(gr2, i2, fma(gr1, i1, gr0 * i0));
     ge0 = -gr0 * r0 * i0;
     ge1 = -gr1 * r1 * i1;
     ge2 = -gr2 * r2 * i2;
-    gb0 += sg * gtau;
-    gb2 -= sg * gtau;
+    gb0 = sg * gtau;
+    gb2 = -gb0;
   }
   gb0 += ge0;
   const double gb1 = ge1;
   gb2 += ge2;
-  const double gt0 = gb0 * 2.0 * k1312 * t0, gs0 = gb0 * 0.5 * s0;
-  const double gt1 = gb1 * 2.0 * k1312 * t1, gs1 = gb1 * 0.5 * s1;
-  const double gt2 = gb2 * 2.0 * k1312 * t2, gs2 = gb2 * 0.5 * s2;
-  gq[0] = 2.0 * gC0 + gt0 + gs0;
-  gq[1] = -7.0 * gC0 - gC1 - 2.0 * gt0 - 4.0 * gs0 + gt1 + gs1;
-  gq[2] = 11.0 * gC0 + 5.0 * gC1 + 2.0 * gC2 + gt0 + 3.0 * gs0 - 2.0 * gt1 + gt2 + 3.0 * gs2;
-  gq[3] = 2.0 * gC1 + 5.0 * gC2 + gt1 - gs1 - 2.0 * gt2 - 4.0 * gs2;
-  gq[4] = -gC2 + gt2 + gs2;
+  // b_k = (13/3) t_k^2 + s_k^2: gt_k = gb_k (26/3) t_k, gs_k = 2 gb_k s_k, folded below as
+  // u_k = gb_k t_k and v_k = gb_k s_k with the factors in the coefficients
+  const double u0 = gb0 * t0, v0 = gb0 * s0;
+  const double u1 = gb1 * t1, v1 = gb1 * s1;
+  const double u2 = gb2 * t2, v2 = gb2 * s2;
+  constexpr double T = 2.0 * K4;
+  gq[0] = fma(2.0, gC0, fma(T, u0, 2.0 * v0));
+  gq[1] = fma(-7.0, gC0, -gC1) + fma(-2.0 * T, u0, fma(-8.0, v0, fma(T, u1, 2.0 * v1)));
+  gq[3] = fma(2.0, gC1, 5.0 * gC2) + fma(T, u1, fma(-2.0, v1, fma(-2.0 * T, u2, -8.0 * v2)));
+  gq[4] = -gC2 + fma(T, u2, 2.0 * v2);
+  // translation: f(q + c) = f(q) + c, so the five partial derivatives sum to one and the
+  // cotangents to g_out; the centre one follows from the other four
+  gq[2] = g_out - ((gq[0] + gq[1]) + (gq[3] + gq[4]));
 }
 
 // ------------------------------------------------------------------------------------------------
