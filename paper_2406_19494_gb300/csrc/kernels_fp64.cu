@@ -671,10 +671,14 @@ void face_shape(int D, const Geo& g, int& block, int& seg, int& grid) {
   if (block <= 0) block = 128;
   if (seg <= 0) {
     // longest segment (fewest redundant faces) that still gives >= 4 blocks of 128 per SM, down
-    // to 4 cells (small 2-D grids such as the 512 x 128 boundary layer: segments of 4 take 40 %
-    // less time than 8, segments of 2 more than 4); the result does not depend on the choice
+    // to 8 cells; 4 cells only where segments of 8 would leave SMs without a block (small 2-D
+    // grids such as the 512 x 128 boundary layer: there segments of 4 take 40 % less time than 8,
+    // while on TGV 64^3, which 8 already spreads over every SM, they take 14 % more).  The result
+    // does not depend on the choice.
     seg = 64;
-    while (seg > 4 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
+    auto threads = [&](int sg) { return lines * ((g.n[D] + sg - 1) / sg); };
+    while (seg > 8 && threads(seg) < 152LL * 4 * 128) seg >>= 1;
+    if (seg == 8 && threads(8) < 152LL * 128) seg = 4;
   }
   grid = grid_for(lines * ((g.n[D] + seg - 1) / seg), block);
 }
