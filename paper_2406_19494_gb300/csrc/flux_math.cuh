@@ -75,27 +75,11 @@ FL_HD double weno5_beta(double qm2, double qm1, double q0, double qp1, double qp
 // serves both faces, and weno_x_value forms the value from the stencil's centre and cell
 // differences and the X's, with the linear weights d_k and 1/6 folded into the candidate
 // coefficients.
-template <int SCHEME>
-FL_HD void weno_x(double b0, double b1, double b2, double eps, double X[3]) {
-  const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps;
-  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
-  if (SCHEME == FLUID_WENO_JS) {
-    X[0] = Q0 * Q0; X[1] = Q1 * Q1; X[2] = Q2 * Q2;
-  } else {
-    const double tau = fabs(b0 - b2);
-    const double P = e0 * Q0;
-    const double PP = P * P;
-    const double T0 = tau * Q0, T1 = tau * Q1, T2 = tau * Q2;
-    X[0] = fma(T0, T0, PP);
-    X[1] = fma(T1, T1, PP);
-    X[2] = fma(T2, T2, PP);
-  }
-}
 
-// weno_x for indicators that already include epsilon: e_k = beta_k + eps (so that
-// tau = |e0 - e2| = |beta0 - beta2|)
+// The scaled weights X_k of an indicator set whose members already include epsilon,
+// e_k = beta_k + eps (so that tau = |e0 - e2| = |beta0 - beta2|)
 template <int SCHEME>
-FL_HD void weno_x_e(double e0, double e1, double e2, double X[3]) {
+FL_HD void weno_x(double e0, double e1, double e2, double X[3]) {
   const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
   if (SCHEME == FLUID_WENO_JS) {
     X[0] = Q0 * Q0; X[1] = Q1 * Q1; X[2] = Q2 * Q2;
@@ -123,13 +107,6 @@ FL_HD double weno_x_value(double q0, double dm2, double dm1, double dp0, double 
   const double num = fma(X[2], C2, fma(X[1], C1, X[0] * C0));
   const double den = fma(3.0, X[2], fma(6.0, X[1], X[0]));
   return fma(num, fl_rcp(den), q0);
-}
-
-// 13/12 t^2 with t the second difference of a three-cell stencil: the part the three indicator
-// positions A, B, C of one stencil have in common (A = K + s_A^2 / 4 and so on)
-FL_HD double weno_k(double a, double b, double c) {
-  const double t = fma(-2.0, b, a) + c;
-  return k1312 * t * t;
 }
 
 // WENO5 (Jiang & Shu; Borges et al. Z variant): left-biased value at i+1/2 from q_{i-2..i+2}

@@ -229,7 +229,7 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
                                           double F[5], double xl[5][3], double k0[5], double k1[5]) {
   // Carried along the march, per primitive: xl, the scaled weights (weno_x) of the left-biased
   // value at this face, whose indicator set (A_{a-1}, B_a, C_{a+1}) was the right-biased set of
-  // the previous face; k0, k1 = 4 weno_k + 4 eps of the stencils centred at a and a+1 (epsilon
+  // the previous face; k0, k1 = (13/3) t^2 + 4 eps of the stencils centred at a and a+1 (epsilon
   // enters each indicator through its stencil's carried term).  The right-biased value needs
   // C_{a+2}, B_{a+1}, A_a: one new stencil (centred at a+2) per face.
   // The indicators are taken times 4 (13/3 t^2 + s^2) with epsilon times 4: the weights of
@@ -248,7 +248,7 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
     const double d0 = q[v][1] - q[v][0], d1 = q[v][2] - q[v][1], d2 = q[v][3] - q[v][2];
     const double d3 = q[v][4] - q[v][3], d4 = q[v][5] - q[v][4];
     const double t2 = d4 - d3;
-    const double k2 = fma((4.0 * k1312) * t2, t2, eps4);   // 4 weno_k + 4 eps, cells a+1 .. a+3
+    const double k2 = fma((4.0 * k1312) * t2, t2, eps4);   // (13/3) t^2 + 4 eps, cells a+1 .. a+3
     const double sA = fma(3.0, d2, -d1);                   // q_{a-1} - 4 q_a + 3 q_{a+1}
     const double sB = d2 + d3;                             // -(q_a - q_{a+2})
     const double sC = fma(-3.0, d3, d4);                   // 3 q_{a+1} - 4 q_{a+2} + q_{a+3}
@@ -257,7 +257,7 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
     const double Cn = fma(sC, sC, k2);                     // 4 (C_{a+2} + eps)
     wl[v] = weno_x_value(q[v][2], d0, d1, d2, d3, xl[v]);
     double xr[3];
-    weno_x_e<SCHEME>(Cn, Bn, An, xr);
+    weno_x<SCHEME>(Cn, Bn, An, xr);
     // mirrored stencil: centre q_{a+1}, differences -d4, -d3, -d2, -d1
     wr[v] = weno_x_value(q[v][3], -d4, -d3, -d2, -d1, xr);
     xl[v][0] = xr[2];
@@ -272,7 +272,7 @@ __device__ __forceinline__ void face_flux(const double* __restrict__ W, const do
 
 // The carried terms with which the march arrives at face a+1/2, formed by the operations the
 // march itself uses at face a-1/2 from cells a-2 .. a+2 (q[0..4]): the scaled weights xl of the
-// left-biased set (A_{a-1}, B_a, C_{a+1}) and k0, k1 = 4 weno_k + 4 eps of the stencils centred at
+// left-biased set (A_{a-1}, B_a, C_{a+1}) and k0, k1 = (13/3) t^2 + 4 eps of the stencils centred at
 // a and a+1.  A segment start therefore continues bit for bit as if the march had come from
 // further back, and the right-hand side does not depend on the segment length.
 template <int SCHEME>
@@ -286,7 +286,7 @@ __device__ __forceinline__ void march_start(const double q[5], double eps4, doub
   k1 = fma(c * t3, t3, eps4);                               // centred at a+1
   const double sA = fma(3.0, d2, -d1), sB = d2 + d3, sC = fma(-3.0, d3, d4);
   double xr[3];
-  weno_x_e<SCHEME>(fma(sC, sC, k1), fma(sB, sB, k0), fma(sA, sA, km), xr);
+  weno_x<SCHEME>(fma(sC, sC, k1), fma(sB, sB, k0), fma(sA, sA, km), xr);
   xl[0] = xr[2];
   xl[1] = xr[1];
   xl[2] = xr[0];
