@@ -25,7 +25,8 @@ template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
                                                double F[5], int lev[5][3], double b3[5][3],
-                                               double kk[5][2], const double (*omega)[16]) {
+                                               double i3[5][3], double kk[5][2],
+                                               const double (*omega)[16]) {
   const int nc = g.ncell;
   double q[5][6];
 #pragma unroll
@@ -38,7 +39,7 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
     // cells a-2 .. a+3 are q[v][0..5]; the sensor level of cell a+2 is the new one
     const int l3 = teno::sensor_level(q[v][4] - q[v][3], q[v][5] - q[v][4]);
     const double ct = teno::cutoff_of_level(min(min(lev[v][0], lev[v][1]), min(lev[v][2], l3)));
-    teno::face_states(q[v], ct, b3[v], kk[v], omega, wl[v], wr[v]);
+    teno::face_states(q[v], ct, b3[v], i3[v], kk[v], omega, wl[v], wr[v]);
     lev[v][0] = lev[v][1];
     lev[v][1] = lev[v][2];
     lev[v][2] = l3;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], b3[5][3], kk[5][2];
+    double Fp[5], F[5], b3[5][3], i3[5][3], kk[5][2];
     int lev[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -109,11 +110,13 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
       b3[v][2] = fma(0.25 * sC, sC, Km);
       kk[v][0] = Ka;
       kk[v][1] = Kb;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) i3[v][j] = teno::rcp6(b3[v][j]);
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, kk, omega);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, i3, kk, omega);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, kk, omega);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, i3, kk, omega);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

@@ -72,19 +72,24 @@ FL_HD void weight_entry(int i, double omega[4][16]) {
   omega[k][mask] = ((mask >> k) & 1) ? lin_weight(k) / (den * (k < 3 ? 6.0 : 12.0)) : 0.0;
 }
 
-// TENO6 value from the candidates p_k (times 6, the four-cell one times 12) and smoothness measures
-// b_k (b6 = 6 beta6): stencil k is kept
+// TENO6 value from the candidates p_k (times 6, the four-cell one times 12), the three-cell
+// smoothness measures b_k and i_k = rcp6(b_k) of all four (b6 = 6 beta6): stencil k is kept
 // unless gamma_k / sum gamma < C_T, and the value is the kept candidates' combination with the
 // normalised weights of omega (weight_entry)
+// 1 / (6 (beta + eps)), the factor of tau in gamma_k
+FL_HD double rcp6(double beta) { return rcp_decide(fma(6.0, beta, 6.0 * kEps)); }
+
 FL_HD double combine(double p0, double p1, double p2, double p3, double b0, double b1, double b2,
-                     double b3, double b6, double ct, const double (*omega)[16]) {
-  // b6 is 6 beta6 (beta6_pair), so tau = 6 tau6 and gamma_k = (1 + tau / (6 (beta_k + eps)))^6
+                     double i0, double i1, double i2, double i3, double b6, double ct,
+                     const double (*omega)[16]) {
+  // b6 is 6 beta6 (beta6_pair), so tau = 6 tau6 and gamma_k = (1 + tau / (6 (beta_k + eps)))^6;
+  // i_k = rcp6(beta_k)
   const double tau = fabs(b6 - fma(4.0, b0, b1 + b2));
   double g[4];
-  const double bk[4] = {b0, b1, b2, b3};
+  const double ik[4] = {i0, i1, i2, i3};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double x = fma(tau, rcp_decide(fma(6.0, bk[k], 6.0 * kEps)), 1.0);
+    const double x = fma(tau, ik[k], 1.0);
     const double x2 = x * x;
     g[k] = x2 * x2 * x2;
   }
@@ -99,8 +104,9 @@ FL_HD double combine(double p0, double p1, double p2, double p3, double b0, doub
 //   * the right state's three-cell measures (B of the stencil centred at a+1, A at a, C at a+2) are
 //     the next face's left-state measures (B at a+1, C at a+2, A at a): b3c carries them as
 //     (beta0, beta1, beta2) of that next left state.
-// On entry b3c holds this face's left-state (beta0, beta1, beta2); on exit the next face's.
-FL_HD void face_states(const double q[6], double ct, double b3c[3], double kk[2],
+// On entry b3c holds this face's left-state (beta0, beta1, beta2) and i3c their rcp6; on exit the
+// next face's.
+FL_HD void face_states(const double q[6], double ct, double b3c[3], double i3c[3], double kk[2],
                        const double (*omega)[16], double& wl, double& wr) {
   // candidates times 6 (three cells) and 12 (four cells); the factors are in omega
   const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1]));       // cells a-1..a+1
@@ -111,7 +117,8 @@ FL_HD void face_states(const double q[6], double ct, double b3c[3], double kk[2]
   // 6 beta6 of the window and of its mirror image together (the reversal negates the odd part)
   double b6l, b6r;
   beta6_pair(q, b6l, b6r);
-  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], beta4_form(e4), b6l, ct, omega);
+  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], i3c[0], i3c[1], i3c[2], rcp6(beta4_form(e4)),
+               b6l, ct, omega);
   // right state: the mirrored stencil q'_j = q[5 - j]
   const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5]));
   const double r4 = q[0] + fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]));
@@ -126,11 +133,16 @@ FL_HD void face_states(const double q[6], double ct, double b3c[3], double kk[2]
   const double rb2 = fma(0.25 * sA, sA, K2);                // A of (q3, q4, q5)
   kk[0] = kk[1];
   kk[1] = K2;
-  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, beta4_form(f4), b6r, ct, omega);
-  // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at a (rb1's)
+  const double ib0 = rcp6(rb0), ib1 = rcp6(rb1), ib2 = rcp6(rb2);
+  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, ib0, ib1, ib2, rcp6(beta4_form(f4)), b6r, ct, omega);
+  // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at
+  // a (rb1's), with their reciprocal factors
   b3c[0] = rb0;
   b3c[1] = rb2;
   b3c[2] = rb1;
+  i3c[0] = ib0;
+  i3c[1] = ib2;
+  i3c[2] = ib1;
 }
 
 }  // namespace teno

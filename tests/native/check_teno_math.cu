@@ -21,7 +21,8 @@ int main() {
     const double ta = std::fma(-2.0, q[2], q[1]) + q[3], tb = std::fma(-2.0, q[3], q[2]) + q[4];
     double kk[2] = {fl::k1312 * ta * ta, fl::k1312 * tb * tb};
     double wl, wr;
-    fl::teno::face_states(q, ct, b3c, kk, omega, wl, wr);
+    double i3c[3] = {fl::teno::rcp6(b3c[0]), fl::teno::rcp6(b3c[1]), fl::teno::rcp6(b3c[2])};
+    fl::teno::face_states(q, ct, b3c, i3c, kk, omega, wl, wr);
     std::printf("%.17g %.17g %.17g\n", wl, wr, ct);
   }
   return 0;
