@@ -5,12 +5,14 @@
 //   k_prim_bc   primitives (rho, u, v, w, p, T) of every padded cell; halo cells are built directly
 //               from interior cells by composing the boundary maps of the active axes in x, y, z
 //               order (Section 3.2: halo cells take values assigned by the boundary conditions)
-//   k_grad      fourth-order central velocity gradients at cell centres (tangential derivatives of
-//               the dissipative fluxes)
+//   k_grad      fourth- or sixth-order central velocity gradients at cell centres (tangential
+//               derivatives of the dissipative fluxes)
 //   k_face<D>   per axis D: WENO5 reconstruction of the primitives, HLLC convective flux, the
 //               dissipative flux at the same face, and the flux difference -(F+ - F-)/dx into R.
 //               One thread marches along a segment of a grid line so each face is computed once
-//               and reused by the two cells that share it.
+//               and reused by the two cells that share it; a segment starts with the carried
+//               terms formed by the march's own operations (march_start), so the result is the
+//               same for every segment length.
 //   k_source / k_stage   body-force source, RK3 stage combination, non-finite check
 //   k_stage_prim / k_halo_prim   the stage combination fused with the primitives of its result
 //               (interior cells), then the halo cells from those; fluid_step uses this pair in

@@ -7,8 +7,11 @@
 // falls back, in all five primitives, to the cell on its side of the face.
 //
 // One thread marches along a segment of a grid line, as the WENO5 kernel does; each face is
-// computed once and serves the two cells that share it.  The scale sensors of the TENO-A cut-off
-// depend on single cells, so three of the four a face needs carry over from the previous face.
+// computed once and serves the two cells that share it.  The cut-off levels of the TENO-A scale
+// sensors depend on single cells, so three of the four a face needs carry over from the previous
+// face, as do the right state's three-cell measures (the next left state's) and their factors.  A
+// segment starts with the terms the march would have carried there, formed by the same
+// operations, so the result is the same for every segment length.
 #include <cuda_runtime.h>
 
 #include "fluid_internal.cuh"
