@@ -621,6 +621,21 @@ def _oracle_sample(case_dict):
     return nf, sc, sg, Us
 
 
+def host_cpu():
+    """The host's logical CPU count and model (from /proc/cpuinfo where it names one)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key, _, val = line.partition(":")
+            if key.strip() in ("model name", "Model", "Hardware") and val.strip():
+                model = val.strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"host_cpus": os.cpu_count(), "host_cpu": model or platform.machine()}
+
+
 def cpu_baseline(args, case_dict, samples=1):
     nf, sc, sg, Us = _oracle_sample(case_dict)
     cells = sc.n[0] * sc.n[1] * sc.n[2]
@@ -629,9 +644,9 @@ def cpu_baseline(args, case_dict, samples=1):
         for _stage in range(3):
             nf.rhs_filled(Us, sc, sg)
     dt = (time.perf_counter() - t0) / samples
-    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the same "
-                      "state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2])}
+    return dict({"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": "3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the "
+                           "same state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2])}, **host_cpu())
 
 
 def run_reference(args):
@@ -657,7 +672,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": describe(args.workload, case), "impl": "reference",
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                                **host_cpu()),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

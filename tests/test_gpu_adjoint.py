@@ -121,6 +121,28 @@ def test_rhs_adjoint_matches_complex_step(name):
     assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs)
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_adjoint_matches_differences_of_the_gpu_forward(name):
+    """The dot-product identity <mu, (dR/dU) dU> = <(dR/dU)^T mu, dU> with the left side from
+    central differences of the GPU right-hand side itself (fluid_rhs), so the adjoint kernels are
+    checked against the kernels they differentiate, not only against the oracle."""
+    c, case, grid, U, phi, inflow = _setup(name, seed=4)
+    rng = np.random.default_rng(13)
+    mu = _interior_random(case, rng, U.shape)
+    dU = _interior_random(case, rng, U.shape) * np.abs(U).max(axis=(1, 2, 3))[:, None, None, None] * 0.1
+    s = _solver(c, phi, inflow)
+    h = 1e-6
+    Rp = s.rhs(torch.from_numpy(U + h * dU).cuda()).cpu().numpy()
+    Rm = s.rhs(torch.from_numpy(U - h * dU).cuda()).cpu().numpy()
+    inner = (slice(None),) + case.interior()
+    jvp = (Rp - Rm)[inner] / (2 * h)
+    lhs = float(np.sum(mu[inner] * jvp))
+    gU = s.adjoint_rhs(torch.from_numpy(U).cuda(), torch.from_numpy(mu).cuda()).cpu().numpy()
+    rhs = float(np.sum(gU[inner] * dU[inner]))
+    scale = float(np.sum(np.abs(mu[inner] * jvp))) + 1e-300
+    assert abs(lhs - rhs) <= 1e-6 * scale, (lhs, rhs)
+
+
 @pytest.mark.parametrize("stored_stages", [False, True])
 @pytest.mark.parametrize("name", ["bl2d_porous_inflow", "channel3d_walls_force_js"])
 def test_step_adjoint_matches_complex_step(name, stored_stages):
