@@ -8,63 +8,12 @@ sympy, available on the development machine only).  Run from this directory:
 For a stencil of cells with unit width centred at the integer offsets s (x measured from the centre
 of the target cell), the reconstruction polynomial P has the stencil's cell averages, and
 beta = sum_{l >= 1} int_{-1/2}^{1/2} (P^(l))^2 dx.  beta vanishes on constants, so it is written as
-a quadratic form in the differences e_j = q_{s_j} - q_{s_0} (j >= 1): beta = sum_{j<=k} c_jk e_j e_k
-/ den with integer c_jk, emitted as a function of the differences.
+a quadratic form in the consecutive cell differences of the stencil (the marching kernel carries
+them from face to face); the six-cell measures of a window and of its mirror image are emitted as
+one pair.  Every emitted form is checked here, exactly, against the definition.  The header also
+holds the adaptive cut-off of TENO-A as thresholds on the scale sensor.
 """
 import sympy as sp
-
-
-def quadratic_form(offsets):
-    x = sp.symbols("x")
-    n = len(offsets)
-    a = sp.symbols("a0:%d" % n)
-    q = sp.symbols("q0:%d" % n)
-    P = sum(a[m] * x ** m for m in range(n))
-    eqs = [sp.integrate(P, (x, o - sp.Rational(1, 2), o + sp.Rational(1, 2))) - q[j]
-           for j, o in enumerate(offsets)]
-    sol = sp.solve(eqs, a, dict=True)[0]
-    Pq = P.subs(sol)
-    beta = sum(sp.integrate(sp.diff(Pq, x, l) ** 2, (x, -sp.Rational(1, 2), sp.Rational(1, 2)))
-               for l in range(1, n))
-    e = sp.symbols("e1:%d" % n)
-    beta = sp.expand(beta.subs({q[j]: q[0] + e[j - 1] for j in range(1, n)}))
-    assert beta.free_symbols <= set(e)
-    poly = sp.Poly(beta, *e)
-    den = sp.ilcm(*[sp.fraction(c)[1] for c in poly.coeffs()])
-    terms = []
-    for j in range(n - 1):
-        for k in range(j, n - 1):
-            mono = [0] * (n - 1)
-            mono[j] += 1
-            mono[k] += 1
-            terms.append((j, k, int(poly.coeff_monomial(tuple(mono)) * den)))
-    return int(den), terms
-
-
-def emit(name, offsets):
-    den, terms = quadratic_form(offsets)
-    n = len(offsets) - 1
-    print("// %s: cells %s (offsets from the target cell), e[j-1] = q_{s_j} - q_{s_0}, j = 1 .. %d:"
-          % (name, offsets, n))
-    print("// beta = sum_{j<=k} c_jk e_j e_k / %d, grouped by rows: sum_j e_j (sum_{k>=j} c_jk e_k / %d)"
-          % (den, den))
-    print("// (the coefficients c_jk / %d rounded to FP64)." % den)
-    print("FL_HD double %s(const double e[%d]) {" % (name, n))
-    rows = []
-    f = lambda c: "%r" % (float(sp.Rational(c, den)))
-    for j in range(n):
-        row = [(k, c) for (jj, k, c) in terms if jj == j]
-        expr = "%s * e[%d]" % (f(row[0][1]), row[0][0])
-        for k, c in row[1:]:
-            expr = "fma(%s, e[%d], %s)" % (f(c), k, expr)
-        print("  const double r%d = %s;" % (j, expr))
-        rows.append(j)
-    acc = "e[0] * r0"
-    for j in rows[1:]:
-        acc = "fma(e[%d], r%d, %s)" % (j, j, acc)
-    print("  return %s;" % acc)
-    print("}")
-    print()
 
 
 def beta_matrix(offsets):
@@ -83,72 +32,83 @@ def beta_matrix(offsets):
     return sp.Matrix(n, n, lambda i, j: sp.Rational(1, 2) * sp.diff(beta, q[i], q[j])), q, beta
 
 
-def emit_pair(name, offsets, scale=6):
-    """Both smoothness measures of a six-cell window and of its mirror image, the form evaluated on
-    q and on (q5, .., q0).  With u_j = q_j + q_{5-j} and v_j = q_j - q_{5-j} (j = 0, 1, 2), the
-    reversal leaves u and negates v, so beta(q) = S + T + 2 X and beta(Jq) = S + T - 2 X with S a
-    form in u, T a form in v and X bilinear; S and X vanish on constants, so they are written in
-    a_k = u_k - u_0 (k = 1, 2)."""
-    A, q, beta = beta_matrix(offsets)
-    n = len(offsets)
-    assert n == 6 and all(offsets[j] + offsets[5 - j] == 1 for j in range(3))   # symmetric about the face
-    u = sp.symbols("u0:3")
-    v = sp.symbols("v0:3")
-    sub = {}
-    for j in range(3):
-        sub[q[j]] = (u[j] + v[j]) / 2
-        sub[q[5 - j]] = (u[j] - v[j]) / 2
-    bq = sp.expand(beta.subs(sub, simultaneous=True))
-    a1, a2 = sp.symbols("a1 a2")
-    bq = sp.expand(bq.subs({u[1]: u[0] + a1, u[2]: u[0] + a2}, simultaneous=True))
-    assert u[0] not in bq.free_symbols
-    poly = sp.Poly(bq, a1, a2, *v)
-    coeff = lambda mono: poly.coeff_monomial(mono)
-    # S = s11 a1^2 + s12 a1 a2 + s22 a2^2; X = sum x_kj a_k v_j (the part odd in v, halved);
-    # T = sum_{i<=j} t_ij v_i v_j
-    S = {(1, 1): coeff((2, 0, 0, 0, 0)), (1, 2): coeff((1, 1, 0, 0, 0)), (2, 2): coeff((0, 2, 0, 0, 0))}
-    X = {}
-    for k in (1, 2):
-        for j in range(3):
-            mono = [0] * 5
-            mono[k - 1] = 1
-            mono[2 + j] = 1
-            X[(k, j)] = coeff(tuple(mono)) / 2
-    T = {}
-    for i in range(3):
-        for j in range(i, 3):
-            mono = [0] * 5
-            mono[2 + i] += 1
-            mono[2 + j] += 1
-            T[(i, j)] = coeff(tuple(mono))
-    # exact check: the pair reproduces the form on the window and on its mirror image
-    qs = sp.symbols("w0:6")
-    us = [qs[j] + qs[5 - j] for j in range(3)]
-    vs = [qs[j] - qs[5 - j] for j in range(3)]
-    A1, A2 = us[1] - us[0], us[2] - us[0]
-    Sv = S[(1, 1)] * A1 ** 2 + S[(1, 2)] * A1 * A2 + S[(2, 2)] * A2 ** 2
-    Xv = sum(X[(k, j)] * (A1 if k == 1 else A2) * vs[j] for k in (1, 2) for j in range(3))
-    Tv = sum(T[(i, j)] * vs[i] * vs[j] for i in range(3) for j in range(i, 3))
-    bL = beta.subs(dict(zip(q, qs)), simultaneous=True)
-    bR = beta.subs(dict(zip(q, reversed(qs))), simultaneous=True)
-    assert sp.expand(Sv + Tv + 2 * Xv - bL) == 0 and sp.expand(Sv + Tv - 2 * Xv - bR) == 0
-    f = lambda c: "%r" % float(scale * c)
-    print("// %s: %d times the TENO6 measure of the window q[0..5] (cells %s around the target cell)"
-          % (name, scale, offsets))
-    print("// and of its mirror image (q[5..0]): bL = S + T + 2 X, bR = S + T - 2 X with u_j = q_j + q_{5-j},")
-    print("// v_j = q_j - q_{5-j}, a_k = u_k - u_0; coefficients are %d times the exact rationals, rounded" % scale)
-    print("// to FP64 (the factor is the 6 of tau6 = |beta6 - (beta1 + beta2 + 4 beta0) / 6|).")
-    print("FL_HD void %s(const double q[6], double& bL, double& bR) {" % name)
-    print("  // a_k from differences of neighbouring values, exact for close values, never from the sums u_k")
-    print("  const double a1 = (q[1] - q[0]) + (q[4] - q[5]), a2 = (q[2] - q[0]) + (q[3] - q[5]);")
-    print("  const double v0 = q[0] - q[5], v1 = q[1] - q[4], v2 = q[2] - q[3];")
-    print("  const double S = fma(a1, fma(%s, a2, %s * a1), (%s * a2) * a2);" % (f(S[(1, 2)]), f(S[(1, 1)]), f(S[(2, 2)])))
-    print("  const double t0 = fma(%s, v2, fma(%s, v1, %s * v0));" % (f(T[(0, 2)]), f(T[(0, 1)]), f(T[(0, 0)])))
-    print("  const double t1 = fma(%s, v2, %s * v1);" % (f(T[(1, 2)]), f(T[(1, 1)])))
-    print("  const double T = fma(v2, %s * v2, fma(v1, t1, v0 * t0));" % f(T[(2, 2)]))
-    print("  const double x1 = fma(%s, v2, fma(%s, v1, %s * v0));" % (f(2 * X[(1, 2)]), f(2 * X[(1, 1)]), f(2 * X[(1, 0)])))
-    print("  const double x2 = fma(%s, v2, fma(%s, v1, %s * v0));" % (f(2 * X[(2, 2)]), f(2 * X[(2, 1)]), f(2 * X[(2, 0)])))
-    print("  const double X2 = fma(a2, x2, a1 * x1);")
+def emit_diff_forms():
+    """The four-cell measure and the paired six-cell measures written in the consecutive cell
+    differences d_j = q_{j+1} - q_j of the six-cell window q[0..5] (d[0..4]), the form the marching
+    kernel carries (one new difference per face).
+      * beta4 of cells (0, 1, 2, 3) around target 0 is a form Q in (d_0, d_1, d_2) of those cells;
+        the left state's is Q(d2, d3, d4), the right state's (mirror image, cells q3, q2, q1, q0)
+        Q(d2, d1, d0) (a quadratic form is even, so the signs of the mirrored differences drop).
+      * the reversal of the window maps d_j to -d_{4-j}; with the even combinations
+        u0 = d0 + d4, u1 = d1 + d3, u2 = d2 and the odd ones w0 = d0 - d4, w1 = d1 - d3,
+        6 beta6 of the window is S + T + 2 X and of its mirror S + T - 2 X (S a form in u, T in w,
+        X bilinear).  Both are checked exactly against the row forms above."""
+    # beta4 in consecutive differences
+    A, q, beta = beta_matrix((0, 1, 2, 3))
+    d = sp.symbols("d0:3")
+    sub = {q[0]: 0, q[1]: d[0], q[2]: d[0] + d[1], q[3]: d[0] + d[1] + d[2]}
+    b4 = sp.expand(beta.subs(sub, simultaneous=True))
+    P4 = sp.Poly(b4, *d)
+    c4 = {(i, j): P4.coeff_monomial(tuple(int(k == i) + int(k == j) for k in range(3)))
+          for i in range(3) for j in range(i, 3)}
+    # paired beta6 in consecutive differences
+    A6, q6, beta6 = beta_matrix((-2, -1, 0, 1, 2, 3))
+    dd = sp.symbols("e0:5")
+    sub6 = {q6[0]: 0}
+    acc = 0
+    for j in range(5):
+        acc = acc + dd[j]
+        sub6[q6[j + 1]] = acc
+    bL = sp.expand(6 * beta6.subs(sub6, simultaneous=True))
+    rev = {dd[j]: -dd[4 - j] for j in range(5)}
+    bR = sp.expand(bL.subs(rev, simultaneous=True))
+    u0, u1, u2, w0, w1 = sp.symbols("u0 u1 u2 w0 w1")
+    inv = {dd[0]: (u0 + w0) / 2, dd[4]: (u0 - w0) / 2, dd[1]: (u1 + w1) / 2, dd[3]: (u1 - w1) / 2, dd[2]: u2}
+    even = sp.expand(((bL + bR) / 2).subs(inv, simultaneous=True))
+    odd = sp.expand(((bL - bR) / 4).subs(inv, simultaneous=True))      # X, with bL = S + T + 2 X
+    PE = sp.Poly(even, u0, u1, u2, w0, w1)
+    PO = sp.Poly(odd, u0, u1, u2, w0, w1)
+    mono = lambda **k: tuple(k.get(n, 0) for n in ("u0", "u1", "u2", "w0", "w1"))
+    S = {}
+    for i, a in enumerate(("u0", "u1", "u2")):
+        for b in ("u0", "u1", "u2")[i:]:
+            m = {a: 1}
+            m[b] = m.get(b, 0) + 1
+            S[(a, b)] = PE.coeff_monomial(mono(**m))
+    T = {("w0", "w0"): PE.coeff_monomial(mono(w0=2)), ("w0", "w1"): PE.coeff_monomial(mono(w0=1, w1=1)),
+         ("w1", "w1"): PE.coeff_monomial(mono(w1=2))}
+    X = {(a, b): PO.coeff_monomial(mono(**{a: 1, b: 1})) for a in ("u0", "u1", "u2") for b in ("w0", "w1")}
+    # exact checks against the definitions
+    Sv = sum(c * sp.Symbol(a) * sp.Symbol(b) for (a, b), c in S.items())
+    Tv = sum(c * sp.Symbol(a) * sp.Symbol(b) for (a, b), c in T.items())
+    Xv = sum(c * sp.Symbol(a) * sp.Symbol(b) for (a, b), c in X.items())
+    back = {u0: dd[0] + dd[4], u1: dd[1] + dd[3], u2: dd[2], w0: dd[0] - dd[4], w1: dd[1] - dd[3]}
+    assert sp.expand((Sv + Tv + 2 * Xv).subs(back, simultaneous=True) - bL) == 0
+    assert sp.expand((Sv + Tv - 2 * Xv).subs(back, simultaneous=True) - bR) == 0
+    assert sp.expand(sum(c * d[i] * d[j] for (i, j), c in c4.items()) - b4) == 0
+    f = lambda c: "%r" % float(c)
+    print("// beta4_diff: beta4 of cells (0, 1, 2, 3) around target 0 in the consecutive differences")
+    print("// of those cells, d[0..2]; coefficients are the exact rationals rounded to FP64.")
+    print("FL_HD double beta4_diff(double d0, double d1, double d2) {")
+    print("  const double r0 = fma(%s, d2, fma(%s, d1, %s * d0));" % (f(c4[(0, 2)]), f(c4[(0, 1)]), f(c4[(0, 0)])))
+    print("  const double r1 = fma(%s, d2, %s * d1);" % (f(c4[(1, 2)]), f(c4[(1, 1)])))
+    print("  return fma(d2, %s * d2, fma(d1, r1, d0 * r0));" % f(c4[(2, 2)]))
+    print("}")
+    print()
+    print("// beta6_pair_diff: 6 beta6 of the window q[0..5] and of its mirror image from the window's")
+    print("// consecutive differences d[0..4]: bL = S + T + 2 X, bR = S + T - 2 X with u0 = d0 + d4,")
+    print("// u1 = d1 + d3, u2 = d2, w0 = d0 - d4, w1 = d1 - d3 (the reversal keeps u and negates w).")
+    print("FL_HD void beta6_pair_diff(const double d[5], double& bL, double& bR) {")
+    print("  const double u0 = d[0] + d[4], u1 = d[1] + d[3], u2 = d[2];")
+    print("  const double w0 = d[0] - d[4], w1 = d[1] - d[3];")
+    print("  const double s0 = fma(%s, u2, fma(%s, u1, %s * u0));" % (f(S[("u0", "u2")]), f(S[("u0", "u1")]), f(S[("u0", "u0")])))
+    print("  const double s1 = fma(%s, u2, %s * u1);" % (f(S[("u1", "u2")]), f(S[("u1", "u1")])))
+    print("  const double S = fma(u2, %s * u2, fma(u1, s1, u0 * s0));" % f(S[("u2", "u2")]))
+    print("  const double T = fma(w1, %s * w1, w0 * fma(%s, w1, %s * w0));" % (f(T[("w1", "w1")]), f(T[("w0", "w1")]), f(T[("w0", "w0")])))
+    print("  const double x0 = fma(%s, w1, %s * w0);" % (f(2 * X[("u0", "w1")]), f(2 * X[("u0", "w0")])))
+    print("  const double x1 = fma(%s, w1, %s * w0);" % (f(2 * X[("u1", "w1")]), f(2 * X[("u1", "w0")])))
+    print("  const double x2 = fma(%s, w1, %s * w0);" % (f(2 * X[("u2", "w1")]), f(2 * X[("u2", "w0")])))
+    print("  const double X2 = fma(u2, x2, fma(u1, x1, u0 * x0));")
     print("  const double ST = S + T;")
     print("  bL = ST + X2;")
     print("  bR = ST - X2;")
@@ -182,8 +142,7 @@ print("#define FL_HD __host__ __device__ __forceinline__")
 print("#endif")
 print("namespace fl {")
 print("namespace teno {")
-emit("beta4_form", (0, 1, 2, 3))
-emit_pair("beta6_pair", (-2, -1, 0, 1, 2, 3))
+emit_diff_forms()
 emit_cutoff_thresholds()
 print("}  // namespace teno")
 print("}  // namespace fl")

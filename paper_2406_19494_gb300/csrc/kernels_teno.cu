@@ -28,7 +28,7 @@ template <int D, int VORD>
 __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, const double* __restrict__ G,
                                                int cell, int s, int a, const Geo& g, const Phys& ph,
                                                double F[5], int lev[5][3], double b3[5][3],
-                                               double i3[5][3], double kk[5][2],
+                                               double i3[5][3], double kk[5][2], double dd[5][4],
                                                const double (*omega)[16]) {
   const int nc = g.ncell;
   double q[5][6];
@@ -39,10 +39,14 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
   double wl[5], wr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    // cells a-2 .. a+3 are q[v][0..5]; the sensor level of cell a+2 is the new one
-    const int l3 = teno::sensor_level(q[v][4] - q[v][3], q[v][5] - q[v][4]);
+    // cells a-2 .. a+3 are q[v][0..5]; their differences are dd[v][0..3] (carried) and the new
+    // d4; the sensor level of cell a+2 is the new one
+    const double d[5] = {dd[v][0], dd[v][1], dd[v][2], dd[v][3], q[v][5] - q[v][4]};
+    const int l3 = teno::sensor_level(d[3], d[4]);
     const double ct = teno::cutoff_of_level(min(min(lev[v][0], lev[v][1]), min(lev[v][2], l3)));
-    teno::face_states(q[v], ct, b3[v], i3[v], kk[v], omega, wl[v], wr[v]);
+    teno::face_states(q[v], d, ct, b3[v], i3[v], kk[v], omega, wl[v], wr[v]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dd[v][j] = d[j + 1];
     lev[v][0] = lev[v][1];
     lev[v][1] = lev[v][2];
     lev[v][2] = l3;
@@ -89,25 +93,29 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     const int a1 = min(a0 + seg, g.h[D] + nd);
     c[D] = a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    double Fp[5], F[5], b3[5][3], i3[5][3], kk[5][2];
+    double Fp[5], F[5], b3[5][3], i3[5][3], kk[5][2], dd[5][4];
     int lev[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      // sensors of cells a0-2, a0-1, a0 and the left-state three-cell measures of the first face
-      // a0 - 1/2 (f points at cell a0 - 1)
-      const double* f = W + v * nc + cell;
+      const double* f = W + v * nc + cell;                   // cell a0 - 1
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
-      lev[v][0] = teno::sensor_level(qm1 - qm2, q0 - qm1);
-      lev[v][1] = teno::sensor_level(q0 - qm1, qp1 - q0);
-      lev[v][2] = teno::sensor_level(qp1 - q0, qp2 - qp1);
-      // the three-cell measures and 13/12 t^2 terms the march carries into the first face, formed
-      // by the march's own operations (teno::face_states at the face before), so that a segment
-      // start continues bit for bit: K of the stencils centred at a-1, a, a+1 (a = a0 - 1), then
-      // B centred at a, A centred at a+1 and C centred at a-1
-      const double tm = fma(-2.0, qm1, qm2) + q0, ta = fma(-2.0, q0, qm1) + qp1, tb = fma(-2.0, qp1, q0) + qp2;
+      // the differences of cells a-2 .. a+2 (a = a0 - 1), and the terms the march carries into
+      // the first face formed by the march's own operations (teno::face_states at the face
+      // before), so that a segment start continues bit for bit: the sensor levels of cells a-1,
+      // a, a+1, K of the stencils centred at a-1, a, a+1, then B centred at a, A centred at a+1
+      // and C centred at a-1, with their reciprocal factors
+      const double D0 = qm1 - qm2, D1 = q0 - qm1, D2 = qp1 - q0, D3 = qp2 - qp1;
+      dd[v][0] = D0;
+      dd[v][1] = D1;
+      dd[v][2] = D2;
+      dd[v][3] = D3;
+      lev[v][0] = teno::sensor_level(D0, D1);
+      lev[v][1] = teno::sensor_level(D1, D2);
+      lev[v][2] = teno::sensor_level(D2, D3);
+      const double tm = D1 - D0, ta = D2 - D1, tb = D3 - D2;
       const double Km = k1312 * tm * tm, Ka = k1312 * ta * ta, Kb = k1312 * tb * tb;
-      const double sB = qp1 - qm1, sA = fma(-4.0, qp1, qp2) + 3.0 * q0, sC = fma(-4.0, qm1, 3.0 * q0) + qm2;
+      const double sB = D1 + D2, sA = fma(-3.0, D2, D3), sC = fma(3.0, D1, -D0);
       b3[v][0] = fma(0.25 * sB, sB, Ka);
       b3[v][1] = fma(0.25 * sA, sA, Kb);
       b3[v][2] = fma(0.25 * sC, sC, Km);
@@ -116,10 +124,10 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
 #pragma unroll
       for (int j = 0; j < 3; ++j) i3[v][j] = teno::rcp6(b3[v][j]);
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, i3, kk, omega);
+    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, i3, kk, dd, omega);
     for (int a = a0; a < a1; ++a) {
       cell += s;
-      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, i3, kk, omega);
+      face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, i3, kk, dd, omega);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {

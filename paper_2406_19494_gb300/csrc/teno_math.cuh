@@ -98,43 +98,48 @@ FL_HD double combine(double p0, double p1, double p2, double p3, double b0, doub
   return fma(omega[3][mask], p3, fma(omega[2][mask], p2, fma(omega[1][mask], p1, omega[0][mask] * p0)));
 }
 
-// Both states of the face a+1/2 from q[0..5] = q_{a-2} .. q_{a+3} while marching along +D.
+// Both states of the face a+1/2 from q[0..5] = q_{a-2} .. q_{a+3} and the window's consecutive
+// differences d[0..4] (d_j = q[j+1] - q[j]; the march carries d[0..3] and forms d[4]) while
+// marching along +D.
+//   * the candidates are written as offsets from 6 q_a (6 q_{a+1} for the mirrored stencil), the
+//     smoothness measures in the differences (beta4_diff, beta6_pair_diff);
 //   * the left state's central and downwind candidates are the right state's downwind and central
 //     ones (the same quadratics through cells a-1..a+1 and a..a+2, at the same point);
 //   * the right state's three-cell measures (B of the stencil centred at a+1, A at a, C at a+2) are
 //     the next face's left-state measures (B at a+1, C at a+2, A at a): b3c carries them as
-//     (beta0, beta1, beta2) of that next left state.
+//     (beta0, beta1, beta2) of that next left state, and kk the 13/12 t^2 parts of the stencils
+//     centred at a and a+1.
 // On entry b3c holds this face's left-state (beta0, beta1, beta2) and i3c their rcp6; on exit the
 // next face's.
-FL_HD void face_states(const double q[6], double ct, double b3c[3], double i3c[3], double kk[2],
-                       const double (*omega)[16], double& wl, double& wr) {
+FL_HD void face_states(const double q[6], const double d[5], double ct, double b3c[3], double i3c[3],
+                       double kk[2], const double (*omega)[16], double& wl, double& wr) {
   // candidates times 6 (three cells) and 12 (four cells); the factors are in omega
-  const double pc = fma(2.0, q[3], fma(5.0, q[2], -q[1]));       // cells a-1..a+1
-  const double pd = fma(-1.0, q[4], fma(5.0, q[3], 2.0 * q[2]));  // cells a..a+2
-  const double pu = fma(11.0, q[2], fma(-7.0, q[1], 2.0 * q[0]));
-  const double p4 = q[5] + fma(-5.0, q[4], fma(13.0, q[3], 3.0 * q[2]));
-  const double e4[3] = {q[3] - q[2], q[4] - q[2], q[5] - q[2]};
+  const double q6 = 6.0 * q[2], r6 = 6.0 * q[3];
+  const double pc = fma(2.0, d[2], d[1]) + q6;                  // cells a-1..a+1
+  const double pd = fma(4.0, d[2], -d[3]) + q6;                 // cells a..a+2
+  const double pu = fma(5.0, d[1], -2.0 * d[0]) + q6;
+  const double p4 = fma(9.0, d[2], fma(-4.0, d[3], d[4])) + 2.0 * q6;
   // 6 beta6 of the window and of its mirror image together (the reversal negates the odd part)
   double b6l, b6r;
-  beta6_pair(q, b6l, b6r);
-  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], i3c[0], i3c[1], i3c[2], rcp6(beta4_form(e4)),
-               b6l, ct, omega);
+  beta6_pair_diff(d, b6l, b6r);
+  wl = combine(pc, pd, pu, p4, b3c[0], b3c[1], b3c[2], i3c[0], i3c[1], i3c[2],
+               rcp6(beta4_diff(d[2], d[3], d[4])), b6l, ct, omega);
   // right state: the mirrored stencil q'_j = q[5 - j]
-  const double ru = fma(11.0, q[3], fma(-7.0, q[4], 2.0 * q[5]));
-  const double r4 = q[0] + fma(-5.0, q[1], fma(13.0, q[2], 3.0 * q[3]));
-  const double f4[3] = {q[2] - q[3], q[1] - q[3], q[0] - q[3]};
+  const double ru = fma(-5.0, d[3], 2.0 * d[4]) + r6;
+  const double r4 = fma(-9.0, d[2], fma(4.0, d[1], -d[0])) + 2.0 * r6;
   // three-cell measures K + s^2 / 4 with K = 13/12 t^2 of the stencil: K of the stencils centred at
   // a and a+1 carry over from the previous face (kk), the one centred at a+2 is new
-  const double t2 = fma(-2.0, q[4], q[3]) + q[5];
+  const double t2 = d[4] - d[3];
   const double K2 = k1312 * t2 * t2;
-  const double sB = q[4] - q[2], sC = fma(-4.0, q[2], 3.0 * q[3]) + q[1], sA = fma(-4.0, q[4], q[5]) + 3.0 * q[3];
+  const double sB = d[2] + d[3], sC = fma(3.0, d[2], -d[1]), sA = fma(-3.0, d[3], d[4]);
   const double rb0 = fma(0.25 * sB, sB, kk[1]);             // B of (q2, q3, q4)
   const double rb1 = fma(0.25 * sC, sC, kk[0]);             // C of (q1, q2, q3)
   const double rb2 = fma(0.25 * sA, sA, K2);                // A of (q3, q4, q5)
   kk[0] = kk[1];
   kk[1] = K2;
   const double ib0 = rcp6(rb0), ib1 = rcp6(rb1), ib2 = rcp6(rb2);
-  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, ib0, ib1, ib2, rcp6(beta4_form(f4)), b6r, ct, omega);
+  wr = combine(pd, pc, ru, r4, rb0, rb1, rb2, ib0, ib1, ib2, rcp6(beta4_diff(d[2], d[1], d[0])), b6r,
+               ct, omega);
   // next face's left state: beta0 = B at a+1 (rb0), beta1 = C at a+2 (rb2's stencil), beta2 = A at
   // a (rb1's), with their reciprocal factors
   b3c[0] = rb0;

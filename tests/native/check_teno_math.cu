@@ -22,7 +22,8 @@ int main() {
     double kk[2] = {fl::k1312 * ta * ta, fl::k1312 * tb * tb};
     double wl, wr;
     double i3c[3] = {fl::teno::rcp6(b3c[0]), fl::teno::rcp6(b3c[1]), fl::teno::rcp6(b3c[2])};
-    fl::teno::face_states(q, ct, b3c, i3c, kk, omega, wl, wr);
+    const double d[5] = {q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4]};
+    fl::teno::face_states(q, d, ct, b3c, i3c, kk, omega, wl, wr);
     std::printf("%.17g %.17g %.17g\n", wl, wr, ct);
   }
   return 0;
