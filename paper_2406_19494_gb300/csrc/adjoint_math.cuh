@@ -94,6 +94,112 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
 }
 
 // ------------------------------------------------------------------------------------------------
+// Both WENO5 values of one cell and their gradients, sharing the cell's indicator set
+// ------------------------------------------------------------------------------------------------
+// The left-biased value at face i+1/2 ("up") and the right-biased value at face i-1/2 ("dn") both
+// reconstruct in cell i from q_{i-2..i+2}, and their three stencils are the same three cells
+// triples with the same target cell: the mirror image of the right-biased stencil set is the
+// left-biased one, so the indicators, their reciprocals and the Z ratios r_k = tau / (beta_k + eps)
+// are shared and only the linear weights and candidates differ by side (in the up frame:
+// d = (1/10, 6/10, 3/10) for up and (3/10, 6/10, 1/10) for dn).  The derivative of tau = |b0 - b2|
+// is taken as sign(b0 - b2) in this frame, +1 at zero, for both sides.
+
+// One side from the shared set: the value offset out (= face value - q_i), the cotangents gC of the
+// candidates C (times 6, offsets from q_i) and gb of the (times 4) indicators for a unit cotangent.
+template <int SCHEME>
+FL_HD void weno5_side_vjp(const double f[3], const double r[3], const double iv[3], double sg,
+                          double d0, double d1, double d2, const double C[3], double& out,
+                          double gC[3], double gb[3]) {
+  const double a0 = d0 * f[0], a1 = d1 * f[1], a2 = d2 * f[2];
+  const double S = a0 + a1 + a2;
+  const double N = fma(a2, C[2], fma(a1, C[1], a0 * C[0]));
+  const double iS6 = fl_rcp(6.0 * S);
+  out = N * iS6;
+  const double gS = -6.0 * out * iS6;                // -out / S
+  const double ga0 = fma(iS6, C[0], gS), ga1 = fma(iS6, C[1], gS), ga2 = fma(iS6, C[2], gS);
+  gC[0] = iS6 * a0;
+  gC[1] = iS6 * a1;
+  gC[2] = iS6 * a2;
+  if (SCHEME == FLUID_WENO_JS) {
+    // a_k = d_k / e_k^2: da/de = -2 a / e
+    gb[0] = -2.0 * ga0 * a0 * r[0];
+    gb[1] = -2.0 * ga1 * a1 * r[1];
+    gb[2] = -2.0 * ga2 * a2 * r[2];
+  } else {
+    // a_k = d_k (1 + r_k^2), r_k = tau / e_k
+    const double gr0 = ga0 * (2.0 * d0) * r[0], gr1 = ga1 * (2.0 * d1) * r[1], gr2 = ga2 * (2.0 * d2) * r[2];
+    const double gtau = sg * fma(gr2, iv[2], fma(gr1, iv[1], gr0 * iv[0]));
+    gb[0] = fma(-gr0 * r[0], iv[0], gtau);
+    gb[1] = -gr1 * r[1] * iv[1];
+    gb[2] = fma(-gr2 * r[2], iv[2], -gtau);
+  }
+}
+
+// up / dn select the values formed; each gradient J (unit cotangent, over q_{i-2..i+2}) sums to
+// one, so its centre entry follows from the other four.
+template <int SCHEME>
+FL_HD void weno5_vjp_cell(const double qin[5], double eps4, bool up, bool dn, double& v_up,
+                          double J_up[5], double& v_dn, double J_dn[5]) {
+  // shifted by the centre value (see weno5_vjp); q2 = 0
+  const double q0 = qin[0] - qin[2], q1 = qin[1] - qin[2], q3 = qin[3] - qin[2], q4 = qin[4] - qin[2];
+  // 4 beta_k = (13/3) t_k^2 + s_k^2 of the stencils (i-2..i), (i-1..i+1), (i..i+2) for target i
+  const double t0 = fma(-2.0, q1, q0), s0 = fma(-4.0, q1, q0);
+  const double t1 = q1 + q3, s1 = q1 - q3;
+  const double t2 = fma(-2.0, q3, q4), s2 = fma(-4.0, q3, q4);
+  constexpr double K4 = 4.0 * k1312;
+  const double b0 = fma(K4 * t0, t0, s0 * s0);
+  const double b1 = fma(K4 * t1, t1, s1 * s1);
+  const double b2 = fma(K4 * t2, t2, s2 * s2);
+  double iv[3], r[3], f[3], sg = 1.0;
+  iv[0] = fl_rcp(b0 + eps4);
+  iv[1] = fl_rcp(b1 + eps4);
+  iv[2] = fl_rcp(b2 + eps4);
+  if (SCHEME == FLUID_WENO_JS) {
+    for (int k = 0; k < 3; ++k) {
+      r[k] = iv[k];
+      f[k] = iv[k] * iv[k];
+    }
+  } else {
+    const double db = b0 - b2;
+    const double tau = db < 0.0 ? -db : db;
+    sg = db < 0.0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) {
+      r[k] = tau * iv[k];
+      f[k] = fma(r[k], r[k], 1.0);
+    }
+  }
+  constexpr double T = 2.0 * K4;
+  if (up) {
+    // candidates at i+1/2 times 6: 2 q0 - 7 q1 + 11 q2, -q1 + 5 q2 + 2 q3, 2 q2 + 5 q3 - q4
+    const double C[3] = {fma(2.0, q0, -7.0 * q1), fma(2.0, q3, -q1), fma(5.0, q3, -q4)};
+    double out, gC[3], gb[3];
+    weno5_side_vjp<SCHEME>(f, r, iv, sg, 0.1, 0.6, 0.3, C, out, gC, gb);
+    v_up = out + qin[2];
+    const double u0 = gb[0] * t0, v0 = gb[0] * s0, u1 = gb[1] * t1, v1 = gb[1] * s1;
+    const double u2 = gb[2] * t2, v2 = gb[2] * s2;
+    J_up[0] = fma(2.0, gC[0], fma(T, u0, 2.0 * v0));
+    J_up[1] = fma(-7.0, gC[0], -gC[1]) + fma(-2.0 * T, u0, fma(-8.0, v0, fma(T, u1, 2.0 * v1)));
+    J_up[3] = fma(2.0, gC[1], 5.0 * gC[2]) + fma(T, u1, fma(-2.0, v1, fma(-2.0 * T, u2, -8.0 * v2)));
+    J_up[4] = -gC[2] + fma(T, u2, 2.0 * v2);
+    J_up[2] = 1.0 - ((J_up[0] + J_up[1]) + (J_up[3] + J_up[4]));
+  }
+  if (dn) {
+    // candidates at i-1/2 times 6: -q0 + 5 q1 + 2 q2, 2 q1 + 5 q2 - q3, 11 q2 - 7 q3 + 2 q4
+    const double C[3] = {fma(5.0, q1, -q0), fma(2.0, q1, -q3), fma(2.0, q4, -7.0 * q3)};
+    double out, gC[3], gb[3];
+    weno5_side_vjp<SCHEME>(f, r, iv, sg, 0.3, 0.6, 0.1, C, out, gC, gb);
+    v_dn = out + qin[2];
+    const double u0 = gb[0] * t0, v0 = gb[0] * s0, u1 = gb[1] * t1, v1 = gb[1] * s1;
+    const double u2 = gb[2] * t2, v2 = gb[2] * s2;
+    J_dn[0] = -gC[0] + fma(T, u0, 2.0 * v0);
+    J_dn[1] = fma(5.0, gC[0], 2.0 * gC[1]) + fma(-2.0 * T, u0, fma(-8.0, v0, fma(T, u1, 2.0 * v1)));
+    J_dn[3] = fma(-7.0, gC[2], -gC[1]) + fma(T, u1, fma(-2.0, v1, fma(-2.0 * T, u2, -8.0 * v2)));
+    J_dn[4] = fma(2.0, gC[2], fma(T, u2, 2.0 * v2));
+    J_dn[2] = 1.0 - ((J_dn[0] + J_dn[1]) + (J_dn[3] + J_dn[4]));
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // HLLC along D: cotangents of the left and right primitive states given the flux cotangent
 // ------------------------------------------------------------------------------------------------
 template <int D>

@@ -2,10 +2,12 @@
 // loss.  Given a state X and a cotangent mu of R(X) on the interior cells, the kernels below form
 // (dR/dX)^T mu and (dR/dphi)^T mu (phi: porous-wall parameters) in gather form -- every value is
 // summed in a fixed order, so the result does not depend on scheduling:
-//   k_adj_face<D>     one thread per face: the face-flux cotangent from the two adjacent cells,
-//                     then the reverse of HLLC, of the ten WENO5 reconstructions (weights included)
-//                     and of the dissipative flux; the contributions to the primitives of the six
-//                     stencil cells (and to the four tangential-gradient cells) go to per-face slots
+//   k_adj_face<D>     one thread per segment of faces along a grid line: per face the face-flux
+//                     cotangent from the two adjacent cells, then the reverse of HLLC, of the ten
+//                     WENO5 reconstructions (weights included; the two values reconstructed in one
+//                     cell share its indicator set) and of the dissipative flux; the contributions
+//                     to the primitives of the six stencil cells (and to the four tangential-
+//                     gradient cells) go to per-face slots
 //   k_adj_gather<D>   one thread per cell: sum of the slots of the faces whose stencil contains it
 //   k_adj_grad        reverse of the centre velocity gradients
 //   k_adj_bc<a>       reverse of the halo passes, z then y then x; one thread owns a boundary
@@ -36,130 +38,149 @@ __device__ __forceinline__ int stride_of(const Geo& g, int d) { return d == 0 ? 
 
 constexpr int kAdjBlock = 64;   // threads per block of k_adj_face (its WENO gradients sit in shared memory)
 
+// One thread marches a segment of faces a+1/2 (a = cfirst .. clast) of one grid line along D; the
+// step to target cell x (x = cfirst .. clast + 1) forms both WENO5 values of x with their gradients
+// from one indicator set (weno5_vjp_cell): the right-biased value at x-1/2, which completes face
+// x-1/2, and the left-biased value at x+1/2, which waits for the next step.  The segment's first
+// cell forms only its left-biased value and the cell after its last face only its right-biased one,
+// so every value is computed once per segment and the result does not depend on the segment length
+// except through these two ends.  Face x-1/2 then takes the reverse HLLC and dissipative flux and
+// writes its contributions to the six stencil cells (and four tangential-gradient cells) to its
+// per-face slots.
 template <int D, int SCHEME, bool VISC>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_face(const double* __restrict__ W,
                                                   const double* __restrict__ G,
                                                   const double* __restrict__ mu,
                                                   double* __restrict__ CW, double* __restrict__ CG,
-                                                  Geo g, Phys ph) {
+                                                  Geo g, Phys ph, int seg) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
-  const long long total = (long long)n1 * n2 * (nd + 1);
+  const int nf = nd + 1;                         // faces a + 1/2, a = h - 1 .. h + nd - 1
+  const int nseg = (nf + seg - 1) / seg;
+  const long long total = (long long)n1 * n2 * nseg;
   const int s = stride_of(g, D);
   const int nc = g.ncell;
+  const double eps4 = 4.0 * ph.eps;
+  // gradients of the reconstructions: [x & 1] the left-biased value of target cell x (read at the
+  // next step), [2] the right-biased value of the current step
+  __shared__ double sJ[3][25][kAdjBlock];
+  const int tid = threadIdx.x;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    // consecutive threads take consecutive x: faces for D = x, columns of faces otherwise
-    int af, i1, i2;                              // face a + 1/2 with a = h - 1 + af
-    if (D == 0) {
-      af = (int)(t % (nd + 1));
-      const long long r = t / (nd + 1);
-      i1 = (int)(r % n1);
-      i2 = (int)(r / n1);
-    } else {
-      i1 = (int)(t % n1);
-      const long long r = t / n1;
-      af = (int)(r % (nd + 1));
-      i2 = (int)(r / (nd + 1));
-    }
+    // consecutive threads take consecutive lines (consecutive x for D = y, z)
+    const int i1 = (int)(t % n1);
+    const long long rr = t / n1;
+    const int i2 = (int)(rr % n2);
+    const int sg = (int)(rr / n2);
+    const int cfirst = g.h[D] - 1 + sg * seg;
+    const int clast = g.h[D] - 1 + min((sg + 1) * seg, nf) - 1;
     int c[3];
     c[A1] = i1 + g.h[A1];
     c[A2] = i2 + g.h[A2];
-    const int a = g.h[D] - 1 + af;
-    c[D] = a;
-    const int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
-    // face-flux cotangent: R_a = -(F_{a+1/2} - F_{a-1/2}) / dx_a
-    double gF[5];
-    const bool inL = af > 0, inR = af < nd;
-    const double iL = inL ? g.idx[D][a] : 0.0, iR = inR ? g.idx[D][a + 1] : 0.0;
+    c[D] = cfirst;
+    int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
+    double wl[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int x = cfirst; x <= clast + 1; ++x, cell += s) {
+      const bool up = x <= clast, dn = x > cfirst;
+      double q[5][5];                            // cells x-2 .. x+2
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const double mL = inL ? mu[v * nc + cell] : 0.0;
-      const double mR = inR ? mu[v * nc + cell + s] : 0.0;
-      gF[v] = mR * iR - mL * iL;
-    }
-    // the ten reconstructions and their gradients in one pass (the reverse form with a unit
-    // cotangent); the gradients wait in shared memory for the HLLC cotangents
-    __shared__ double sJ[10][5][kAdjBlock];
-    const int tid = threadIdx.x;
-    double q[5][6];
+      for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
+        for (int o = 0; o < 5; ++o) q[v][o] = __ldg(W + v * nc + cell + (o - 2) * s);
+      double wn[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, wr[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int o = 0; o < 6; ++o) q[v][o] = __ldg(W + v * nc + cell + (o - 2) * s);
-    double wl[5], wr[5];
+      for (int v = 0; v < 5; ++v) {
+        double Ju[5], Jd[5];
+        weno5_vjp_cell<SCHEME>(q[v], eps4, up, dn, wn[v], Ju, wr[v], Jd);
+        if (up) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      double J[5];
-      const double ql[5] = {q[v][0], q[v][1], q[v][2], q[v][3], q[v][4]};
-      weno5_vjp<SCHEME>(ql, ph.eps, 1.0, J, &wl[v]);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) sJ[2 * v][k][tid] = J[k];
-      const double qr[5] = {q[v][5], q[v][4], q[v][3], q[v][2], q[v][1]};
-      weno5_vjp<SCHEME>(qr, ph.eps, 1.0, J, &wr[v]);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) sJ[2 * v + 1][k][tid] = J[k];
-    }
-    double gwl[5], gwr[5];
-    hllc_vjp<D>(wl, wr, ph, gF, gwl, gwr);
-    double gcell[6][kSlots];
-#pragma unroll
-    for (int v = 0; v < 6; ++v)
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) gcell[v][k] = 0.0;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        gcell[v][k] += gwl[v] * sJ[2 * v][k][tid];
-        gcell[v][5 - k] += gwr[v] * sJ[2 * v + 1][k][tid];
-      }
-    }
-    if (VISC) {
-      double vel[3][4], T[4], gd[3][4], gb[3][4];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        vel[0][o] = q[1][1 + o];
-        vel[1][o] = q[2][1 + o];
-        vel[2][o] = q[3][1 + o];
-        T[o] = __ldg(W + 5 * nc + cell + (o - 1) * s);
-      }
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          gd[b][o] = 0.0;
-          gb[b][o] = 0.0;
+          for (int k = 0; k < 5; ++k) sJ[x & 1][v * 5 + k][tid] = Ju[k];
         }
-        if (b == D || b >= g.ndim) continue;
-        const double* pd = G + (D * 3 + b) * nc + cell;
-        const double* pb = G + (b * 3 + b) * nc + cell;
+        if (dn) {
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          gd[b][o] = __ldg(pd + (o - 1) * s);
-          gb[b][o] = __ldg(pb + (o - 1) * s);
+          for (int k = 0; k < 5; ++k) sJ[2][v * 5 + k][tid] = Jd[k];
         }
       }
-      const double gFd[4] = {-gF[1], -gF[2], -gF[3], -gF[4]};
-      double gvel[3][4], gT[4], ggd[3][4], ggb[3][4];
-      visc_face_vjp<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, gFd, gvel, gT, ggd, ggb);
+      if (dn) {
+        // face a + 1/2 between cells a = x - 1 and x
+        const int a = x - 1;
+        const int fcell = cell - s;
+        const int af = a - (g.h[D] - 1);
+        // face-flux cotangent: R_a = -(F_{a+1/2} - F_{a-1/2}) / dx_a
+        double gF[5];
+        const bool inL = af > 0, inR = af < nd;
+        const double iL = inL ? g.idx[D][a] : 0.0, iR = inR ? g.idx[D][a + 1] : 0.0;
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        gcell[1][1 + o] += gvel[0][o];
-        gcell[2][1 + o] += gvel[1][o];
-        gcell[3][1 + o] += gvel[2][o];
-        gcell[5][1 + o] += gT[o];
-        CG[(o * kGComp + 0) * nc + cell] = ggd[A1][o];
-        CG[(o * kGComp + 1) * nc + cell] = ggb[A1][o];
-        CG[(o * kGComp + 2) * nc + cell] = ggd[A2][o];
-        CG[(o * kGComp + 3) * nc + cell] = ggb[A2][o];
+        for (int v = 0; v < 5; ++v) {
+          const double mL = inL ? mu[v * nc + fcell] : 0.0;
+          const double mR = inR ? mu[v * nc + cell] : 0.0;
+          gF[v] = mR * iR - mL * iL;
+        }
+        double gwl[5], gwr[5];
+        hllc_vjp<D>(wl, wr, ph, gF, gwl, gwr);
+        // slots k = 0 .. 5 are cells a-2 .. a+3; the left value's stencil is a-2 .. a+2, the
+        // right value's a-1 .. a+3
+        const int pl = (x - 1) & 1;
+        double gcell[6][kSlots];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          gcell[v][0] = gwl[v] * sJ[pl][v * 5][tid];
+#pragma unroll
+          for (int k = 1; k < 5; ++k)
+            gcell[v][k] = fma(gwl[v], sJ[pl][v * 5 + k][tid], gwr[v] * sJ[2][v * 5 + k - 1][tid]);
+          gcell[v][5] = gwr[v] * sJ[2][v * 5 + 4][tid];
+        }
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) gcell[5][k] = 0.0;
+        if (VISC) {
+          double vel[3][4], T[4], gd[3][4], gb[3][4];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            vel[0][o] = q[1][o];
+            vel[1][o] = q[2][o];
+            vel[2][o] = q[3][o];
+            T[o] = __ldg(W + 5 * nc + fcell + (o - 1) * s);
+          }
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              gd[b][o] = 0.0;
+              gb[b][o] = 0.0;
+            }
+            if (b == D || b >= g.ndim) continue;
+            const double* pd = G + (D * 3 + b) * nc + fcell;
+            const double* pb = G + (b * 3 + b) * nc + fcell;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              gd[b][o] = __ldg(pd + (o - 1) * s);
+              gb[b][o] = __ldg(pb + (o - 1) * s);
+            }
+          }
+          const double gFd[4] = {-gF[1], -gF[2], -gF[3], -gF[4]};
+          double gvel[3][4], gT[4], ggd[3][4], ggb[3][4];
+          visc_face_vjp<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, gFd, gvel, gT, ggd, ggb);
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            gcell[1][1 + o] += gvel[0][o];
+            gcell[2][1 + o] += gvel[1][o];
+            gcell[3][1 + o] += gvel[2][o];
+            gcell[5][1 + o] += gT[o];
+            CG[(o * kGComp + 0) * nc + fcell] = ggd[A1][o];
+            CG[(o * kGComp + 1) * nc + fcell] = ggb[A1][o];
+            CG[(o * kGComp + 2) * nc + fcell] = ggd[A2][o];
+            CG[(o * kGComp + 3) * nc + fcell] = ggb[A2][o];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k)
+#pragma unroll
+          for (int v = 0; v < 6; ++v) CW[(k * 6 + v) * nc + fcell] = gcell[v][k];
       }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) wl[v] = wn[v];
     }
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k)
-#pragma unroll
-      for (int v = 0; v < 6; ++v) CW[(k * 6 + v) * nc + cell] = gcell[v][k];
   }
 }
 
@@ -452,16 +473,40 @@ __global__ void k_lincomb(double* out, double c0, const double* x0, double c1, c
   }
 }
 
+// Segment length of k_adj_face for lines of nf faces: the one that minimises the modelled time,
+// (waves of resident threads) x (faces per thread) x (FP64 work per face).  A segment of L faces
+// forms 2 + 2 (L - 1) reconstructions' worth of WENO5 work as L + 1 cells (its two ends one value
+// each, the cells between two values from one indicator set, about 1.65 times one value), against
+// 2 L for faces taken one by one; the rest of a face (reverse HLLC, dissipative flux, slots) is
+// about 0.64 of two values.  Resident threads: 8 warps per SM (the kernel's registers).
+int adj_segment(long long lines, int nf) {
+  const long long resident = 152LL * 4 * kAdjBlock;
+  int best = 1;
+  double best_t = 0.0;
+  for (int L = 1; L <= 16; L *= 2) {
+    const long long threads = lines * ((nf + L - 1) / L);
+    const long long waves = (threads + resident - 1) / resident;
+    const double per_face = 1.28 + (2.0 + 1.65 * (L - 1)) / L;
+    const double t = (double)waves * L * per_face;
+    if (L == 1 || t < best_t) {
+      best = L;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
 template <int D, int SCHEME, bool VISC>
 cudaError_t adj_face_t(const double* W, const double* G, const double* mu, double* CW, double* CG,
                        const Geo& g, const Phys& ph, cudaStream_t st) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
-  const long long total = (long long)g.n[A1] * g.n[A2] * (g.n[D] + 1);
-  k_adj_face<D, SCHEME, VISC><<<grid_for(total, kAdjBlock), kAdjBlock, 0, st>>>(W, G, mu, CW, CG, g, ph);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaSuccess;
+  const long long lines = (long long)g.n[A1] * g.n[A2];
+  const int nf = g.n[D] + 1;
+  const int seg = adj_segment(lines, nf);
+  const long long total = lines * ((nf + seg - 1) / seg);
+  k_adj_face<D, SCHEME, VISC><<<grid_for(total, kAdjBlock), kAdjBlock, 0, st>>>(W, G, mu, CW, CG, g, ph, seg);
+  return cudaGetLastError();
 }
 
 template <int SCHEME, bool VISC>

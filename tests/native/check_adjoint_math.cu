@@ -48,6 +48,42 @@ static double check_weno(double eps) {
   return worst;
 }
 
+// Both values of a cell from weno5_vjp_cell: each value against the forward weno5 (the
+// right-biased one is the forward on the mirrored stencil) and each gradient against finite
+// differences of that value.
+template <int S>
+static double check_weno_cell(double eps) {
+  double worst = 0.0;
+  for (int t = 0; t < 400; ++t) {
+    double q[5], d[5], Ju[5], Jd[5], vu = 0.0, vd = 0.0;
+    const double sc = std::pow(10.0, U(-3, 1));
+    for (int k = 0; k < 5; ++k) { q[k] = U(-1, 1) * sc + (t % 3 == 0 ? 5.0 : 0.0); d[k] = U(-1, 1); }
+    weno5_vjp_cell<S>(q, 4.0 * eps, true, true, vu, Ju, vd, Jd);
+    auto fu = [&](double hh) {
+      double x[5];
+      for (int k = 0; k < 5; ++k) x[k] = q[k] + hh * d[k];
+      return weno5<S>(x[0], x[1], x[2], x[3], x[4], eps);
+    };
+    auto fd = [&](double hh) {
+      double x[5];
+      for (int k = 0; k < 5; ++k) x[k] = q[k] + hh * d[k];
+      return weno5<S>(x[4], x[3], x[2], x[1], x[0], eps);
+    };
+    const double scale = std::fabs(q[2]) + sc;
+    worst = std::fmax(worst, std::fabs(vu - fu(0.0)) / scale);
+    worst = std::fmax(worst, std::fabs(vd - fd(0.0)) / scale);
+    const double h = 1e-4 * sc;
+    const double du = (-fu(2 * h) + 8 * fu(h) - 8 * fu(-h) + fu(-2 * h)) / (12 * h);
+    const double dd = (-fd(2 * h) + 8 * fd(h) - 8 * fd(-h) + fd(-2 * h)) / (12 * h);
+    double au = 0.0, ad = 0.0, su = 0.0, sd = 0.0;
+    for (int k = 0; k < 5; ++k) { au += Ju[k] * d[k]; ad += Jd[k] * d[k]; su += Ju[k]; sd += Jd[k]; }
+    worst = std::fmax(worst, relerr(du, au));
+    worst = std::fmax(worst, relerr(dd, ad));
+    worst = std::fmax(worst, std::fmax(std::fabs(su - 1.0), std::fabs(sd - 1.0)));
+  }
+  return worst;
+}
+
 template <int D>
 static double check_hllc(int regime) {
   const Phys ph = make_phys(FLUID_VISC_NONE);
@@ -164,6 +200,8 @@ static double check_wall(int kind) {
 int main() {
   std::printf("weno5_js %.3e\n", check_weno<FLUID_WENO_JS>(1e-6));
   std::printf("weno5_z %.3e\n", check_weno<FLUID_WENO_Z>(1e-40));
+  std::printf("weno5_cell_js %.3e\n", check_weno_cell<FLUID_WENO_JS>(1e-6));
+  std::printf("weno5_cell_z %.3e\n", check_weno_cell<FLUID_WENO_Z>(1e-40));
   for (int r = 0; r < 3; ++r) {
     std::printf("hllc_x_regime%d %.3e\n", r, check_hllc<0>(r));
     std::printf("hllc_y_regime%d %.3e\n", r, check_hllc<1>(r));
