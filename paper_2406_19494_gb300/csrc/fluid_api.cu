@@ -32,6 +32,8 @@ struct fluid_solver {
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
   double* R = nullptr;             // right-hand side accumulator, NV * ncell
+  double* FB = nullptr;            // seam buffer of the FP64 face kernels, 10 * fb_cap
+  long long fb_cap = 0;
   double* partial = nullptr;       // dt: per-block maxima of the CFL rates
   int nparts = 0;
   Ctl* ctl = nullptr;
@@ -256,7 +258,8 @@ int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
     FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
   for (int d = 0; d < g.ndim; ++d)
     FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
-             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg, st));
+             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg,
+                             fl::SeamBuf{s->FB, s->fb_cap}, st));
   return FLUID_OK;
 }
 
@@ -415,6 +418,11 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   }
   if ((e = cudaMalloc(&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
   if ((e = cudaMalloc(&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
+  if (!s->mixed && c.weno != FLUID_TENO6A) {
+    s->fb_cap = fl::seam_capacity(g);
+    if ((e = cudaMalloc(&s->FB, 10 * (size_t)s->fb_cap * sizeof(double))) != cudaSuccess)
+      return bail(e, "cudaMalloc FB");
+  }
   if ((e = cudaMalloc(&s->partial, s->nparts * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc partial");
   if ((e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
   Ctl c0{};
@@ -542,6 +550,7 @@ void fluid_destroy(fluid_solver* s) {
     cudaFree(p);
   cudaFree(s->A);
   cudaFree(s->R);
+  cudaFree(s->FB);
   cudaFree(s->partial);
   cudaFree(s->ctl);
   cudaFree(s->vw);

@@ -110,8 +110,18 @@ cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g,
 cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph, cudaStream_t st);
 // launch shape of the marching FP64 face kernels: block/seg 0 pick the defaults; grid out
 void face_shape(int D, const Geo& g, int& block, int& seg, int& grid);
+// Seam buffer of the FP64 face kernels: 10 doubles per segment item (lines x segments of a launch),
+// cap items; a launch whose segments are shorter than kSeamMinSeg or that does not fit runs without
+// it (same result).  {nullptr, 0} turns it off.
+struct SeamBuf {
+  double* p;
+  long long cap;
+};
+constexpr int kSeamMinSeg = 4;
+long long seam_capacity(const Geo& g);   // items for segments of kSeamMinSeg cells on every axis
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
-                        const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
+                        const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                        cudaStream_t st);
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st);
 // dt_arg > 0 replaces the solver's dt (used by the adjoint's stage recomputation)
 cudaError_t launch_stage(int stage, const double* Un, const double* Us, const double* R, double* Ud,

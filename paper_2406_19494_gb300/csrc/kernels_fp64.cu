@@ -13,6 +13,9 @@
 //               and reused by the two cells that share it; a segment starts with the carried
 //               terms formed by the march's own operations (march_start), so the result is the
 //               same for every segment length.
+//   k_face_seam<D>   the first cell of every segment after a line's first, from the two fluxes
+//               the neighbouring segments hand over in the seam buffer (with the buffer no face
+//               is formed twice)
 //   k_source / k_stage   body-force source, RK3 stage combination, non-finite check
 //   k_stage_prim / k_halo_prim   the stage combination fused with the primitives of its result
 //               (interior cells), then the halo cells from those; fluid_step uses this pair in
@@ -294,15 +297,29 @@ __device__ __forceinline__ void march_start(const double q[5], double eps4, doub
   xl[2] = xr[0];
 }
 
+// R_a (+)= -(F_{a+1/2} - F_{a-1/2}) / dx_a with the product rounded before the sum (no fused
+// multiply-add), so that k_face and k_face_seam give the same bits
+__device__ __forceinline__ void update_r(double* dst, double F, double Fp, double id, int accumulate) {
+  const double val = __dmul_rn(-(F - Fp), id);
+  *dst = accumulate ? *dst + val : val;
+}
+
+// With a seam buffer FB (2 x 5 doubles per segment, [side][v][item]), a segment after the first
+// starts its march at face a0+1/2 instead of a0-1/2: it leaves its first cell a0 to k_face_seam,
+// with the flux at a0+1/2 in FB side 0, and its own last flux goes to FB side 1 of the next
+// segment, which is the flux at that segment's a0-1/2.  Every face is then formed once; without FB
+// each segment forms the face before its first cell as well.  Both give the same bits.
 template <int D, int SCHEME, int VORD>
 __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
                                               const double* __restrict__ G, double* __restrict__ R,
-                                              Geo g, Phys ph, int accumulate, int seg) {
+                                              double* __restrict__ FB, Geo g, Phys ph,
+                                              int accumulate, int seg) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
   const int nseg = (nd + seg - 1) / seg;
-  const long long total = (long long)n1 * n2 * nseg;
+  const long long lines = (long long)n1 * n2;
+  const long long total = lines * nseg;
   const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
   const int nc = g.ncell;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -316,29 +333,65 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
     c[A2] = i2 + g.h[A2];
     const int a0 = g.h[D] + sg * seg;
     const int a1 = min(a0 + seg, g.h[D] + nd);
-    c[D] = a0 - 1;
+    const bool seam = FB != nullptr && sg > 0;
+    c[D] = seam ? a0 : a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
     double Fp[5], F[5], xl[5][3], k0[5], k1[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      // the left-biased set of face a0 - 1/2 and the stencil terms it carries forward
+      // the left-biased set of the march's first face and the stencil terms it carries forward
       const double* f = W + v * nc + cell;
       const double qw[5] = {__ldg(f - 2 * s), __ldg(f - s), __ldg(f), __ldg(f + s), __ldg(f + 2 * s)};
       march_start<SCHEME>(qw, 4.0 * ph.eps, xl[v], k0[v], k1[v]);
     }
-    face_flux<D, SCHEME, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, xl, k0, k1);
-    for (int a = a0; a < a1; ++a) {
+    face_flux<D, SCHEME, VORD>(W, G, cell, s, c[D], g, ph, Fp, xl, k0, k1);
+    if (seam) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) FB[v * total + t] = Fp[v];
+    }
+    for (int a = seam ? a0 + 1 : a0; a < a1; ++a) {
       cell += s;
       face_flux<D, SCHEME, VORD>(W, G, cell, s, a, g, ph, F, xl, k0, k1);
       const double id = g.idx[D][a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double val = -(F[v] - Fp[v]) * id;
-        double* dst = R + v * nc + cell;
-        *dst = accumulate ? *dst + val : val;
+        update_r(R + v * nc + cell, F[v], Fp[v], id, accumulate);
         Fp[v] = F[v];
       }
     }
+    if (FB != nullptr && sg + 1 < nseg) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) FB[(5 + v) * total + t + lines] = Fp[v];
+    }
+  }
+}
+
+// The first cell a0 of every segment after the first: the same update as k_face, from the two
+// fluxes its neighbouring segments left in FB.
+template <int D>
+__global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ R, Geo g,
+                            int accumulate, int seg) {
+  constexpr int A1 = (D == 0) ? 1 : 0;
+  constexpr int A2 = (D == 2) ? 1 : 2;
+  const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
+  const int nseg = (nd + seg - 1) / seg;
+  const long long lines = (long long)n1 * n2;
+  const long long total = lines * nseg;
+  const int nc = g.ncell;
+  for (long long t = lines + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t % n1);
+    const long long r = t / n1;
+    const int i2 = (int)(r % n2);
+    const int sg = (int)(r / n2);
+    int c[3];
+    c[A1] = i1 + g.h[A1];
+    c[A2] = i2 + g.h[A2];
+    c[D] = g.h[D] + sg * seg;
+    const int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
+    const double id = g.idx[D][c[D]];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) update_r(R + v * nc + cell, FB[v * total + t], FB[(5 + v) * total + t], id, accumulate);
   }
 }
 
@@ -637,31 +690,55 @@ __global__ void k_wall_velocity(const double* __restrict__ phi, double* __restri
   }
 }
 
+// the seam buffer of a launch of nseg > 1 segments per line when it fits, else null (each
+// segment then forms the face before its first cell itself)
+double* seam_buffer(int D, const Geo& g, int seg, SeamBuf fb) {
+  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+  const long long nseg = (g.n[D] + seg - 1) / seg;
+  return (fb.p != nullptr && nseg > 1 && lines * nseg <= fb.cap) ? fb.p : nullptr;
+}
+
+template <int D>
+void launch_seam(const double* FB, double* R, const Geo& g, int accumulate, int seg, cudaStream_t st) {
+  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+  const long long items = lines * ((g.n[D] + seg - 1) / seg - 1);
+  k_face_seam<D><<<grid_for(items, 256), 256, 0, st>>>(FB, R, g, accumulate, seg);
+}
+
 template <int D, int SCHEME, int VORD>
 cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo& g,
-                          const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+                          const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                          cudaStream_t st) {
   int grid;
   face_shape(D, g, block, seg, grid);
-  k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
+  double* FB = seam_buffer(D, g, seg, fb);
+  k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg);
+  if (FB) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    launch_seam<D>(FB, R, g, accumulate, seg, st);
+  }
   return cudaGetLastError();
 }
 
 template <int SCHEME, int VORD>
 cudaError_t launch_face_sv(int D, const double* W, const double* G, double* R, const Geo& g,
-                           const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  if (D == 0) return launch_face_t<0, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
-  if (D == 1) return launch_face_t<1, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_face_t<2, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+                           const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                           cudaStream_t st) {
+  if (D == 0) return launch_face_t<0, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
+  if (D == 1) return launch_face_t<1, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
+  return launch_face_t<2, SCHEME, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
 }
 
 template <int SCHEME>
 cudaError_t launch_face_s(int D, const double* W, const double* G, double* R, const Geo& g,
-                          const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+                          const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                          cudaStream_t st) {
   if (ph.visc == FLUID_VISC_NONE)
-    return launch_face_sv<SCHEME, 0>(D, W, G, R, g, ph, accumulate, block, seg, st);
+    return launch_face_sv<SCHEME, 0>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
   if (ph.visc_order == 6)
-    return launch_face_sv<SCHEME, 6>(D, W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_face_sv<SCHEME, 4>(D, W, G, R, g, ph, accumulate, block, seg, st);
+    return launch_face_sv<SCHEME, 6>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
+  return launch_face_sv<SCHEME, 4>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
 }
 
 }  // namespace
@@ -707,11 +784,22 @@ cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph
 }
 
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
-                        const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
+                        const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                        cudaStream_t st) {
   if (ph.weno == FLUID_TENO6A) return launch_face_teno(D, W, G, R, g, ph, accumulate, block, seg, st);
   if (ph.weno == FLUID_WENO_JS)
-    return launch_face_s<FLUID_WENO_JS>(D, W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_face_s<FLUID_WENO_Z>(D, W, G, R, g, ph, accumulate, block, seg, st);
+    return launch_face_s<FLUID_WENO_JS>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
+  return launch_face_s<FLUID_WENO_Z>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
+}
+
+long long seam_capacity(const Geo& g) {
+  long long cap = 0;
+  for (int D = 0; D < g.ndim; ++D) {
+    const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+    const long long items = lines * ((g.n[D] + kSeamMinSeg - 1) / kSeamMinSeg);
+    if (items > cap) cap = items;
+  }
+  return cap;
 }
 
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st) {

@@ -279,7 +279,7 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
   if (e == cudaSuccess) e = fl::launch_prim_bc(U_dev, W, nullptr, g, ph, bc, ctl, st);
   if (e == cudaSuccess && visc) e = fl::launch_grad(W, G, g, ph, st);
   for (int d = 0; e == cudaSuccess && d < g.ndim; ++d)
-    e = fl::launch_face(d, W, G, R_dev, g, ph, d > 0, 0, 0, st);
+    e = fl::launch_face(d, W, G, R_dev, g, ph, d > 0, 0, 0, fl::SeamBuf{nullptr, 0}, st);
   if (e == cudaSuccess && ph.has_force) e = fl::launch_source(R_dev, W, g, ph, st);
   if (e != cudaSuccess) {
     put_msg(errbuf, errlen, cudaGetErrorString(e));
