@@ -418,7 +418,7 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
   }
   if ((e = cudaMalloc(&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
   if ((e = cudaMalloc(&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
-  if (!s->mixed && c.weno != FLUID_TENO6A) {
+  if (!s->mixed) {
     s->fb_cap = fl::seam_capacity(g);
     if ((e = cudaMalloc(&s->FB, 10 * (size_t)s->fb_cap * sizeof(double))) != cudaSuccess)
       return bail(e, "cudaMalloc FB");

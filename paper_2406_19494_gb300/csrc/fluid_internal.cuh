@@ -119,6 +119,12 @@ struct SeamBuf {
 };
 constexpr int kSeamMinSeg = 4;
 long long seam_capacity(const Geo& g);   // items for segments of kSeamMinSeg cells on every axis
+// the buffer for a launch of segments of `seg` cells along D, or null when it runs without
+double* seam_buffer(int D, const Geo& g, int seg, SeamBuf fb);
+// the first cells of the segments after each line's first, from the fluxes in FB (fused: the
+// TENO kernel's update form fma(-1/dx, F+ - F-, R), else the FP64 kernel's)
+cudaError_t launch_face_seam(int D, const double* FB, double* R, const Geo& g, int accumulate,
+                             int seg, bool fused, cudaStream_t st);
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
                         cudaStream_t st);
@@ -139,7 +145,8 @@ cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, C
 int dt_partial_count(const Geo& g);
 // ---- TENO6-A face kernels implemented in kernels_teno.cu ----------------------------------------
 cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R, const Geo& g,
-                             const Phys& ph, int accumulate, int block, int seg, cudaStream_t st);
+                             const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                             cudaStream_t st);
 // ---- mixed-precision launchers implemented in kernels_mixed.cu --------------------------------
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,

@@ -366,9 +366,10 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
   }
 }
 
-// The first cell a0 of every segment after the first: the same update as k_face, from the two
-// fluxes its neighbouring segments left in FB.
-template <int D>
+// The first cell a0 of every segment after the first: the same update as the face kernel that
+// filled FB, from the two fluxes its neighbouring segments left there (FUSED: the TENO kernel's
+// form, R = fma(-1/dx, F+ - F-, R))
+template <int D, bool FUSED>
 __global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ R, Geo g,
                             int accumulate, int seg) {
   constexpr int A1 = (D == 0) ? 1 : 0;
@@ -391,7 +392,16 @@ __global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ 
     const int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
     const double id = g.idx[D][c[D]];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) update_r(R + v * nc + cell, FB[v * total + t], FB[(5 + v) * total + t], id, accumulate);
+    for (int v = 0; v < 5; ++v) {
+      const double Fv = FB[v * total + t], Fpv = FB[(5 + v) * total + t];
+      double* dst = R + v * nc + cell;
+      if (FUSED) {
+        const double dF = Fv - Fpv;
+        *dst = accumulate ? fma(-id, dF, *dst) : -id * dF;
+      } else {
+        update_r(dst, Fv, Fpv, id, accumulate);
+      }
+    }
   }
 }
 
@@ -690,21 +700,6 @@ __global__ void k_wall_velocity(const double* __restrict__ phi, double* __restri
   }
 }
 
-// the seam buffer of a launch of nseg > 1 segments per line when it fits, else null (each
-// segment then forms the face before its first cell itself)
-double* seam_buffer(int D, const Geo& g, int seg, SeamBuf fb) {
-  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
-  const long long nseg = (g.n[D] + seg - 1) / seg;
-  return (fb.p != nullptr && nseg > 1 && lines * nseg <= fb.cap) ? fb.p : nullptr;
-}
-
-template <int D>
-void launch_seam(const double* FB, double* R, const Geo& g, int accumulate, int seg, cudaStream_t st) {
-  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
-  const long long items = lines * ((g.n[D] + seg - 1) / seg - 1);
-  k_face_seam<D><<<grid_for(items, 256), 256, 0, st>>>(FB, R, g, accumulate, seg);
-}
-
 template <int D, int SCHEME, int VORD>
 cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo& g,
                           const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
@@ -713,12 +708,9 @@ cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo
   face_shape(D, g, block, seg, grid);
   double* FB = seam_buffer(D, g, seg, fb);
   k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg);
-  if (FB) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    launch_seam<D>(FB, R, g, accumulate, seg, st);
-  }
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !FB) return e;
+  return launch_face_seam(D, FB, R, g, accumulate, seg, false, st);
 }
 
 template <int SCHEME, int VORD>
@@ -742,6 +734,30 @@ cudaError_t launch_face_s(int D, const double* W, const double* G, double* R, co
 }
 
 }  // namespace
+
+double* seam_buffer(int D, const Geo& g, int seg, SeamBuf fb) {
+  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+  const long long nseg = (g.n[D] + seg - 1) / seg;
+  return (fb.p != nullptr && nseg > 1 && lines * nseg <= fb.cap) ? fb.p : nullptr;
+}
+
+cudaError_t launch_face_seam(int D, const double* FB, double* R, const Geo& g, int accumulate,
+                             int seg, bool fused, cudaStream_t st) {
+  const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+  const long long items = lines * ((g.n[D] + seg - 1) / seg - 1);
+  const int grid = grid_for(items, 256);
+  if (D == 0) {
+    if (fused) k_face_seam<0, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    else k_face_seam<0, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+  } else if (D == 1) {
+    if (fused) k_face_seam<1, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    else k_face_seam<1, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+  } else {
+    if (fused) k_face_seam<2, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    else k_face_seam<2, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+  }
+  return cudaGetLastError();
+}
 
 void face_shape(int D, const Geo& g, int& block, int& seg, int& grid) {
   const int A1 = (D == 0) ? 1 : 0;
@@ -786,7 +802,8 @@ cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph
 cudaError_t launch_face(int D, const double* W, const double* G, double* R, const Geo& g,
                         const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
                         cudaStream_t st) {
-  if (ph.weno == FLUID_TENO6A) return launch_face_teno(D, W, G, R, g, ph, accumulate, block, seg, st);
+  if (ph.weno == FLUID_TENO6A)
+    return launch_face_teno(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
   if (ph.weno == FLUID_WENO_JS)
     return launch_face_s<FLUID_WENO_JS>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
   return launch_face_s<FLUID_WENO_Z>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);

@@ -7,7 +7,8 @@
 // falls back, in all five primitives, to the cell on its side of the face.
 //
 // One thread marches along a segment of a grid line, as the WENO5 kernel does; each face is
-// computed once and serves the two cells that share it.  The cut-off levels of the TENO-A scale
+// computed once and serves the two cells that share it (across segments through the seam buffer,
+// as in k_face).  The cut-off levels of the TENO-A scale
 // sensors depend on single cells, so three of the four a face needs carry over from the previous
 // face, as do the right state's three-cell measures (the next left state's) and their factors.  A
 // segment starts with the terms the march would have carried there, formed by the same
@@ -67,12 +68,14 @@ __device__ __forceinline__ void face_flux_teno(const double* __restrict__ W, con
 template <int D, int VORD>
 __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
                                                    const double* __restrict__ G, double* __restrict__ R,
-                                                   Geo g, Phys ph, int accumulate, int seg) {
+                                                   double* __restrict__ FB, Geo g, Phys ph,
+                                                   int accumulate, int seg) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
   const int nseg = (nd + seg - 1) / seg;
-  const long long total = (long long)n1 * n2 * nseg;
+  const long long lines = (long long)n1 * n2;
+  const long long total = lines * nseg;
   const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
   const int nc = g.ncell;
   // normalised weights per keep mask, k-major: for each k the 16 masks' weights sit in distinct
@@ -91,13 +94,16 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
     c[A2] = i2 + g.h[A2];
     const int a0 = g.h[D] + sg * seg;
     const int a1 = min(a0 + seg, g.h[D] + nd);
-    c[D] = a0 - 1;
+    // with the seam buffer a segment after the first starts at the face after its first cell
+    // (as in k_face)
+    const bool seam = FB != nullptr && sg > 0;
+    c[D] = seam ? a0 : a0 - 1;
     int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
     double Fp[5], F[5], b3[5][3], i3[5][3], kk[5][2], dd[5][4];
     int lev[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double* f = W + v * nc + cell;                   // cell a0 - 1
+      const double* f = W + v * nc + cell;                   // cell a = c[D]
       const double qm2 = __ldg(f - 2 * s), qm1 = __ldg(f - s), q0 = __ldg(f), qp1 = __ldg(f + s),
                    qp2 = __ldg(f + 2 * s);
       // the differences of cells a-2 .. a+2 (a = a0 - 1), and the terms the march carries into
@@ -124,8 +130,12 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
 #pragma unroll
       for (int j = 0; j < 3; ++j) i3[v][j] = teno::rcp6(b3[v][j]);
     }
-    face_flux_teno<D, VORD>(W, G, cell, s, a0 - 1, g, ph, Fp, lev, b3, i3, kk, dd, omega);
-    for (int a = a0; a < a1; ++a) {
+    face_flux_teno<D, VORD>(W, G, cell, s, c[D], g, ph, Fp, lev, b3, i3, kk, dd, omega);
+    if (seam) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) FB[v * total + t] = Fp[v];
+    }
+    for (int a = seam ? a0 + 1 : a0; a < a1; ++a) {
       cell += s;
       face_flux_teno<D, VORD>(W, G, cell, s, a, g, ph, F, lev, b3, i3, kk, dd, omega);
       const double id = g.idx[D][a];
@@ -137,33 +147,41 @@ __global__ void __launch_bounds__(128) k_face_teno(const double* __restrict__ W,
         Fp[v] = F[v];
       }
     }
+    if (FB != nullptr && sg + 1 < nseg) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) FB[(5 + v) * total + t + lines] = Fp[v];
+    }
   }
 }
 
 template <int D, int VORD>
 cudaError_t launch_d(const double* W, const double* G, double* R, const Geo& g, const Phys& ph,
-                     int accumulate, int block, int seg, cudaStream_t st) {
+                     int accumulate, int block, int seg, SeamBuf fb, cudaStream_t st) {
   int grid;
   face_shape(D, g, block, seg, grid);
-  k_face_teno<D, VORD><<<grid, block, 0, st>>>(W, G, R, g, ph, accumulate, seg);
-  return cudaGetLastError();
+  double* FB = seam_buffer(D, g, seg, fb);
+  k_face_teno<D, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !FB) return e;
+  return launch_face_seam(D, FB, R, g, accumulate, seg, true, st);
 }
 
 template <int VORD>
 cudaError_t launch_v(int D, const double* W, const double* G, double* R, const Geo& g,
-                     const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  if (D == 0) return launch_d<0, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
-  if (D == 1) return launch_d<1, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_d<2, VORD>(W, G, R, g, ph, accumulate, block, seg, st);
+                     const Phys& ph, int accumulate, int block, int seg, SeamBuf fb, cudaStream_t st) {
+  if (D == 0) return launch_d<0, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
+  if (D == 1) return launch_d<1, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
+  return launch_d<2, VORD>(W, G, R, g, ph, accumulate, block, seg, fb, st);
 }
 
 }  // namespace
 
 cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R, const Geo& g,
-                             const Phys& ph, int accumulate, int block, int seg, cudaStream_t st) {
-  if (ph.visc == FLUID_VISC_NONE) return launch_v<0>(D, W, G, R, g, ph, accumulate, block, seg, st);
-  if (ph.visc_order == 6) return launch_v<6>(D, W, G, R, g, ph, accumulate, block, seg, st);
-  return launch_v<4>(D, W, G, R, g, ph, accumulate, block, seg, st);
+                             const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
+                             cudaStream_t st) {
+  if (ph.visc == FLUID_VISC_NONE) return launch_v<0>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
+  if (ph.visc_order == 6) return launch_v<6>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
+  return launch_v<4>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
 }
 
 }  // namespace fl
