@@ -49,6 +49,7 @@ struct fluid_solver {
     cudaEvent_t a, b;
   };
   int face_block = 0, face_seg = 0;   // launch shape of the face kernels (0 = automatic)
+  int face_seg_d[3] = {0, 0, 0};      // FP64 path: segment length per axis (0 = automatic)
   // adjoint scratch (cfg.adjoint != 0)
   double* gW = nullptr;            // cotangent of the primitives, NW * ncell
   double* gG = nullptr;            // cotangent of the velocity gradients, NG * ncell
@@ -258,7 +259,7 @@ int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
     FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
   for (int d = 0; d < g.ndim; ++d)
     FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
-             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg,
+             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg_d[d],
                              fl::SeamBuf{s->FB, s->fb_cap}, st));
   return FLUID_OK;
 }
@@ -794,6 +795,53 @@ int fluid_tune_faces(fluid_solver* s, int block, int seg) {
   if (seg < 0 && !s->mixed) return fail(s, FLUID_EINVAL, "seg must be >= 0 for the FP64 path");
   s->face_block = block;
   s->face_seg = seg;
+  for (int d = 0; d < 3; ++d) s->face_seg_d[d] = seg;
+  return FLUID_OK;
+}
+
+int fluid_autotune_faces(fluid_solver* s, const double* U_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (s->mixed) return FLUID_OK;
+  cudaStream_t st = as_stream(stream);
+  const Geo& g = s->geo;
+  FL_CUDA(s, fl::launch_prim_bc(U_dev, s->W, s->W32, g, s->ph, s->bc, s->ctl, st));
+  if (s->ph.visc != FLUID_VISC_NONE) FL_CUDA(s, fl::launch_grad(s->W, s->G, g, s->ph, st));
+  cudaEvent_t e0, e1;
+  FL_CUDA(s, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(s, FLUID_ECUDA, "cudaEventCreate");
+  }
+  // candidates: the automatic rule (0) and segments of 8 to 32 cells; block 128
+  static const int kCand[] = {0, 8, 10, 12, 14, 16, 17, 18, 19, 20, 22, 24, 28, 32};
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < g.ndim && e == cudaSuccess; ++d) {
+    int best_seg = 0;
+    float best_ms = 0.0f;
+    for (int c : kCand) {
+      if (c > g.n[d]) continue;
+      auto launch = [&]() {
+        return fl::launch_face(d, s->W, s->G, s->R, g, s->ph, 0, 128, c, fl::SeamBuf{s->FB, s->fb_cap}, st);
+      };
+      if ((e = launch()) != cudaSuccess) break;                       // warm-up
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+      if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (c == 0 || ms < best_ms) {
+        best_ms = ms;
+        best_seg = c;
+      }
+    }
+    if (e == cudaSuccess) s->face_seg_d[d] = best_seg;
+  }
+  s->face_block = 128;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(s, e, "fluid_autotune_faces");
   return FLUID_OK;
 }
 

@@ -44,6 +44,7 @@ SIGNATURES = {
     "fluid_set_time": (_i, [_vp, _d, _vp]),
     "fluid_check": (_i, [_vp, _vp]),
     "fluid_tune_faces": (_i, [_vp, _i, _i]),
+    "fluid_autotune_faces": (_i, [_vp, _vp, _vp]),
     "fluid_profile_enable": (_i, [_vp, _i]),
     "fluid_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64), _i]),
     "fluid_measure_peak": (_i, [_i, ctypes.POINTER(_d), _vp]),

@@ -136,6 +136,11 @@ class Solver:
     def tune_faces(self, block=0, seg=0):
         self._check(self.lib.fluid_tune_faces(self.handle, int(block), int(seg)))
 
+    def autotune_faces(self, U, stream=None):
+        """Time the FP64 face kernels' segment lengths on state U and keep the fastest per axis
+        (fluid_autotune_faces); the result of every later call is unchanged."""
+        self._check(self.lib.fluid_autotune_faces(self.handle, self._state(U), _stream(stream)))
+
     def profile(self, enable=True):
         self._check(self.lib.fluid_profile_enable(self.handle, 1 if enable else 0))
 

@@ -63,3 +63,35 @@ def test_mixed_shapes_agree():
     for block, seg in ((64, -8), (128, -5), (32, -3)):
         R = _rhs(c, U, "mixed", block, seg)[inner]
         assert max(rel_err(R, base)) <= 1e-6, (block, seg)
+
+
+@pytest.mark.parametrize("scheme", [dict(), dict(weno="teno6a", visc_order=6)])
+def test_autotuned_shapes_agree_bitwise(scheme):
+    """fluid_autotune_faces picks a segment length per axis by timing; whatever it picks, the
+    right-hand side and a step are bitwise those of the automatic shape, and the state it was
+    timed on is untouched."""
+    from paper_2406_19494_gb300.solver import Solver
+    c = dict(CASE(), **scheme)
+    case, grid, U = padded_state(c, seed=10)
+    inner = (slice(None),) + case.interior()
+    Ud = torch.from_numpy(U).cuda()
+    ref, tuned = Solver(c), Solver(c)
+    U0 = Ud.clone()
+    tuned.autotune_faces(Ud)
+    assert torch.equal(Ud, U0)
+    assert np.array_equal(tuned.rhs(Ud).cpu().numpy()[inner], ref.rhs(Ud).cpu().numpy()[inner])
+    Ua, Ub = Ud.clone(), Ud.clone()
+    ref.step(Ua, 2)
+    tuned.step(Ub, 2)
+    assert torch.equal(Ua, Ub)
+
+
+def test_autotune_mixed_is_a_no_op():
+    from paper_2406_19494_gb300.solver import Solver
+    c = CASE()
+    case, grid, U = padded_state(c, seed=11)
+    s = Solver(c, precision="mixed")
+    Ud = torch.from_numpy(U).cuda()
+    before = s.rhs(Ud).cpu().numpy()
+    s.autotune_faces(Ud)
+    assert np.array_equal(s.rhs(Ud).cpu().numpy(), before)
