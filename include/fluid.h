@@ -216,7 +216,7 @@ int fluid_check(fluid_solver* s, void* stream);
 
 /* Launch shape of the face kernels: threads per block (a multiple of 32 in [32, 128]; 0 = 128)
  * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8/4
- * that still fills the GPU).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
+ * that still fills the GPU), for every axis (fluid_autotune_faces picks one per axis).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
  * tiles of 2 warps (block 64) or 4 warps (otherwise) by default; seg < 0 selects the register-window
  * marching kernels with |seg| cells per segment and `block` threads instead.  FP64 results and
  * those of the two mixed tiles are bitwise the same for every shape; the mixed register-window
