@@ -61,6 +61,10 @@ struct fluid_solver {
   double* L1 = nullptr;            // stage adjoints
   double* L2 = nullptr;
   double* GT = nullptr;            // right-hand-side adjoint result
+  double* Wn = nullptr;            // primitives and gradients of Un and U1 formed by the step
+  double* Gn = nullptr;            // adjoint's stage recomputation, kept for its reverse passes
+  double* W1 = nullptr;
+  double* G1 = nullptr;
   double* gvw = nullptr;           // porous wall-velocity cotangent per wall column
   size_t gvw_count = 0;
   double* parts = nullptr;         // wall-loss partial sums
@@ -298,20 +302,25 @@ int stage_prim_into(fluid_solver* s, int stage, const double* Un, const double* 
   return FLUID_OK;
 }
 
-// (dR/dX)^T mu on the interior into gX; (dR/dphi)^T mu added to gphi when given
+// (dR/dX)^T mu on the interior into gX; (dR/dphi)^T mu added to gphi when given.  Wx / Gx: the
+// primitives and gradients of X when already formed (else computed into the solver's W / G).
 int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, double* gphi,
-            cudaStream_t st) {
+            cudaStream_t st, double* Wx = nullptr, double* Gx = nullptr) {
   const Geo& g = s->geo;
   const bool visc = s->ph.visc != FLUID_VISC_NONE;
-  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(X, s->W, nullptr, g, s->ph, s->bc, s->ctl, st));
-  if (visc) FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
+  double* W = Wx ? Wx : s->W;
+  double* G = Wx ? Gx : s->G;
+  if (!Wx) {
+    FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(X, W, nullptr, g, s->ph, s->bc, s->ctl, st));
+    if (visc) FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(W, G, g, s->ph, st));
+  }
   FL_CUDA(s, cudaMemsetAsync(s->gW, 0, fl::NW * (size_t)g.ncell * sizeof(double), st));
   if (visc) FL_CUDA(s, cudaMemsetAsync(s->gG, 0, fl::NG * (size_t)g.ncell * sizeof(double), st));
   FL_CUDA(s, cudaMemsetAsync(s->gvw, 0, s->gvw_count * sizeof(double), st));
   FL_TIMED(s, FLUID_KERNEL_ADJ_FACE, st,
-           fl::launch_adj_faces(s->W, s->G, mu, s->CW, s->CG, s->gW, s->gG, g, s->ph, st));
+           fl::launch_adj_faces(W, G, mu, s->CW, s->CG, s->gW, s->gG, g, s->ph, st));
   if (s->ph.has_force) FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_source(mu, s->gW, g, s->ph, st));
-  FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_bc(s->W, s->gW, s->gvw, g, s->ph, s->bc, st));
+  FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_bc(W, s->gW, s->gvw, g, s->ph, s->bc, st));
   FL_TIMED(s, FLUID_KERNEL_ADJ_CELL, st, fl::launch_adj_prim(X, s->gW, gX, g, s->ph, st));
   if (gphi && s->bc.porous_axis >= 0) {
     const int A = s->bc.porous_axis, t1 = s->bc.porous_t1, t2 = 3 - A - t1;
@@ -513,6 +522,12 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       if ((e = cudaMalloc(&s->gG, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gG");
       if ((e = cudaMalloc(&s->CG, 16 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
     }
+    if ((e = cudaMalloc(&s->Wn, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wn");
+    if ((e = cudaMalloc(&s->W1, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W1");
+    if (visc) {
+      if ((e = cudaMalloc(&s->Gn, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Gn");
+      if ((e = cudaMalloc(&s->G1, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G1");
+    }
     double** bufs[] = {&s->S1, &s->S2, &s->MU, &s->L1, &s->L2, &s->GT};
     for (double** b : bufs) {
       if ((e = cudaMalloc(b, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc adjoint state");
@@ -547,7 +562,7 @@ void fluid_destroy(fluid_solver* s) {
   cudaFree(s->mf32);
   cudaFree(s->G32);
   for (double* p : {s->gW, s->gG, s->CW, s->CG, s->S1, s->S2, s->MU, s->L1, s->L2, s->GT, s->gvw,
-                    s->parts, s->gT2})
+                    s->parts, s->gT2, s->Wn, s->Gn, s->W1, s->G1})
     cudaFree(p);
   cudaFree(s->A);
   cudaFree(s->R);
@@ -705,10 +720,21 @@ int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_d
   cudaStream_t st = as_stream(stream);
   const double* X1 = U1_dev;
   const double* X2 = U2_dev;
-  if (!X1) {
-    // recompute the stage states of the step
+  const bool recompute = !X1;
+  if (recompute) {
+    // recompute the stage states of the step; the primitives and gradients of Un and U1 go to
+    // Wn / Gn and W1 / G1, where the reverse passes of those stages find them
+    struct Restore {
+      fluid_solver* s;
+      double *W, *G;
+      ~Restore() { s->W = W; s->G = G; }
+    } restore{s, s->W, s->G};
+    s->W = s->Wn;
+    s->G = s->Gn;
     if (int r = rhs_into(s, Un_dev, s->R, st)) return r;
     FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_stage(1, Un_dev, Un_dev, s->R, s->S1, s->W, g, s->ph, s->ctl, 0.0, st, dt));
+    s->W = s->W1;
+    s->G = s->G1;
     if (int r = rhs_into(s, s->S1, s->R, st)) return r;
     FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_stage(2, Un_dev, s->S1, s->R, s->S2, s->W, g, s->ph, s->ctl, 0.0, st, dt));
     X1 = s->S1;
@@ -720,11 +746,11 @@ int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_d
   FL_CUDA(s, fl::launch_lincomb(s->L2, 2.0 / 3.0, lam_dev, 1.0, s->GT, 0, nullptr, 0, nullptr, g, st));
   // U2 = 3/4 Un + 1/4 U1 + 1/4 dt R(U1)
   FL_CUDA(s, fl::launch_lincomb(s->MU, 0.25 * dt, s->L2, 0, nullptr, 0, nullptr, 0, nullptr, g, st));
-  if (int r = rhs_vjp(s, X1, s->MU, s->GT, gphi_dev, st)) return r;
+  if (int r = rhs_vjp(s, X1, s->MU, s->GT, gphi_dev, st, recompute ? s->W1 : nullptr, s->G1)) return r;
   FL_CUDA(s, fl::launch_lincomb(s->L1, 0.25, s->L2, 1.0, s->GT, 0, nullptr, 0, nullptr, g, st));
   // U1 = Un + dt R(Un)
   FL_CUDA(s, fl::launch_lincomb(s->MU, dt, s->L1, 0, nullptr, 0, nullptr, 0, nullptr, g, st));
-  if (int r = rhs_vjp(s, Un_dev, s->MU, s->GT, gphi_dev, st)) return r;
+  if (int r = rhs_vjp(s, Un_dev, s->MU, s->GT, gphi_dev, st, recompute ? s->Wn : nullptr, s->Gn)) return r;
   FL_CUDA(s, fl::launch_lincomb(lam_dev, 1.0 / 3.0, lam_dev, 0.75, s->L2, 1.0, s->L1, 1.0, s->GT, g, st));
   return FLUID_OK;
 }

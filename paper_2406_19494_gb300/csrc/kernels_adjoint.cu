@@ -296,10 +296,14 @@ __device__ __forceinline__ int bc_src(int kind, int side, int a, int n, int h) {
   return side == 0 ? 2 * h - 1 - a : 2 * (h + n) - 1 - a;
 }
 
-// reverse of the halo pass of axis A: columns over (axes < A: padded, axes > A: interior)
+// reverse of the halo pass of axis A: columns over (axes < A: padded, axes > A: interior).  Per side
+// all loads of the column's layers come first (ghost cotangents, source primitives, source
+// cotangents), then the layers' contributions are added in layer order, as the halo pass wrote
+// them (a zero-gradient side adds all layers to one source cell, in the same order).
 template <int A>
 __global__ void k_adj_bc(const double* __restrict__ W, double* __restrict__ gW,
                          double* __restrict__ gvw_col, Geo g, Phys ph, BC bc) {
+  constexpr int H = FLUID_HALO;
   int lo[3], ext[3];
   for (int b = 0; b < 3; ++b) {
     if (b < A) { lo[b] = 0; ext[b] = g.p[b]; }
@@ -309,7 +313,7 @@ __global__ void k_adj_bc(const double* __restrict__ W, double* __restrict__ gW,
   const int total = ext[0] * ext[1] * ext[2];
   const int nc = g.ncell;
   const int s = stride_of(g, A);
-  const int h = g.h[A], n = g.n[A];
+  const int n = g.n[A];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     int c[3];
     c[0] = lo[0] + t % ext[0];
@@ -322,26 +326,46 @@ __global__ void k_adj_bc(const double* __restrict__ W, double* __restrict__ gW,
     for (int side = 0; side < 2; ++side) {
       const int kind = bc.kind[A][side];
       if (kind == FLUID_BC_INFLOW) continue;            // fixed values: no dependence
-      for (int m = 0; m < h; ++m) {
-        const int gi = side == 0 ? h - 1 - m : h + n + m;
-        const int si = bc_src(kind, side, gi, n, h);
-        const int gc = base + gi * s, sc = base + si * s;
-        double gg[6], gw[6];
-        for (int v = 0; v < 6; ++v) gg[v] = gW[v * nc + gc];
-        if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) {
-          for (int v = 0; v < 6; ++v) gw[v] = gg[v];
+      const bool copy = kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT;
+      const bool one_source = kind == FLUID_BC_ZERO_GRADIENT;
+      int gc[H], sc[H];
+      double gg[H][6], w[H][6], gs[H][6];
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int gi = side == 0 ? H - 1 - m : H + n + m;
+        gc[m] = base + gi * s;
+        sc[m] = base + bc_src(kind, side, gi, n, H) * s;
+      }
+#pragma unroll
+      for (int m = 0; m < H; ++m)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+          gg[m][v] = gW[v * nc + gc[m]];
+          w[m][v] = copy ? 0.0 : W[v * nc + sc[m]];
+          gs[m][v] = gW[v * nc + sc[m]];
+        }
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        double gw[6];
+        if (copy) {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) gw[v] = gg[m][v];
         } else {
-          double w[6];
-          for (int v = 0; v < 6; ++v) w[v] = W[v * nc + sc];
           double gvw = 0.0;
-          wall_map_vjp(w, kind, bc.Tw[A][side], A, ph, gg, gw, &gvw);
+          wall_map_vjp(w[m], kind, bc.Tw[A][side], A, ph, gg[m], gw, &gvw);
           gvw_sum += gvw;
         }
-        for (int v = 0; v < 6; ++v) {
-          gW[v * nc + sc] += gw[v];
-          gW[v * nc + gc] = 0.0;
-        }
+        const int k = one_source ? 0 : m;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) gs[k][v] += gw[v];
       }
+#pragma unroll
+      for (int m = 0; m < H; ++m)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+          if (m == 0 || !one_source) gW[v * nc + sc[m]] = gs[m][v];
+          gW[v * nc + gc[m]] = 0.0;
+        }
     }
     if (gvw_col && bc.porous_axis == A) {
       // column index over the two tangential axes (t1 fastest)
