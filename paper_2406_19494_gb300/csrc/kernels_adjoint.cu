@@ -36,7 +36,10 @@ constexpr int kGComp = 4;     // tangential gradient components read by one face
 
 __device__ __forceinline__ int stride_of(const Geo& g, int d) { return d == 0 ? 1 : (d == 1 ? g.sy : g.sz); }
 
-constexpr int kAdjBlock = 64;   // threads per block of k_adj_face (its WENO gradients sit in shared memory)
+// threads per block of k_adj_face (its WENO gradients sit in shared memory): one warp, so that a
+// launch of a few blocks per SM spreads evenly (the registers allow eight warps per SM)
+constexpr int kAdjBlock = 32;
+constexpr int kAdjWarpsPerSM = 8;
 
 // One thread marches a segment of faces a+1/2 (a = cfirst .. clast) of one grid line along D; the
 // step to target cell x (x = cfirst .. clast + 1) forms both WENO5 values of x with their gradients
@@ -504,7 +507,7 @@ __global__ void k_lincomb(double* out, double c0, const double* x0, double c1, c
 // 2 L for faces taken one by one; the rest of a face (reverse HLLC, dissipative flux, slots) is
 // about 0.64 of two values.  Resident threads: 8 warps per SM (the kernel's registers).
 int adj_segment(long long lines, int nf) {
-  const long long resident = 152LL * 4 * kAdjBlock;
+  const long long resident = 152LL * kAdjWarpsPerSM * 32;
   int best = 1;
   double best_t = 0.0;
   for (int L = 1; L <= 16; L *= 2) {
