@@ -246,10 +246,11 @@ enum {
   FLUID_KERNEL_COUNT = 10
 };
 
-/* Kernel timing.  While enabled, every kernel the solver launches is bracketed by a CUDA event
- * pair recorded on the launch stream (the measured time is the kernel's device time plus event
- * overhead of a few microseconds).  fluid_profile_read synchronises on the pending events, adds
- * them to per-class totals and returns the total milliseconds and launch count of class `kind`;
+/* Kernel timing.  While enabled, every launch step of the solver (one kernel, or a face kernel with
+ * its seam kernel, a stage kernel with its halo kernel) is bracketed by a CUDA event pair recorded
+ * on the launch stream (the measured time is the kernels' device time plus event overhead of a few
+ * microseconds).  fluid_profile_read synchronises on the pending events, adds them to per-class
+ * totals and returns the total milliseconds and the number of kernels launched in class `kind`;
  * reset != 0 clears all totals after reading. */
 int fluid_profile_enable(fluid_solver* s, int enable);
 int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* launches, int reset);

@@ -47,6 +47,7 @@ struct fluid_solver {
   struct ProfEvent {
     int kind;
     cudaEvent_t a, b;
+    long long kernels;   // kernels enqueued between the two events
   };
   int face_block = 0, face_seg = 0;   // launch shape of the face kernels (0 = automatic)
   int face_seg_d[3] = {0, 0, 0};      // FP64 path: segment length per axis (0 = automatic)
@@ -220,7 +221,8 @@ int check_ptr(fluid_solver* s, const void* p, const char* what) {
 // Run one launch; when profiling is on, bracket it with an event pair on the same stream.
 template <class F>
 int timed(fluid_solver* s, int kind, cudaStream_t st, const char* what, F&& launch) {
-  fluid_solver::ProfEvent ev{kind, nullptr, nullptr};
+  fluid_solver::ProfEvent ev{kind, nullptr, nullptr, 0};
+  const long long before = fl::t_launches;
   if (s->prof_on) {
     if (!s->prof_pool.empty()) {
       ev.a = s->prof_pool.back().a;
@@ -236,6 +238,7 @@ int timed(fluid_solver* s, int kind, cudaStream_t st, const char* what, F&& laun
   if (e != cudaSuccess) return cuda_fail(s, e, what);
   if (s->prof_on) {
     FL_CUDA(s, cudaEventRecord(ev.b, st));
+    ev.kernels = fl::t_launches - before;
     s->prof_pending.push_back(ev);
   }
   return FLUID_OK;
@@ -884,7 +887,7 @@ int fluid_profile_read(fluid_solver* s, int kind, double* total_ms, int64_t* lau
     float ms = 0.f;
     FL_CUDA(s, cudaEventElapsedTime(&ms, ev.a, ev.b));
     s->prof_ms[ev.kind] += ms;
-    s->prof_n[ev.kind] += 1;
+    s->prof_n[ev.kind] += ev.kernels;
     s->prof_pool.push_back(ev);
   }
   s->prof_pending.clear();

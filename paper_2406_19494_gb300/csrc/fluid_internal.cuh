@@ -102,6 +102,10 @@ inline void set_power_law(Phys& ph, double e) {
 // Configuration check shared by the entry points: NULL if valid, else a static message.
 const char* config_error(const fluid_config* c);
 
+// Kernels the launchers below have enqueued from this host thread (each launch site adds one); the
+// solver's profiler counts the kernels of a bracketed call by the difference.
+inline thread_local long long t_launches = 0;
+
 // ---- launchers implemented in kernels_fp64.cu --------------------------------------------------
 // W32 (mixed path only, else null): exact FP32 (hi, lo) split of the primitives, [2 NW][ncell];
 // with it W must hold NW + 1 rows, the last receiving H = E + p

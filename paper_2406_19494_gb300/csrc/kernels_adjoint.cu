@@ -532,7 +532,7 @@ cudaError_t adj_face_t(const double* W, const double* G, const double* mu, doubl
   const int nf = g.n[D] + 1;
   const int seg = adj_segment(lines, nf);
   const long long total = lines * ((nf + seg - 1) / seg);
-  k_adj_face<D, SCHEME, VISC><<<grid_for(total, kAdjBlock), kAdjBlock, 0, st>>>(W, G, mu, CW, CG, g, ph, seg);
+  (k_adj_face<D, SCHEME, VISC><<<grid_for(total, kAdjBlock), kAdjBlock, 0, st>>>(W, G, mu, CW, CG, g, ph, seg), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -546,13 +546,13 @@ cudaError_t adj_dir(int D, const double* W, const double* G, const double* mu, d
   const long long tg = ncol * g.p[D];
   if (D == 0) {
     if ((e = adj_face_t<0, SCHEME, VISC>(W, G, mu, CW, CG, g, ph, st)) != cudaSuccess) return e;
-    k_adj_gather<0, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g);
+    (k_adj_gather<0, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g), ++t_launches);
   } else if (D == 1) {
     if ((e = adj_face_t<1, SCHEME, VISC>(W, G, mu, CW, CG, g, ph, st)) != cudaSuccess) return e;
-    k_adj_gather<1, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g);
+    (k_adj_gather<1, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g), ++t_launches);
   } else {
     if ((e = adj_face_t<2, SCHEME, VISC>(W, G, mu, CW, CG, g, ph, st)) != cudaSuccess) return e;
-    k_adj_gather<2, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g);
+    (k_adj_gather<2, VISC><<<grid_for(tg, 256), 256, 0, st>>>(CW, CG, gW, gG, g), ++t_launches);
   }
   return cudaGetLastError();
 }
@@ -574,7 +574,7 @@ cudaError_t launch_adj_faces(const double* W, const double* G, const double* mu,
     if (e != cudaSuccess) return e;
   }
   if (visc) {
-    k_adj_grad<<<grid_for(g.ncell, 256), 256, 0, st>>>(gG, gW, g);
+    (k_adj_grad<<<grid_for(g.ncell, 256), 256, 0, st>>>(gG, gW, g), ++t_launches);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -583,7 +583,7 @@ cudaError_t launch_adj_faces(const double* W, const double* G, const double* mu,
 
 cudaError_t launch_adj_source(const double* mu, double* gW, const Geo& g, const Phys& ph, cudaStream_t st) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_adj_source<<<grid_for(total, 256), 256, 0, st>>>(mu, gW, g, ph);
+  (k_adj_source<<<grid_for(total, 256), 256, 0, st>>>(mu, gW, g, ph), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -594,9 +594,9 @@ cudaError_t launch_adj_bc(const double* W, double* gW, double* gvw_col, const Ge
     for (int b = 0; b < 3; ++b)
       if (b != A) cols *= b < A ? g.p[b] : g.n[b];
     const int grid = grid_for(cols, 128);
-    if (A == 0) k_adj_bc<0><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc);
-    else if (A == 1) k_adj_bc<1><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc);
-    else k_adj_bc<2><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc);
+    if (A == 0) (k_adj_bc<0><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc), ++t_launches);
+    else if (A == 1) (k_adj_bc<1><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc), ++t_launches);
+    else (k_adj_bc<2><<<grid, 128, 0, st>>>(W, gW, gvw_col, g, ph, bc), ++t_launches);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -606,15 +606,15 @@ cudaError_t launch_adj_bc(const double* W, double* gW, double* gvw_col, const Ge
 cudaError_t launch_adj_prim(const double* U, const double* gW, double* gU, const Geo& g,
                             const Phys& ph, cudaStream_t st) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_adj_prim<<<grid_for(total, 256), 256, 0, st>>>(U, gW, gU, g, ph);
+  (k_adj_prim<<<grid_for(total, 256), 256, 0, st>>>(U, gW, gU, g, ph), ++t_launches);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_phi(const double* gvw_col, const double* xc, double* gphi, int p_t1,
                            int h_t1, int ext_t2, int begin, int count, double amp,
                            double two_pi_kappa, cudaStream_t st) {
-  k_adj_phi<<<grid_for(count, 128), 128, 0, st>>>(gvw_col, xc, gphi, p_t1, h_t1, ext_t2, begin,
-                                                   count, amp, two_pi_kappa);
+  (k_adj_phi<<<grid_for(count, 128), 128, 0, st>>>(gvw_col, xc, gphi, p_t1, h_t1, ext_t2, begin,
+                                                   count, amp, two_pi_kappa), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -630,10 +630,10 @@ cudaError_t launch_wall_loss(const double* W, double* part, int nparts, double* 
                              const Geo& g, const Phys& ph, int A, int side, double Tw,
                              cudaStream_t st) {
   const double lam_w = viscosity(Tw, ph) * ph.lam_fac;
-  k_wall_loss<<<nparts, 256, 0, st>>>(W, part, gT2, g, ph, A, side, Tw, lam_w);
+  (k_wall_loss<<<nparts, 256, 0, st>>>(W, part, gT2, g, ph, A, side, Tw, lam_w), ++t_launches);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sum_parts<<<1, 32, 0, st>>>(part, nparts, J);
+  (k_sum_parts<<<1, 32, 0, st>>>(part, nparts, J), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -641,7 +641,7 @@ cudaError_t launch_wall_loss_grad(const double* U, const double* gT2, double* dJ
                                   const Phys& ph, int A, int side, cudaStream_t st) {
   const int t1 = A == 0 ? 1 : 0, t2 = 3 - A - t1;
   const long long total = (long long)g.n[t1] * g.n[t2];
-  k_wall_loss_grad<<<grid_for(total, 128), 128, 0, st>>>(U, gT2, dJdU, g, ph, A, side);
+  (k_wall_loss_grad<<<grid_for(total, 128), 128, 0, st>>>(U, gT2, dJdU, g, ph, A, side), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -649,7 +649,7 @@ cudaError_t launch_lincomb(double* out, double c0, const double* x0, double c1, 
                            double c2, const double* x2, double c3, const double* x3, const Geo& g,
                            cudaStream_t st) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_lincomb<<<grid_for(total, 256), 256, 0, st>>>(out, c0, x0, c1, x1, c2, x2, c3, x3, g);
+  (k_lincomb<<<grid_for(total, 256), 256, 0, st>>>(out, c0, x0, c1, x1, c2, x2, c3, x3, g), ++t_launches);
   return cudaGetLastError();
 }
 

@@ -707,7 +707,7 @@ cudaError_t launch_face_t(const double* W, const double* G, double* R, const Geo
   int grid;
   face_shape(D, g, block, seg, grid);
   double* FB = seam_buffer(D, g, seg, fb);
-  k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg);
+  (k_face<D, SCHEME, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg), ++t_launches);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !FB) return e;
   return launch_face_seam(D, FB, R, g, accumulate, seg, false, st);
@@ -747,14 +747,14 @@ cudaError_t launch_face_seam(int D, const double* FB, double* R, const Geo& g, i
   const long long items = lines * ((g.n[D] + seg - 1) / seg - 1);
   const int grid = grid_for(items, 256);
   if (D == 0) {
-    if (fused) k_face_seam<0, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
-    else k_face_seam<0, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    if (fused) (k_face_seam<0, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
+    else (k_face_seam<0, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
   } else if (D == 1) {
-    if (fused) k_face_seam<1, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
-    else k_face_seam<1, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    if (fused) (k_face_seam<1, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
+    else (k_face_seam<1, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
   } else {
-    if (fused) k_face_seam<2, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
-    else k_face_seam<2, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg);
+    if (fused) (k_face_seam<2, true><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
+    else (k_face_seam<2, false><<<grid, 256, 0, st>>>(FB, R, g, accumulate, seg), ++t_launches);
   }
   return cudaGetLastError();
 }
@@ -785,8 +785,8 @@ cudaError_t launch_prim_bc(const double* U, double* W, float* W32, const Geo& g,
   const int block = ((g.p[0] + nb - 1) / nb + 31) / 32 * 32;
   const dim3 grid((g.p[0] + block - 1) / block, g.p[1] < 65535 ? g.p[1] : 65535,
                   g.p[2] < 65535 ? g.p[2] : 65535);
-  if (W32) k_prim_bc<true><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl);
-  else k_prim_bc<false><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl);
+  if (W32) (k_prim_bc<true><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl), ++t_launches);
+  else (k_prim_bc<false><<<grid, block, 0, st>>>(U, W, W32, g, ph, bc, ctl), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -794,8 +794,8 @@ cudaError_t launch_grad(const double* W, double* G, const Geo& g, const Phys& ph
   const int m = ph.visc_order == 6 ? 3 : 2;
   long long total = 1;
   for (int a = 0; a < 3; ++a) total *= g.n[a] + (a < g.ndim ? 2 * m : 0);
-  if (m == 3) k_grad<6><<<grid_for(total, 256), 256, 0, st>>>(W, G, g);
-  else k_grad<4><<<grid_for(total, 256), 256, 0, st>>>(W, G, g);
+  if (m == 3) (k_grad<6><<<grid_for(total, 256), 256, 0, st>>>(W, G, g), ++t_launches);
+  else (k_grad<4><<<grid_for(total, 256), 256, 0, st>>>(W, G, g), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -821,7 +821,7 @@ long long seam_capacity(const Geo& g) {
 
 cudaError_t launch_source(double* R, const double* W, const Geo& g, const Phys& ph, cudaStream_t st) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_source<<<grid_for(total, 256), 256, 0, st>>>(R, W, g, ph);
+  (k_source<<<grid_for(total, 256), 256, 0, st>>>(R, W, g, ph), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -829,7 +829,7 @@ cudaError_t launch_stage(int stage, const double* Un, const double* Us, const do
                          const double* W, const Geo& g, const Phys& ph, Ctl* ctl, double t_end,
                          cudaStream_t st, double dt_arg) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_stage<<<grid_for(total, 256), 256, 0, st>>>(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end, dt_arg);
+  (k_stage<<<grid_for(total, 256), 256, 0, st>>>(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end, dt_arg), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -841,14 +841,14 @@ cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, con
   const int block = ((g.n[0] + nb - 1) / nb + 31) / 32 * 32;
   const int j2 = (g.n[1] + 1) / 2;                                     // row pairs
   const dim3 grid((g.n[0] + block - 1) / block, j2 < 65535 ? j2 : 65535, g.n[2] < 65535 ? g.n[2] : 65535);
-  if (W32) k_stage_prim<true><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
-  else k_stage_prim<false><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end);
+  if (W32) (k_stage_prim<true><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end), ++t_launches);
+  else (k_stage_prim<false><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end), ++t_launches);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long total = (long long)g.p[0] * g.p[1] * g.p[2] - (long long)g.n[0] * g.n[1] * g.n[2];
   if (total <= 0) return cudaSuccess;
-  if (W32) k_halo_prim<true><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total);
-  else k_halo_prim<false><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total);
+  if (W32) (k_halo_prim<true><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total), ++t_launches);
+  else (k_halo_prim<false><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -861,28 +861,28 @@ int dt_partial_count(const Geo& g) {
 
 cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, double* partial,
                               int nparts, cudaStream_t st) {
-  k_dt_partial<<<nparts, kDtBlock, 0, st>>>(W, g, ph, partial);
+  (k_dt_partial<<<nparts, kDtBlock, 0, st>>>(W, g, ph, partial), ++t_launches);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,
                             double* dt_out, int clip_to_ctl, double t_end, cudaStream_t st) {
-  k_dt_final<<<1, kDtBlock, 0, st>>>(partial, ph.dt_fixed > 0.0 ? 0 : nparts, ph, ctl, dt_out,
-                                     clip_to_ctl, t_end);
+  (k_dt_final<<<1, kDtBlock, 0, st>>>(partial, ph.dt_fixed > 0.0 ? 0 : nparts, ph, ctl, dt_out,
+                                     clip_to_ctl, t_end), ++t_launches);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prim_to_cons(const double* W, double* U, int ncell, const Phys& ph,
                                 cudaStream_t st) {
-  k_prim_to_cons<<<grid_for(ncell, 256), 256, 0, st>>>(W, U, ncell, ph);
+  (k_prim_to_cons<<<grid_for(ncell, 256), 256, 0, st>>>(W, U, ncell, ph), ++t_launches);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wall_velocity(const double* phi, double* vw, const double* xc, int p, int h,
                                  int begin, int count, double amp, double two_pi_kappa,
                                  cudaStream_t st) {
-  k_wall_velocity<<<grid_for(p, 128), 128, 0, st>>>(phi, vw, xc, p, h, begin, count, amp,
-                                                    two_pi_kappa);
+  (k_wall_velocity<<<grid_for(p, 128), 128, 0, st>>>(phi, vw, xc, p, h, begin, count, amp,
+                                                    two_pi_kappa), ++t_launches);
   return cudaGetLastError();
 }
 

@@ -553,7 +553,7 @@ cudaError_t launch_t(const MixedIn& in, double* R, const Geo& g, const PhysF& pf
     while (seg > 8 && lines * ((g.n[D] + seg - 1) / seg) < 152LL * 4 * 128) seg >>= 1;
   }
   const long long total = lines * ((g.n[D] + seg - 1) / seg);
-  k_face_mixed<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(in, R, g, pf, accumulate, seg);
+  (k_face_mixed<D, SCHEME, VISC><<<grid_for(total, block), block, 0, st>>>(in, R, g, pf, accumulate, seg), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -569,12 +569,12 @@ cudaError_t launch_tile(int D, const MixedIn& in, double* R, const Geo& g, const
     cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<1, SCHEME, VISC, NWARP, FPW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_face_mixed_t<1, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+    (k_face_mixed_t<1, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate), ++t_launches);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_face_mixed_t<2, SCHEME, VISC, NWARP, FPW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_face_mixed_t<2, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate);
+    (k_face_mixed_t<2, SCHEME, VISC, NWARP, FPW><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, accumulate), ++t_launches);
   }
   return cudaGetLastError();
 }
@@ -585,7 +585,7 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
   if (D == 0) {
     const long long lines = (long long)g.n[1] * g.n[2];
     const dim3 grid((g.n[0] + kXCells - 1) / kXCells, (unsigned)((lines + kXRows - 1) / kXRows));
-    k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(in, R, g, pf, accumulate);
+    (k_face_mixed_x<SCHEME, VISC><<<grid, dim3(32, kXRows), 0, st>>>(in, R, g, pf, accumulate), ++t_launches);
     return cudaGetLastError();
   }
   const int other = D == 1 ? 2 : 1;
@@ -618,13 +618,13 @@ cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const fl
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st) {
   long long total = 1;
   for (int a = 0; a < 3; ++a) total *= g.n[a] + (a < g.ndim ? 4 : 0);
-  k_grad32<<<grid_for(total, 256), 256, 0, st>>>(W32, G32, g);
+  (k_grad32<<<grid_for(total, 256), 256, 0, st>>>(W32, G32, g), ++t_launches);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
                                 int nparts, cudaStream_t st) {
-  k_dt_partial32<<<nparts, kDtBlock, 0, st>>>(W32, g, phys_f(ph), partial);
+  (k_dt_partial32<<<nparts, kDtBlock, 0, st>>>(W32, g, phys_f(ph), partial), ++t_launches);
   return cudaGetLastError();
 }
 

@@ -160,7 +160,7 @@ cudaError_t launch_d(const double* W, const double* G, double* R, const Geo& g, 
   int grid;
   face_shape(D, g, block, seg, grid);
   double* FB = seam_buffer(D, g, seg, fb);
-  k_face_teno<D, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg);
+  (k_face_teno<D, VORD><<<grid, block, 0, st>>>(W, G, R, FB, g, ph, accumulate, seg), ++t_launches);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !FB) return e;
   return launch_face_seam(D, FB, R, g, accumulate, seg, true, st);

@@ -95,3 +95,24 @@ def test_autotune_mixed_is_a_no_op():
     before = s.rhs(Ud).cpu().numpy()
     s.autotune_faces(Ud)
     assert np.array_equal(s.rhs(Ud).cpu().numpy(), before)
+
+
+def test_profiler_counts_kernels():
+    """The profiler's launch count is the number of kernels: a face call with segment seams is two
+    kernels (the face kernel and its seam kernel), one without (segments shorter than the seam
+    buffer's minimum of 4 cells run without it)."""
+    from paper_2406_19494_gb300.solver import Solver
+    c = CASE()
+    case, grid, U = padded_state(c, seed=12)
+    s = Solver(c)
+    Ud = torch.from_numpy(U).cuda()
+    for seg, per_call in ((4, 2), (3, 1)):
+        s.tune_faces(128, seg)
+        s.profile(True)
+        s.profile_read(True)
+        s.rhs(Ud)
+        p = s.profile_read(True)
+        s.profile(False)
+        for axis in ("face_x", "face_y", "face_z"):
+            assert p[axis][1] == per_call, (seg, axis, p[axis])
+        assert p["prim_bc"][1] == 1 and p["grad"][1] == 1, p
