@@ -223,9 +223,10 @@ int fluid_check(fluid_solver* s, void* stream);
  * kernels agree with the tiles to FP32 rounding. */
 int fluid_tune_faces(fluid_solver* s, int block, int seg);
 
-/* Time the FP64 face kernels (block 128, segments of 8 to 32 cells and the automatic choice) on the
- * primitives of U_dev (device, the solver's padded layout; not modified) and keep the fastest
- * segment length per axis; the launch shape never changes a result, so this only changes speed.
+/* Time the FP64 face kernels (blocks of 128 threads with segments of 8 to 32 cells and the
+ * automatic choice, then blocks of 64 and 32 threads with the fastest segment length) on the
+ * primitives of U_dev (device, the solver's padded layout; not modified) and keep the fastest shape
+ * per axis; the launch shape never changes a result, so this only changes speed.
  * Enqueued on `stream` and synchronised; uses the solver's scratch, so no other call on the solver
  * may run meanwhile.  No-op (FLUID_OK) for FLUID_PREC_MIXED.  FLUID_EINVAL for a NULL solver or a
  * foreign pointer, FLUID_ECUDA on a launch error. */

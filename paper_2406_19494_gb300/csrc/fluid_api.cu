@@ -51,6 +51,7 @@ struct fluid_solver {
   };
   int face_block = 0, face_seg = 0;   // launch shape of the face kernels (0 = automatic)
   int face_seg_d[3] = {0, 0, 0};      // FP64 path: segment length per axis (0 = automatic)
+  int face_block_d[3] = {0, 0, 0};    // FP64 path: threads per block per axis (0 = 128)
   // adjoint scratch (cfg.adjoint != 0)
   double* gW = nullptr;            // cotangent of the primitives, NW * ncell
   double* gG = nullptr;            // cotangent of the velocity gradients, NG * ncell
@@ -266,7 +267,7 @@ int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
     FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad(s->W, s->G, g, s->ph, st));
   for (int d = 0; d < g.ndim; ++d)
     FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
-             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block, s->face_seg_d[d],
+             fl::launch_face(d, s->W, s->G, R, g, s->ph, d > 0, s->face_block_d[d], s->face_seg_d[d],
                              fl::SeamBuf{s->FB, s->fb_cap}, st));
   return FLUID_OK;
 }
@@ -824,7 +825,10 @@ int fluid_tune_faces(fluid_solver* s, int block, int seg) {
   if (seg < 0 && !s->mixed) return fail(s, FLUID_EINVAL, "seg must be >= 0 for the FP64 path");
   s->face_block = block;
   s->face_seg = seg;
-  for (int d = 0; d < 3; ++d) s->face_seg_d[d] = seg;
+  for (int d = 0; d < 3; ++d) {
+    s->face_seg_d[d] = seg;
+    s->face_block_d[d] = block;
+  }
   return FLUID_OK;
 }
 
@@ -842,32 +846,46 @@ int fluid_autotune_faces(fluid_solver* s, const double* U_dev, void* stream) {
     cudaEventDestroy(e0);
     return fail(s, FLUID_ECUDA, "cudaEventCreate");
   }
-  // candidates: the automatic rule (0) and segments of 8 to 32 cells; block 128
+  // candidates: the automatic rule (0) and segments of 8 to 32 cells with blocks of 128 threads,
+  // then blocks of 64 and 32 threads with the fastest segment length
   static const int kCand[] = {0, 8, 10, 12, 14, 16, 17, 18, 19, 20, 22, 24, 28, 32};
   cudaError_t e = cudaSuccess;
   for (int d = 0; d < g.ndim && e == cudaSuccess; ++d) {
-    int best_seg = 0;
+    int best_seg = 0, best_block = 128;
     float best_ms = 0.0f;
+    bool have = false;
+    auto trial = [&](int block, int seg) {
+      auto launch = [&]() {
+        return fl::launch_face(d, s->W, s->G, s->R, g, s->ph, 0, block, seg, fl::SeamBuf{s->FB, s->fb_cap}, st);
+      };
+      if ((e = launch()) != cudaSuccess) return;                      // warm-up
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return;
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+      if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess) return;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return;
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return;
+      if (!have || ms < best_ms) {
+        have = true;
+        best_ms = ms;
+        best_seg = seg;
+        best_block = block;
+      }
+    };
     for (int c : kCand) {
       if (c > g.n[d]) continue;
-      auto launch = [&]() {
-        return fl::launch_face(d, s->W, s->G, s->R, g, s->ph, 0, 128, c, fl::SeamBuf{s->FB, s->fb_cap}, st);
-      };
-      if ((e = launch()) != cudaSuccess) break;                       // warm-up
-      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
-      if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess) break;
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.0f;
-      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
-      if (c == 0 || ms < best_ms) {
-        best_ms = ms;
-        best_seg = c;
-      }
+      trial(128, c);
+      if (e != cudaSuccess) break;
     }
-    if (e == cudaSuccess) s->face_seg_d[d] = best_seg;
+    for (int b : {64, 32}) {
+      if (e != cudaSuccess) break;
+      trial(b, best_seg);
+    }
+    if (e == cudaSuccess) {
+      s->face_seg_d[d] = best_seg;
+      s->face_block_d[d] = best_block;
+    }
   }
-  s->face_block = 128;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(s, e, "fluid_autotune_faces");
