@@ -73,8 +73,21 @@ size_t footprint(const fluid_config& c) {
   const bool visc = c.visc_law != FLUID_VISC_NONE;
   size_t b = 8 * (nc * (fl::NW + 3 * fl::NV) + metric + 4096);   // W, A, R, the state U, metrics
   // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients and face metrics
-  if (c.precision == FLUID_PREC_MIXED) b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
-  else if (visc) b += 8 * nc * fl::NG;
+  if (c.precision == FLUID_PREC_MIXED) {
+    b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
+  } else {
+    if (visc) b += 8 * nc * fl::NG;
+    // seam buffer of the face kernels: 10 doubles per segment of kSeamMinSeg cells, on the axis
+    // with the most segments
+    size_t cap = 0;
+    for (int a = 0; a < c.ndim; ++a) {
+      size_t lines = 1;
+      for (int d = 0; d < 3; ++d)
+        if (d != a) lines *= (size_t)c.n[d];
+      cap = std::max(cap, lines * (((size_t)c.n[a] + fl::kSeamMinSeg - 1) / fl::kSeamMinSeg));
+    }
+    b += 8 * 10 * cap;
+  }
   return b;
 }
 
