@@ -185,8 +185,8 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
 // ------------------------------------------------------------------------------------------------
 // centre gradients G[c*3+b] = d u_c / d x_b, only where the cell is interior along b (the only
 // places the face fluxes read it), for the cells the face stencils reach along the other axes:
-//   order 4: ((f[-2] - f[+2]) + 8 (f[+1] - f[-1])) / 12 * mc
-//   order 6: (45 (f[+1] - f[-1]) - 9 (f[+2] - f[-2]) + (f[+3] - f[-3])) / 60 * mc
+//   order 4: ((f[-2] - f[+2]) + 8 (f[+1] - f[-1])) * (mc / 12)
+//   order 6: (45 (f[+1] - f[-1]) - 9 (f[+2] - f[-2]) + (f[+3] - f[-3])) * (mc / 60)
 // ------------------------------------------------------------------------------------------------
 template <int ORDER>
 __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo g) {
@@ -208,16 +208,16 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
     for (int b = 0; b < 3; ++b) {
       const bool inb = b < g.ndim && c[b] >= g.h[b] && c[b] < g.h[b] + g.n[b];
       const int s = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
-      const double m = inb ? g.mc[b][c[b]] : 0.0;
+      // the stencil's 1/12 (1/60) and the metric as one factor per axis
+      const double cm = inb ? (ORDER == 4 ? kTwelfth : 1.0 / 60.0) * g.mc[b][c[b]] : 0.0;
       for (int comp = 0; comp < 3; ++comp) {
         double d = 0.0;
         if (inb) {
           const double* f = W + (1 + comp) * g.ncell + cell;
           if (ORDER == 4)
-            d = ((f[-2 * s] - f[2 * s]) + 8.0 * (f[s] - f[-s])) * kTwelfth * m;
+            d = ((f[-2 * s] - f[2 * s]) + 8.0 * (f[s] - f[-s])) * cm;
           else
-            d = (45.0 * (f[s] - f[-s]) - 9.0 * (f[2 * s] - f[-2 * s]) + (f[3 * s] - f[-3 * s])) *
-                (1.0 / 60.0) * m;
+            d = (45.0 * (f[s] - f[-s]) - 9.0 * (f[2 * s] - f[-2 * s]) + (f[3 * s] - f[-3 * s])) * cm;
         }
         G[(comp * 3 + b) * g.ncell + cell] = d;
       }
