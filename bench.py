@@ -328,7 +328,7 @@ def run_fluid(args):
         "roofline": {"bound": "alu", "kernel": "k_face (x, y, z) with its seam kernel, FP64", "achieved": achieved, "peak": peak64,
                      "unit": "TFLOP/s", "frac": achieved / peak64 if achieved else None,
                      "traffic": face_traffic(ncell),
-                     "traffic_note": "bytes per launch: ncu dram read+write of the 64^3 capture scaled by cells",
+                     "traffic_note": "bytes per launch: ncu dram read+write of the benchmark workload's x, y, z face launches (mean), profiles/k_face_tgv128_traffic.md",
                      "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); "
                                     "measured by the FMA probe as fp64_fma_probe_tflops",
                      "fp64_fma_probe_tflops": fp64_probe / 1e3 if fp64_probe else None,
