@@ -234,8 +234,8 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   const double Dd = mL - mR;
   const double iDd = fl_rcp(Dd);
   const double Ss = Nn * iDd;
-  const bool left = (SL >= 0.0) || (Ss >= 0.0);
-  const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
+  const bool left = fl_nonneg(SL) || fl_nonneg(Ss);
+  const bool star = left ? !fl_nonneg(SL) : fl_pos(SR);
   const double r = left ? rL : rR, p = left ? pL : pR, E = left ? EL : ER;
   const double un = left ? unL : unR, S = left ? SL : SR, m = left ? mL : mR;
   const double ir = left ? irL : irR;

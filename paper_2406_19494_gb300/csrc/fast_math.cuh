@@ -72,28 +72,56 @@ FL_HD double fl_ipow(double x, int n) {
   return r;
 }
 
-// x^(p/q) for 0 < p, q <= 16 and x in (1e-15, 1e15) (so that x^p and y^q stay normal and
-// finite): y = x^(p/q) is the positive root of y^q = a, a = x^p.  An FP32 estimate
-// y0 = 2^(e log2 x) from the hardware approximations (ex2.approx, lg2.approx; relative error below
-// about 3e-6 on this range) takes one step of Halley's method for that equation,
+// x^(p/q) for 0 < p, q <= 16 and x in [2^-B, 2^B): y = x^(p/q) is the positive root of y^q = a,
+// a = x^p.  B (at most 49, and such that the FP32 estimate and x^p stay normal: |(p/q) log2 x| <
+// 125, |p log2 x| < 1021) is set on the host (set_power_law) as the high-word bounds hw_lo, hw_hi:
+// the high word of a positive double orders like the number, so the range test, the conversion of
+// x to FP32 (truncated: the estimate needs only its leading bits) and the exact conversion of the
+// estimate back to FP64 are integer operations.  An FP32 estimate y0 = 2^(e log2 x) from the
+// hardware approximations (ex2.approx, lg2.approx; relative error below about 3e-6 on this range)
+// takes one step of Halley's method for y^q = a,
 // y1 = y0 ((q + 1) a + (q - 1) y0^q) / ((q - 1) a + (q + 1) y0^q), whose error is about
 // (q^2 - 1) / 12 times the cube of y0's, below FP64 rounding.  The step is written as the
 // correction y1 = y0 + 2 y0 (a - y0^q) / ((q + 1) y0^q + (q - 1) a), of relative size about 1e-6,
 // so that its own rounding stays far below an ulp of y1.  Other x take the library
 // exp(e log x).  e32 is p/q in FP32.  Checked on the GPU against x^(p/q) (fluid_check_pow).
-FL_HD double fl_pow_rational(double x, int p, int q, float e32) {
+FL_HD double fl_pow_rational(double x, int p, int q, float e32, int hw_lo, int hw_hi) {
 #ifdef __CUDA_ARCH__
-  if (x > 1e-15 && x < 1e15) {
+  const int hw = __double2hiint(x);
+  if (hw >= hw_lo && hw < hw_hi) {
+    // exponent rebiased from 1023 to 127, the top 23 fraction bits
+    const float xf = __int_as_float(((hw - ((1023 - 127) << 20)) << 3) |
+                                    (int)((unsigned)__double2loint(x) >> 29));
     float l, y32;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"((float)x));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(xf));
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y32) : "f"(e32 * l));
-    const double y0 = (double)y32;
+    const int yb = __float_as_int(y32);
+    const double y0 = __hiloint2double((yb >> 3) + ((1023 - 127) << 20), yb << 29);
     const double a = fl_ipow(x, p), yq = fl_ipow(y0, q);
     const double den = fma(0.5 * (double)(q + 1), yq, (0.5 * (double)(q - 1)) * a);
     return fma(y0 * (a - yq), fl_rcp(den), y0);
   }
 #endif
   return exp(((double)p / (double)q) * log(x));
+}
+
+// x >= 0 and x > 0 from the sign and magnitude bits (integer operations in device code; -0 >= 0
+// holds and -0 > 0 does not; a NaN counts by its sign bit)
+FL_HD bool fl_nonneg(double x) {
+#ifdef __CUDA_ARCH__
+  const int hw = __double2hiint(x);
+  return hw >= 0 || ((hw & 0x7fffffff) | __double2loint(x)) == 0;
+#else
+  return x >= 0.0;
+#endif
+}
+FL_HD bool fl_pos(double x) {
+#ifdef __CUDA_ARCH__
+  const int hw = __double2hiint(x);
+  return hw >= 0 && (hw | __double2loint(x)) != 0;
+#else
+  return x > 0.0;
+#endif
 }
 
 }  // namespace fl

@@ -36,6 +36,7 @@ struct Phys {
   double mu_ref, T_ref, iT_ref, visc_exp, suth_S;
   int visc_p, visc_q;  // power law: visc_exp = visc_p / visc_q (small integers), else visc_q = 0
   float visc_e32;      // visc_exp in FP32
+  int visc_hw_lo, visc_hw_hi;   // high-word bounds of the fast range of fl_pow_rational
   int visc, weno;
   int visc_order;     // central differences of the dissipative fluxes: 4 or 6
   double eps;
@@ -67,7 +68,8 @@ __host__ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return ph.mu_ref;
   const double r = T * ph.iT_ref;
   if (ph.visc == FLUID_VISC_POWER) {
-    if (ph.visc_q > 0) return ph.mu_ref * fl_pow_rational(r, ph.visc_p, ph.visc_q, ph.visc_e32);
+    if (ph.visc_q > 0)
+      return ph.mu_ref * fl_pow_rational(r, ph.visc_p, ph.visc_q, ph.visc_e32, ph.visc_hw_lo, ph.visc_hw_hi);
     return ph.mu_ref * exp(ph.visc_exp * log(r));
   }
   // Sutherland
@@ -88,12 +90,18 @@ inline void set_power_law(Phys& ph, double e) {
   ph.visc_exp = e;
   ph.visc_e32 = (float)e;
   ph.visc_p = ph.visc_q = 0;
+  ph.visc_hw_lo = ph.visc_hw_hi = 0;
   for (int q = 1; q <= 16; ++q) {
     const double pq = e * q;
     const int p = (int)(pq + 0.5);
     if (p >= 1 && p <= 16 && fabs((double)p / q - e) <= 4.0 * 2.220446049250313e-16 * fabs(e)) {
       ph.visc_p = p;
       ph.visc_q = q;
+      // |log2 x| < B keeps the FP32 estimate and x^p normal
+      int B = 49;
+      while (B > 1 && (B * e >= 125.0 || B * p >= 1021)) --B;
+      ph.visc_hw_lo = (1023 - B) << 20;
+      ph.visc_hw_hi = (1023 + B) << 20;
       return;
     }
   }

@@ -150,8 +150,8 @@ FL_HD void hllc(const double wl[5], const double wr[5], const Phys& ph,
   const double mL = rL * (SL - unL), mR = rR * (SR - unR);
   const double Ss = (pR - pL + unL * mL - unR * mR) * fl_rcp(mL - mR);
 
-  const bool left = (SL >= 0.0) || (Ss >= 0.0);
-  const bool star = left ? !(SL >= 0.0) : (SR > 0.0);
+  const bool left = fl_nonneg(SL) || fl_nonneg(Ss);
+  const bool star = left ? !fl_nonneg(SL) : fl_pos(SR);
   const double r = left ? rL : rR;
   const double p = left ? pL : pR;
   const double H = left ? HL : HR;
