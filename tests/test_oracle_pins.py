@@ -533,3 +533,331 @@ def test_taylor_green_initial_dissipation():
     rate = nf.kinetic_energy_rate(U, R, case, grid) / vol
     assert abs(nf.kinetic_energy(U, case, grid) / vol - 0.125) < 2e-3
     assert abs(-rate - 0.75 / 1600.0) < 0.03 * 0.75 / 1600.0, rate
+
+
+# ---------------------------------------------------------------------------------------------
+# viscosity laws (Sec. 3.2 uses Sutherland's law)
+# ---------------------------------------------------------------------------------------------
+def _suth_case(mu_ref, T_ref, S):
+    return nf.Case(wl.random_box(1, (4, 1, 1), visc="sutherland", mu_ref=mu_ref, suth_S=S) |
+                   dict(T_ref=T_ref))
+
+
+def test_sutherland_reproduces_measured_air_viscosity():
+    """Sutherland's law with White's constants for air against measured viscosities of air
+    (tests/golden/air_viscosity.txt): within 1 % over 200-400 K.  A wrong exponent (1/2 instead of
+    3/2) or the two sums T_ref + S and T + S exchanged misses by 10 % or more."""
+    case = _suth_case(1.716e-5, 273.15, 110.4)
+    rows = read_golden("air_viscosity.txt")
+    T = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows]) * 1e-7
+    mu = nf.viscosity(T, case)
+    assert np.max(np.abs(mu / ref - 1.0)) < 0.01, mu / ref
+    assert nf.viscosity(np.array([273.15]), case)[0] == pytest.approx(1.716e-5, rel=1e-15)
+
+
+def test_sutherland_log_slope():
+    """d ln mu / d ln T = 3/2 - T / (T + S) for Sutherland's law (differentiate
+    ln mu = 3/2 ln T - ln(T + S) + const): mu grows like T^(3/2) far below S and like T^(1/2) far
+    above it.  Checked by central differences of the oracle's mu in ln T."""
+    S = 0.368
+    case = _suth_case(0.7, 1.3, S)
+    h = 1e-4
+    for T in (0.01, 0.2, 1.0, 3.0, 50.0):
+        lo, hi = nf.viscosity(np.array([T * math.exp(-h), T * math.exp(h)]), case)
+        slope = (math.log(hi) - math.log(lo)) / (2 * h)
+        assert abs(slope - (1.5 - T / (T + S))) < 1e-7, (T, slope)
+
+
+def test_power_law_viscosity():
+    """mu = mu_ref (T / T_ref)^e: mu(T_ref) = mu_ref and the log slope is the exponent."""
+    case = nf.Case(wl.random_box(1, (4, 1, 1), visc="power", mu_ref=0.3) | dict(T_ref=2.0,
+                                                                               visc_exp=0.7))
+    assert nf.viscosity(np.array([2.0]), case)[0] == 0.3
+    a, b = nf.viscosity(np.array([1.0, 4.0]), case)
+    assert math.log(b / a) / math.log(4.0) == pytest.approx(0.7, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------
+# CFL time step: the viscous branch
+# ---------------------------------------------------------------------------------------------
+def _rest_state(ndim, n, rho, p, mu, Pr, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), stretch=None):
+    P = ("periodic", "periodic")
+    c = wl.random_box(ndim, (n,) * 3, bc=(P, P, P), visc="constant", mu_ref=mu, lo=lo, hi=hi,
+                      stretch=stretch) | dict(Pr=Pr, cfl=0.5)
+    return padded_state(c, uniform=(rho, 0.0, 0.0, 0.0, p))
+
+
+def test_cfl_viscous_branch_worked_examples():
+    """Fluid at rest: hand-worked time steps (tests/golden/cfl_worked_examples.txt) where the
+    viscous limit binds (with gamma / Pr and with the 4/3 of the normal stress) and where the
+    acoustic limit binds."""
+    for name, n, rho, p, mu, Pr, dt in read_golden("cfl_worked_examples.txt"):
+        for ndim in (1, 2, 3):
+            case, grid, U = _rest_state(ndim, int(n), float(rho), float(p), float(mu), float(Pr))
+            got = nf.cfl_dt(U, case, grid)
+            assert got == pytest.approx(float(dt), rel=1e-14), (name, ndim, got)
+
+
+def test_cfl_viscous_branch_scaling():
+    """The viscous limit scales like dx^2 / nu: halving the spacing quarters it, doubling mu halves
+    it, doubling rho doubles it; on a stretched axis the smallest cell decides."""
+    base = _rest_state(2, 16, 1.0, 1.0, 2.0, 0.7)
+    dt0 = nf.cfl_dt(base[2], base[0], base[1])
+    fine = _rest_state(2, 32, 1.0, 1.0, 2.0, 0.7)
+    assert nf.cfl_dt(fine[2], fine[0], fine[1]) == pytest.approx(dt0 / 4, rel=1e-13)
+    visc = _rest_state(2, 16, 1.0, 1.0, 4.0, 0.7)
+    assert nf.cfl_dt(visc[2], visc[0], visc[1]) == pytest.approx(dt0 / 2, rel=1e-13)
+    dens = _rest_state(2, 16, 2.0, 2.0, 2.0, 0.7)        # same sound speed, twice the density
+    assert nf.cfl_dt(dens[2], dens[0], dens[1]) == pytest.approx(dt0 * 2, rel=1e-13)
+    case, grid, U = _rest_state(2, 16, 1.0, 1.0, 2.0, 0.7, lo=(0.0, -1.0, 0.0),
+                                stretch=("uniform", "tanh2", "uniform"))
+    dy = grid.axes[1].dx[3:3 + 16].min()
+    k = 2.0 * max(4.0 / 3.0, 1.4 / 0.7)
+    assert nf.cfl_dt(U, case, grid) == pytest.approx(0.5 * dy * dy / (k * 2.0), rel=1e-13)
+    assert dy < 2.0 / 16
+
+
+# ---------------------------------------------------------------------------------------------
+# adiabatic wall and Dirichlet inflow halos
+# ---------------------------------------------------------------------------------------------
+def test_adiabatic_wall_face_values():
+    """Adiabatic no-slip wall: at the wall face the interpolated velocity vanishes and so does the
+    normal temperature derivative (fourth-order stencils); density and pressure are mirrored."""
+    P = ("periodic", "periodic")
+    c = wl.random_box(2, (10, 12, 1), bc=(P, ("adiabatic", "adiabatic"), P))
+    case, grid, U = padded_state(c, seed=3)
+    nf.fill_halos(U, case, grid)
+    W, T = nf.cons_to_prim(U, case)
+    h, n = 3, 12
+    ix = slice(h, h + 10)
+    for a in (h - 1, h + n - 1):                     # faces a + 1/2: south and north walls
+        f = lambda q, o: q[0, a + o, ix]
+        interp = lambda q: (9.0 * (f(q, 0) + f(q, 1)) - (f(q, -1) + f(q, 2))) / 16.0
+        dn = lambda q: (f(q, -1) - f(q, 2)) + 27.0 * (f(q, 1) - f(q, 0))
+        for comp in (1, 2, 3):
+            assert np.max(np.abs(interp(W[comp]))) < 1e-15
+        assert np.max(np.abs(dn(T))) < 1e-13 * np.max(np.abs(T))
+    for m in range(h):
+        for g, s in ((h - 1 - m, h + m), (h + n + m, h + n - 1 - m)):
+            assert np.allclose(W[0, 0, g, ix], W[0, 0, s, ix], rtol=1e-15, atol=0)
+            assert np.allclose(W[4, 0, g, ix], W[4, 0, s, ix], rtol=1e-15, atol=0)
+
+
+def test_inflow_halo_layers_hold_the_profile():
+    """Dirichlet inflow: every ghost layer of the inflow face converts back to the prescribed
+    primitive profile, over the interior tangential range."""
+    c = wl.porous_bl_case(nx=16, ny=20)
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xc = grid.axes[0].xc[3:3 + 16]
+    yc = grid.axes[1].xc[3:3 + 20]
+    case, grid, U = padded_state(c, prims=wl.porous_bl_prims(c, xc, yc))
+    U[:, :, :, :3] = 7.0                             # stale values that the pass must replace
+    prof = wl.porous_bl_inflow(c, grid.axes[1].xc)
+    nf.fill_halos(U, case, grid, wl.porous_phi(c), {(0, 0): prof})
+    W, _ = nf.cons_to_prim(U, case)
+    for g in range(3):
+        got = W[:, 0, 3:3 + 20, g]
+        assert max(rel_err(got, prof[:, 0, 3:3 + 20])) < 1e-14, g
+
+
+# ---------------------------------------------------------------------------------------------
+# wall heat flux, wall shear and the integrated loss
+# ---------------------------------------------------------------------------------------------
+def _slab(T_lo, T_hi, prof_u=None, stretch_x=False, visc="power"):
+    """2-D fluid between isothermal walls at y = -1 (T_lo) and y = 1 (T_hi): uniform pressure,
+    T linear in y (so the wall mirror continues it exactly on a uniform y grid), velocity from
+    prof_u(y) or zero."""
+    c = wl.random_box(2, (8, 16, 1), bc=(("zero_gradient", "zero_gradient"), ("wall", "wall"),
+                                          ("periodic", "periodic")),
+                      visc=visc, mu_ref=0.05, t_wall=((1.0, 1.0), (T_lo, T_hi), (1.0, 1.0)),
+                      lo=(0.0, -1.0, 0.0), hi=(2.5, 1.0, 1.0),
+                      stretch=("tanh1" if stretch_x else "uniform", "uniform", "uniform"),
+                      beta=(1.3, 0.0, 0.0))
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xc = grid.axes[0].xc[3:11]
+    yc = grid.axes[1].xc[3:19]
+    y2, x2 = np.meshgrid(yc, xc, indexing="ij")
+    T = T_lo + (T_hi - T_lo) * (y2 + 1.0) / 2.0
+    p = np.full_like(T, 1.3)
+    u = prof_u(y2) if prof_u is not None else 0 * T
+    W = np.stack([p / (case.R * T), u, 0 * T, 0 * T, p])[:, None]
+    return padded_state(c, prims=W)
+
+
+def test_wall_heat_flux_of_a_linear_temperature():
+    """Fluid at rest with T linear between the walls: q_w = -lambda(T_w) dT/dy on both walls (the
+    derivative along +y), exactly, and J = q_w times the wall length, also on a stretched wall
+    axis (the cell widths along the wall sum to its length)."""
+    T_lo, T_hi = 1.0, 2.2
+    for stretch_x in (False, True):
+        case, grid, U = _slab(T_lo, T_hi, stretch_x=stretch_x)
+        grad = (T_hi - T_lo) / 2.0
+        for side, Tw in ((0, T_lo), (1, T_hi)):
+            lam = 0.05 * Tw ** 0.7 * case.cp / case.Pr
+            qw, tw = nf.wall_fluxes(U, case, grid, 1, side)
+            assert qw.shape[-1] == 8
+            assert np.max(np.abs(qw + lam * grad)) < 1e-12 * lam * grad, (side, qw)
+            assert np.max(np.abs(tw)) < 1e-15
+            J = nf.wall_heat_loss(U, case, grid, 1, side)
+            assert J == pytest.approx(-lam * grad * 2.5, rel=1e-12)
+
+
+def test_wall_shear_of_couette_flow():
+    """Linear shear u = s (y + 1) vanishes at the south wall, where the no-slip mirror continues it
+    exactly: the wall shear is mu(T_w) s, and the heat flux is zero in an isothermal fluid."""
+    s = 0.8
+    case, grid, U = _slab(1.7, 1.7, prof_u=lambda y: s * (y + 1.0), visc="sutherland")
+    qw, tw = nf.wall_fluxes(U, case, grid, 1, 0)
+    mu_w = 0.05 * 1.7 ** 1.5 * (1.0 + 0.4) / (1.7 + 0.4)
+    assert np.max(np.abs(tw - mu_w * s)) < 1e-13
+    assert np.max(np.abs(qw)) < 1e-13
+
+
+# ---------------------------------------------------------------------------------------------
+# stretched-grid geometry and metrics (tanh mappings; Sec. 3.2 gives beta = 2.2)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("stretch,beta", [("tanh1", 2.2), ("tanh2", 2.0), ("uniform", 0.0)])
+def test_axis_geometry_and_metrics(stretch, beta):
+    """Faces at eta = 0 and 1 land on the domain ends; cell widths sum to the length; centres are
+    face midpoints; the centre and face metrics d(index)/dx equal n over the derivative of the
+    face mapping taken by fourth-order central differences of x(eta) alone."""
+    n, h, lo, hi = 24, 3, -0.3, 1.9
+    ax = nf.Axis(n, h, lo, hi, stretch, beta)
+    xf_lo = ax.xc[h] - 0.5 * ax.dx[h]
+    xf_hi = ax.xc[h + n - 1] + 0.5 * ax.dx[h + n - 1]
+    assert xf_lo == pytest.approx(lo, abs=1e-15) and xf_hi == pytest.approx(hi, abs=1e-14)
+    assert np.sum(ax.dx[h:h + n]) == pytest.approx(hi - lo, rel=1e-14)
+    assert np.all(ax.dx > 0)
+    xmap = lambda eta: nf._map(stretch, beta, lo, hi, np.asarray(eta, dtype=np.float64))[0]
+    e = 1e-3
+    deriv = lambda eta: (-xmap(eta + 2 * e) + 8 * xmap(eta + e) - 8 * xmap(eta - e)
+                         + xmap(eta - 2 * e)) / (12 * e)
+    a = np.arange(-h, n + h, dtype=np.float64)
+    assert np.allclose(ax.mc, n / deriv((a + 0.5) / n), rtol=1e-9, atol=0)
+    assert np.allclose(ax.mf, n / deriv((a + 1.0) / n), rtol=1e-9, atol=0)
+    xf = xmap(np.arange(-h, n + h + 1) / n)
+    assert np.allclose(ax.xc, 0.5 * (xf[1:] + xf[:-1]), rtol=0, atol=1e-15)
+    if stretch == "tanh1":
+        assert np.all(np.diff(ax.dx[h:h + n]) > 0)               # clustered at the low end
+    if stretch == "tanh2":
+        assert np.allclose(ax.dx[h:h + n], ax.dx[h:h + n][::-1], rtol=1e-12, atol=0)
+        assert ax.dx[h] < ax.dx[h + n // 2] / 3                  # clustered at both ends
+
+
+def _stretched_visc_error(n):
+    """Max error of the dissipative fluxes on the y faces (normal stencils, face metric) and on the
+    x faces (tangential y stencils, centre metric) of a smooth 2-D field on a tanh-stretched y axis.
+    The field is sampled at the mapped centre positions x(eta_centre), so the uniform-index
+    stencils approximate the derivatives in eta to fourth order and the metrics convert them."""
+    P = ("periodic", "periodic")
+    c = wl.random_box(2, (n, n, 1), bc=(P, P, P), visc="power", mu_ref=0.1,
+                      lo=(0.0, -1.0, 0.0), hi=(2 * math.pi, 1.0, 1.0),
+                      stretch=("uniform", "tanh2", "uniform"), beta=(0.0, 1.8, 0.0))
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    h = 3
+    ymap = lambda eta: nf._map("tanh2", 1.8, -1.0, 1.0, eta)[0]
+    a = np.arange(-h, n + h, dtype=np.float64)
+    yc = ymap((a + 0.5) / n)
+    yf = ymap((a + 1.0) / n)
+    xc = grid.axes[0].xc
+    xf = xc + 0.5 * grid.axes[0].dx
+
+    def fields(x, y):
+        rho = 1.0 + 0.2 * np.sin(x) * np.cos(y)
+        u = np.sin(x) * np.cos(1.3 * y)
+        v = 0.5 * np.cos(x) * np.sin(y)
+        p = 1.0 + 0.1 * np.cos(x + y)
+        return rho, u, v, p
+
+    def exact(x, y, d):
+        rho, u, v, p = fields(x, y)
+        rx, ry = 0.2 * np.cos(x) * np.cos(y), -0.2 * np.sin(x) * np.sin(y)
+        ux, uy = np.cos(x) * np.cos(1.3 * y), -1.3 * np.sin(x) * np.sin(1.3 * y)
+        vx, vy = -0.5 * np.sin(x) * np.sin(y), 0.5 * np.cos(x) * np.cos(y)
+        px, py = -0.1 * np.sin(x + y), -0.1 * np.sin(x + y)
+        T = p / rho
+        Tg = ((px * rho - p * rx) / rho ** 2, (py * rho - p * ry) / rho ** 2)
+        mu = 0.1 * T ** 0.7
+        div = ux + vy
+        if d == 0:
+            tn = mu * (2 * ux - 2.0 / 3.0 * div)
+            tt = mu * (uy + vx)
+            return [tn, tt, u * tn + v * tt + mu * case.cp / case.Pr * Tg[0]]
+        tt = mu * (uy + vx)
+        tn = mu * (2 * vy - 2.0 / 3.0 * div)
+        return [tt, tn, u * tt + v * tn + mu * case.cp / case.Pr * Tg[1]]
+
+    y2, x2 = np.meshgrid(yc, xc, indexing="ij")
+    rho, u, v, p = fields(x2, y2)
+    W = np.stack([rho, u, v, 0 * u, p])[:, None]
+    T = W[4] / (W[0] * case.R)
+    err = 0.0
+    inner_x = (0, slice(h, h + n), slice(None))      # x faces over interior rows
+    F = nf.viscous_face_flux(W, T, case, grid, 0)
+    ye, xe = np.meshgrid(yc, xf[h - 1:h + n], indexing="ij")
+    for got, ex in zip((F[1], F[2], F[4]), exact(xe, ye, 0)):
+        err = max(err, np.max(np.abs(got[inner_x] - ex[h:h + n])))
+    inner_y = (0, slice(None), slice(h, h + n))      # y faces over interior columns
+    F = nf.viscous_face_flux(W, T, case, grid, 1)
+    ye, xe = np.meshgrid(yf[h - 1:h + n], xc, indexing="ij")
+    for got, ex in zip((F[1], F[2], F[4]), exact(xe, ye, 1)):
+        err = max(err, np.max(np.abs(got[inner_y] - ex[:, h:h + n])))
+    return err
+
+
+def test_viscous_flux_fourth_order_on_stretched_grid():
+    """Fourth-order convergence of the dissipative fluxes on a tanh-stretched axis: a wrong face or
+    centre metric (for instance the cell width in place of the mapping derivative) drops the order
+    to two or less."""
+    e = [_stretched_visc_error(n) for n in (16, 32, 64)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] > 3.6, (e, orders)
+
+
+def test_wall_fluxes_agree_with_the_face_flux_on_stretched_walls():
+    """On a stretched wall-normal axis (random state, both walls): the wall heat flux is minus the
+    energy component of the dissipative face flux at the wall face (the face velocity is zero there)
+    and the wall shear is its tangential momentum component, whose metric and stencils the
+    stretched-grid convergence test pins."""
+    P = ("periodic", "periodic")
+    c = wl.random_box(2, (12, 16, 1), bc=(P, ("wall", "wall"), P), visc="sutherland",
+                      stretch=("uniform", "tanh2", "uniform"), beta=(0.0, 1.9, 0.0),
+                      t_wall=((1.0, 1.0), (1.1, 0.9), (1.0, 1.0)))
+    case, grid, U = padded_state(c, seed=11, amp=0.3)
+    Uf = U.copy()
+    nf.fill_halos(Uf, case, grid)
+    W, T = nf.cons_to_prim(Uf, case)
+    F = nf.viscous_face_flux(W, T, case, grid, 1)         # faces a + 1/2, a = 2 .. 18
+    for side, row in ((0, 0), (1, -1)):
+        qw, tw = nf.wall_fluxes(U, case, grid, 1, side)
+        assert np.max(np.abs(qw[0, 0] + F[4][0, row, 3:15])) < 1e-13 * np.max(np.abs(qw))
+        assert np.max(np.abs(tw[0, 0] - F[1][0, row, 3:15])) < 1e-13 * np.max(np.abs(tw))
+
+
+def test_wall_heat_loss_weights_by_cell_width():
+    """J = sum_i q_w,i dx_i: with a wall-normal temperature gradient g(x) that varies along a
+    stretched wall, J is -lambda(T_w) times the width-weighted sum of g over the wall cells."""
+    c = wl.random_box(2, (10, 12, 1), bc=(("zero_gradient", "zero_gradient"), ("wall", "wall"),
+                                           ("periodic", "periodic")),
+                      visc="constant", mu_ref=0.05, t_wall=((1.0, 1.0), (1.0, 1.0), (1.0, 1.0)),
+                      lo=(0.0, 0.0, 0.0), hi=(3.0, 1.0, 1.0), stretch=("tanh1", "uniform", "uniform"),
+                      beta=(2.0, 0.0, 0.0))
+    case = nf.Case(c)
+    grid = nf.Grid(case)
+    xc = grid.axes[0].xc[3:13]
+    yc = grid.axes[1].xc[3:15]
+    y2, x2 = np.meshgrid(yc, xc, indexing="ij")
+    g = 0.3 + 0.2 * np.sin(x2)
+    T = 1.0 + g * y2
+    p = np.full_like(T, 1.1)
+    W = np.stack([p / (case.R * T), 0 * T, 0 * T, 0 * T, p])[:, None]
+    case, grid, U = padded_state(c, prims=W)
+    lam = 0.05 * case.cp / case.Pr
+    gw = 0.3 + 0.2 * np.sin(xc)
+    J = nf.wall_heat_loss(U, case, grid, 1, 0)
+    assert J == pytest.approx(-lam * np.sum(gw * grid.axes[0].dx[3:13]), rel=1e-12)
+    assert abs(np.sum(gw * grid.axes[0].dx[3:13]) - np.mean(gw) * 3.0) > 1e-3   # weights matter
