@@ -57,7 +57,10 @@ enum {
   FLUID_BC_WALL = 2,          /* isothermal no-slip: mirrored velocity, T_ghost = 2 T_w - T, same p */
   FLUID_BC_ADIABATIC = 3,     /* adiabatic no-slip: mirrored velocity, same rho and p */
   FLUID_BC_POROUS = 4,        /* isothermal no-slip with wall-normal transpiration v_w,i (below) */
-  FLUID_BC_INFLOW = 5         /* Dirichlet: fixed primitive profile (fluid_set_inflow) */
+  FLUID_BC_INFLOW = 5,        /* Dirichlet: fixed primitive profile (fluid_set_inflow) */
+  FLUID_BC_EXCHANGE = 6       /* sub-domain face of a block decomposition (Section 2.2): the three
+                                 halo layers of U hold the neighbouring sub-domain's cells, written
+                                 by fluid_unpack_halo, and are read as they are */
 };
 /* grid mapping per axis: face coordinate x(eta), eta = index / n */
 enum {
@@ -121,6 +124,13 @@ typedef struct fluid_config {
   int32_t adjoint;          /* nonzero: also allocate the scratch of the adjoint entry points */
   int32_t visc_order;       /* central differences of the dissipative fluxes: 4 (or 0), or 6 as in
                                the paper's channel computation (FP64 path only, no adjoint) */
+  /* Placement of this solve as one block of a decomposed global grid (Section 2.2 splits the
+   * domain into blocks, one per device).  global_n[a] == 0: axis a is not split (offset[a] == 0).
+   * Otherwise the grid mapping of axis a is that of global_n[a] cells on [lo[a], hi[a]], and this
+   * block holds its cells offset[a] .. offset[a] + n[a] - 1, so that its centres, widths and
+   * metrics are bitwise those of the global grid at the same cells. */
+  int32_t global_n[3];
+  int32_t offset[3];
 } fluid_config;
 
 typedef struct fluid_solver fluid_solver; /* opaque; owned by the library */
@@ -203,6 +213,49 @@ int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_d
  * NULL, dJ/dU on the whole padded array (zero except the two wall-adjacent cell layers). */
 int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int side, double* J_dev,
                          double* dJdU_dev, void* stream);
+
+/* ---- block decomposition (Section 2.2: the padded domain is split into blocks, one per device,
+ * and each right-hand side first exchanges N_h = 3 halo layers with the neighbouring blocks).  A
+ * sub-domain solver has FLUID_BC_EXCHANGE on the faces it shares with another block (and on both
+ * faces of a split periodic axis) and global_n / offset in its configuration.  Before every
+ * right-hand side (every RK3 stage) the caller refreshes the exchange halos of the stage's input
+ * state, axis by axis in the order x, y, z: fluid_pack_halo on both faces of the axis, hand each
+ * buffer to the neighbour across that face, fluid_unpack_halo of the received ones.  A buffer of
+ * axis a covers the three layers next to the face over the padded range of the axes below a and
+ * the interior range of the axes above a; halos filled by the earlier axes thus travel on, which
+ * gives the edge and corner cells of blocks that touch diagonally.  The time step is the minimum
+ * over blocks of fluid_compute_dt (one min-reduction), and fluid_rk3_stage advances each block. */
+
+/* Doubles in one packed halo buffer of axis a (either side): 5 * 3 * (product over the other
+ * axes b of p[b] for b < a, n[b] for b > a). */
+int fluid_halo_count(const fluid_solver* s, int axis, size_t* count);
+
+/* Copy the three interior cell layers of U next to face (axis, side) into buf (device,
+ * fluid_halo_count doubles, laid out [5][layer][t2][t1] with t1 < t2 the other axes, layers in
+ * increasing index order).  Side 0 packs layers h .. h+2, which become the halo of the neighbour
+ * below; side 1 packs n .. n+2, the halo of the neighbour above.  FLUID_EINVAL for a bad axis or
+ * pointer. */
+int fluid_pack_halo(fluid_solver* s, const double* U_dev, int axis, int side, double* buf_dev,
+                    void* stream);
+
+/* Write buf (as packed by the neighbour across face (axis, side): its side-1 buffer for side 0,
+ * its side-0 buffer for side 1) into the three halo layers of U at that face.  U's interior is
+ * not touched.  FLUID_EINVAL for a bad axis or pointer. */
+int fluid_unpack_halo(fluid_solver* s, double* U_dev, int axis, int side, const double* buf_dev,
+                      void* stream);
+
+/* One stage of the TVD-RK3 step of fluid_step with a given dt > 0:
+ *   stage 1: Ud = Un + dt R(Un) (pass Us = Un);  stage 2: Ud = 3/4 Un + 1/4 (Us + dt R(Us));
+ *   stage 3: Ud = 1/3 Un + 2/3 (Us + dt R(Us)).
+ * R(Us) reads the halo cells of Us on FLUID_BC_EXCHANGE faces as they are (refresh them first)
+ * and builds every other halo from the interior, exactly as fluid_rhs.  Only interior cells of Ud
+ * are written; Ud may be the same buffer as Us or Un (the combination is per cell).  The solver
+ * time is not advanced.  With the dt of fluid_step, three calls give bitwise fluid_step's
+ * result.  This is the way sub-domain solvers advance: fluid_step, fluid_step_stages, the adjoint
+ * entry points and fluid_wall_heat_loss return FLUID_EINVAL for a configuration with exchange
+ * faces. */
+int fluid_rk3_stage(fluid_solver* s, int stage, const double* Un_dev, const double* Us_dev,
+                    double* Ud_dev, double dt, void* stream);
 
 /* Synchronise `stream` and read the solver time and the last step's dt (either may be NULL). */
 int fluid_get_time(fluid_solver* s, double* t, double* last_dt, void* stream);
@@ -287,15 +340,19 @@ int fluid_check_pow(const double* x_dev, double* fast_dev, double* lib_dev, int 
  *
  * All scratch (primitives, velocity gradients, grid metrics, flags) lives in one fixed file-scope
  * device array of 2^21 doubles (16 MiB), reserved on every GPU the process uses until it exits.
- * A grid fits when about 15 doubles per padded cell plus its metrics fit, e.g. up to 44^3 interior
- * cells in 3-D or 256^2 in 2-D; larger grids return FLUID_EINVAL with a message saying so.  The
+ * A grid fits when its scratch fits: 15 doubles per padded cell with viscosity (6 without) plus
+ * its metrics, i.e. cubes up to 45^3 interior cells viscous / 64^3 inviscid in 3-D, squares up to
+ * 367^2 / 584^2 in 2-D; larger grids return FLUID_EINVAL with a message giving the need.  The
  * caller passes the input U and the output R exactly as for fluid_rhs (same layout, R interior
  * written, halos untouched).  Porous faces use phi_i = phi0; inflow faces return FLUID_ENOTSUP
  * (they need fluid_set_inflow); it computes in FP64 only (FLUID_PREC_MIXED returns
- * FLUID_ENOTSUP).  Non-finite / ghost-temperature flags are not reported.
+ * FLUID_ENOTSUP), and blocks of a decomposed grid (exchange faces, global_n) return
+ * FLUID_ENOTSUP.  Non-finite / ghost-temperature flags are not reported.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  Every call shares the one array and
+ * caches it; make that first call before any stream capture.  The cached address belongs to the
+ * device's primary context: after cudaDeviceReset, do not call this entry point again in the
+ * process on that device.  Every call shares the one array and
  * it keeps the last call's contents: calls whose work overlaps on the GPU (different streams or
  * host threads without ordering) race and give wrong results.  Nothing is allocated on the device
  * or the host; errbuf (may be NULL) receives a message of at most errlen - 1 characters. */

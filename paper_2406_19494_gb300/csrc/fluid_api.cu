@@ -27,6 +27,7 @@ struct fluid_solver {
   double* W = nullptr;             // primitives, NW * ncell
   double* G = nullptr;             // velocity gradients, NG * ncell (viscous, FP64 path)
   bool mixed = false;              // FLUID_PREC_MIXED: FP32 fluxes, FP64 state
+  bool exchange = false;           // some face is FLUID_BC_EXCHANGE (a block of a decomposition)
   float* W32 = nullptr;            // FP32 (hi, lo) primitives, 2 NW * ncell (mixed)
   float* mf32 = nullptr;           // FP32 face metrics of the three axes (mixed)
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
@@ -119,15 +120,18 @@ void axis_map(int stretch, double beta, double lo, double hi, double eta, double
   }
 }
 
-// host metric arrays of one axis: xc, dx, 1/dx, mc, mf over the padded range
+// host metric arrays of one axis: xc, dx, 1/dx, mc, mf over the padded range.  A block of a
+// decomposed grid (global_n > 0) evaluates the global mapping at its global cell indices, so every
+// value is bitwise the global grid's at the same cell.
 void axis_metrics(const fluid_config& c, int a, int h, std::vector<double> out[5]) {
-  const int n = c.n[a];
-  const int p = n + 2 * h;
+  const int p = c.n[a] + 2 * h;
+  const int n = c.global_n[a] > 0 ? c.global_n[a] : c.n[a];
+  const int off = c.global_n[a] > 0 ? c.offset[a] : 0;
   for (int k = 0; k < 5; ++k) out[k].assign(p, 0.0);
   if (c.stretch[a] == FLUID_STRETCH_UNIFORM) {
     const double d = (c.hi[a] - c.lo[a]) / n;
     for (int i = 0; i < p; ++i) {
-      const double ai = (double)(i - h);
+      const double ai = (double)(i + off - h);
       out[0][i] = c.lo[a] + (ai + 0.5) * d;
       out[1][i] = d;
       out[2][i] = 1.0 / d;
@@ -139,9 +143,9 @@ void axis_metrics(const fluid_config& c, int a, int h, std::vector<double> out[5
   std::vector<double> xf(p + 1);
   double dd;
   for (int k = 0; k <= p; ++k)
-    axis_map(c.stretch[a], c.beta[a], c.lo[a], c.hi[a], (double)(k - h) / n, &xf[k], &dd);
+    axis_map(c.stretch[a], c.beta[a], c.lo[a], c.hi[a], (double)(k + off - h) / n, &xf[k], &dd);
   for (int i = 0; i < p; ++i) {
-    const double ai = (double)(i - h);
+    const double ai = (double)(i + off - h);
     double x, dc, df;
     out[1][i] = xf[i + 1] - xf[i];
     out[0][i] = 0.5 * (xf[i + 1] + xf[i]);
@@ -171,12 +175,22 @@ const char* validate(const fluid_config* c) {
     if (!act) continue;
     for (int s = 0; s < 2; ++s) {
       const int k = c->bc[a][s];
-      if (k < 0 || k > FLUID_BC_INFLOW) return "unknown boundary kind";
+      if (k < 0 || k > FLUID_BC_EXCHANGE) return "unknown boundary kind";
       if ((k == FLUID_BC_WALL || k == FLUID_BC_POROUS) && !(c->t_wall[a][s] > 0))
         return "isothermal walls need t_wall > 0";
     }
     if ((c->bc[a][0] == FLUID_BC_PERIODIC) != (c->bc[a][1] == FLUID_BC_PERIODIC))
       return "periodic boundaries must pair";
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (c->global_n[a] < 0) return "global_n must be >= 0";
+    if (c->global_n[a] == 0 && c->offset[a] != 0) return "offset needs global_n > 0 on its axis";
+    if (c->global_n[a] > 0) {
+      if (a >= c->ndim) return "inactive axes cannot be split (global_n must be 0)";
+      if (c->global_n[a] > (1 << 20)) return "global_n must be <= 2^20";
+      if (c->offset[a] < 0 || c->offset[a] + c->n[a] > c->global_n[a])
+        return "the block (offset, n) must lie inside the global grid";
+    }
   }
   if (cells >= (1LL << 31) / 9) return "grid too large for 32-bit cell indexing";
   if (!(c->gamma > 1.0) || !(c->gas_R > 0) || !(c->prandtl > 0)) return "need gamma > 1, R > 0, Pr > 0";
@@ -194,6 +208,10 @@ const char* validate(const fluid_config* c) {
     return "the adjoint covers WENO5 with fourth-order dissipative fluxes only";
   if (c->precision != FLUID_PREC_FP64 && c->precision != FLUID_PREC_MIXED) return "unknown precision";
   if (!(c->dt_fixed > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt_fixed > 0";
+  bool exch = false;
+  for (int a = 0; a < c->ndim; ++a)
+    for (int s = 0; s < 2; ++s) exch |= c->bc[a][s] == FLUID_BC_EXCHANGE;
+  if (exch && c->adjoint) return "the adjoint does not cover sub-domain (exchange) faces";
   int nporous = 0;
   for (int a = 0; a < c->ndim; ++a)
     for (int s = 0; s < 2; ++s) nporous += c->bc[a][s] == FLUID_BC_POROUS;
@@ -338,6 +356,16 @@ int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, doub
 
 int need_adjoint(fluid_solver* s) {
   if (!s->gW) return fail(s, FLUID_EINVAL, "create the solver with cfg.adjoint != 0");
+  return FLUID_OK;
+}
+
+// entry points that run several right-hand sides without returning to the caller cannot refresh
+// exchange halos in between
+int no_exchange(fluid_solver* s, const char* what) {
+  if (s->exchange)
+    return fail(s, FLUID_EINVAL, std::string(what) +
+                                     " cannot refresh exchange halos between stages: advance a "
+                                     "sub-domain solver with fluid_rk3_stage");
   return FLUID_OK;
 }
 
@@ -495,6 +523,8 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
         bc.inflow[a][sd] = s->inflow[a][sd];
       }
     }
+  for (int a = 0; a < c.ndim; ++a)
+    for (int sd = 0; sd < 2; ++sd) s->exchange |= c.bc[a][sd] == FLUID_BC_EXCHANGE;
   for (int a = 0; a < c.ndim; ++a)
     for (int sd = 0; sd < 2; ++sd)
       if (c.bc[a][sd] == FLUID_BC_POROUS) {
@@ -658,6 +688,7 @@ int fluid_compute_dt(fluid_solver* s, const double* U_dev, double* dt_dev, void*
 
 int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* stream) {
   if (!s) return FLUID_EINVAL;
+  if (int r = no_exchange(s, "fluid_step")) return r;
   if (int r = check_ptr(s, U_dev, "U_dev")) return r;
   if (nsteps < 0) return fail(s, FLUID_EINVAL, "nsteps < 0");
   cudaStream_t st = as_stream(stream);
@@ -687,6 +718,7 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
 
 int fluid_step_stages(fluid_solver* s, double* U_dev, double* U1_dev, double* U2_dev, void* stream) {
   if (!s) return FLUID_EINVAL;
+  if (int r = no_exchange(s, "fluid_step_stages")) return r;
   if (int r = check_ptr(s, U_dev, "U_dev")) return r;
   if (int r = check_ptr(s, U1_dev, "U1_dev")) return r;
   if (int r = check_ptr(s, U2_dev, "U2_dev")) return r;
@@ -762,6 +794,7 @@ int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_d
 int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int side, double* J_dev,
                          double* dJdU_dev, void* stream) {
   if (!s) return FLUID_EINVAL;
+  if (int r = no_exchange(s, "fluid_wall_heat_loss")) return r;
   if (int r = need_adjoint(s)) return r;
   if (int r = check_ptr(s, U_dev, "U_dev")) return r;
   if (int r = check_ptr(s, J_dev, "J_dev")) return r;
@@ -779,6 +812,51 @@ int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int sid
     FL_CUDA(s, cudaMemsetAsync(dJdU_dev, 0, fl::NV * (size_t)g.ncell * sizeof(double), st));
     FL_CUDA(s, fl::launch_wall_loss_grad(U_dev, s->gT2, dJdU_dev, g, s->ph, axis, side, st));
   }
+  return FLUID_OK;
+}
+
+int fluid_halo_count(const fluid_solver* s, int axis, size_t* count) {
+  if (!s || !count || axis < 0 || axis >= s->geo.ndim) return FLUID_EINVAL;
+  *count = fl::halo_count(s->geo, axis);
+  return FLUID_OK;
+}
+
+int fluid_pack_halo(fluid_solver* s, const double* U_dev, int axis, int side, double* buf_dev,
+                    void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (axis < 0 || axis >= s->geo.ndim || side < 0 || side > 1) return fail(s, FLUID_EINVAL, "bad face");
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, buf_dev, "buf_dev")) return r;
+  FL_CUDA(s, fl::launch_halo_copy(const_cast<double*>(U_dev), buf_dev, s->geo, axis, side, false,
+                                  as_stream(stream)));
+  return FLUID_OK;
+}
+
+int fluid_unpack_halo(fluid_solver* s, double* U_dev, int axis, int side, const double* buf_dev,
+                      void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (axis < 0 || axis >= s->geo.ndim || side < 0 || side > 1) return fail(s, FLUID_EINVAL, "bad face");
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (int r = check_ptr(s, buf_dev, "buf_dev")) return r;
+  FL_CUDA(s, fl::launch_halo_copy(U_dev, const_cast<double*>(buf_dev), s->geo, axis, side, true,
+                                  as_stream(stream)));
+  return FLUID_OK;
+}
+
+int fluid_rk3_stage(fluid_solver* s, int stage, const double* Un_dev, const double* Us_dev,
+                    double* Ud_dev, double dt, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (stage < 1 || stage > 3) return fail(s, FLUID_EINVAL, "stage must be 1, 2 or 3");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(s, FLUID_EINVAL, "dt must be finite and > 0");
+  if (int r = check_ptr(s, Un_dev, "Un_dev")) return r;
+  if (int r = check_ptr(s, Us_dev, "Us_dev")) return r;
+  if (int r = check_ptr(s, Ud_dev, "Ud_dev")) return r;
+  if (stage == 1 && Us_dev != Un_dev) return fail(s, FLUID_EINVAL, "stage 1 needs Us == Un");
+  cudaStream_t st = as_stream(stream);
+  if (int r = rhs_into(s, Us_dev, s->R, st)) return r;
+  FL_TIMED(s, FLUID_KERNEL_STAGE, st,
+           fl::launch_stage(stage, Un_dev, Us_dev, s->R, Ud_dev, s->W, s->geo, s->ph, s->ctl, 0.0,
+                            st, dt));
   return FLUID_OK;
 }
 

@@ -191,6 +191,12 @@ cudaError_t launch_lincomb(double* out, double c0, const double* x0, double c1, 
 
 cudaError_t launch_prim_to_cons(const double* W, double* U, int ncell, const Phys& ph,
                                 cudaStream_t st);
+// block decomposition: doubles of one packed halo buffer of axis A, and the copy between the three
+// layers next to face (A, side) and the buffer (unpack: buffer -> halo layers; else interior
+// layers -> buffer)
+size_t halo_count(const Geo& g, int A);
+cudaError_t launch_halo_copy(double* U, double* buf, const Geo& g, int A, int side, bool unpack,
+                             cudaStream_t st);
 cudaError_t launch_wall_velocity(const double* phi, double* vw, const double* xc, int p, int h,
                                  int begin, int count, double amp, double two_pi_kappa,
                                  cudaStream_t st);

@@ -82,26 +82,32 @@ __device__ __forceinline__ void inflow_at(const double* __restrict__ prof, int a
 // the conversion twice.
 // Source cell of padded cell own[]: ghost[a] / side[a] / src[a] per axis; returns whether any axis
 // is a halo axis (then src[] is the interior cell the halo maps start from).
+// The halo layers of an exchange face (a sub-domain boundary of a block decomposition) hold the
+// neighbouring block's cells: along that axis the cell is its own source, like an interior cell.
 __device__ __forceinline__ bool halo_source(const int own[3], const Geo& g, const BC& bc,
                                             bool ghost[3], int side[3], int src[3]) {
   bool any = false;
   for (int a = 0; a < 3; ++a) {
-    ghost[a] = own[a] < g.h[a] || own[a] >= g.h[a] + g.n[a];
     side[a] = own[a] < g.h[a] ? 0 : 1;
+    ghost[a] = (own[a] < g.h[a] || own[a] >= g.h[a] + g.n[a]) &&
+               bc.kind[a][side[a]] != FLUID_BC_EXCHANGE;
     src[a] = ghost[a] ? bc_source(bc.kind[a][side[a]], side[a], own[a], g.n[a], g.h[a]) : own[a];
     any |= ghost[a];
   }
   return any;
 }
 
-// the maps of the halo axes of a cell, in axis order, applied to the primitives w of its source
-__device__ __forceinline__ void halo_maps(const int own[3], const bool ghost[3], const int side[3],
+// the maps of the halo axes of a cell, in axis order, applied to the primitives w of its source;
+// returns whether any of them changes values (a wall or inflow map) rather than only indices
+__device__ __forceinline__ bool halo_maps(const int own[3], const bool ghost[3], const int side[3],
                                           const int src[3], const Geo& g, const Phys& ph,
                                           const BC& bc, Ctl* ctl, double w[NW]) {
+  bool valued = false;
   for (int a = 0; a < 3; ++a) {
     if (!ghost[a]) continue;
     const int kind = bc.kind[a][side[a]];
     if (kind == FLUID_BC_PERIODIC || kind == FLUID_BC_ZERO_GRADIENT) continue;
+    valued = true;
     int c[3];
     for (int b = 0; b < 3; ++b) c[b] = b < a ? own[b] : src[b];
     if (kind == FLUID_BC_INFLOW) {
@@ -112,10 +118,12 @@ __device__ __forceinline__ void halo_maps(const int own[3], const bool ghost[3],
     if (kind == FLUID_BC_POROUS) vw = bc.vw[c[bc.porous_t1]];
     wall_map(w, kind, bc.Tw[a][side[a]], vw, a, ph, &ctl->flags);
   }
+  return valued;
 }
 
 // primitives of padded cell own[] (interior: from U; halo: composed boundary maps); E receives the
-// total energy per volume of interior cells (halo cells leave it unset).
+// total energy per volume of the source cell (the cell itself when interior) unless a wall or
+// inflow map changed the values, which the return value says (then E is left unset).
 //
 // The halo passes x -> y -> z compose: the pass of axis a sees own indices on the axes before it
 // and source indices on the axes after it, so a halo cell starts from the cell at the source index
@@ -131,12 +139,9 @@ __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const in
   const bool any = halo_source(own, g, bc, ghost, side, src);
   const int scell = any ? src[0] + src[1] * g.sy + src[2] * g.sz : cell;
   prim_of(U, scell, g.ncell, ph, w);
-  if (!any) {
-    E = U[4 * g.ncell + cell];
-    return false;
-  }
-  halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
-  return true;
+  E = U[4 * g.ncell + scell];
+  if (!any) return false;
+  return halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
 }
 
 // Split x = hi + lo + r with |r| <= 2^-48 |x|, using integer operations only: hi keeps the sign,
@@ -171,12 +176,15 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
       const int cell = i + j * g.sy + k * g.sz;
       double w[NW];
       double E = 0.0;
-      const bool halo = prim_cell(U, own, cell, g, ph, bc, ctl, w, E);
+      // H = E + p of a halo cell: the source cell's own value when only indices map (periodic,
+      // zero gradient, exchange), so that it equals the source's H bitwise; recomputed from the
+      // mapped primitives after a wall or inflow map
+      const bool valued = prim_cell(U, own, cell, g, ph, bc, ctl, w, E);
       for (int v = 0; v < NW; ++v) W[v * g.ncell + cell] = w[v];
       if (MIXED) {
         for (int v = 0; v < NW; ++v)
           split_hi_lo(w[v], W32[v * g.ncell + cell], W32[(NW + v) * g.ncell + cell]);
-        if (halo) E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        if (valued) E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
         W[NW * g.ncell + cell] = E + w[4];
       }
     }
@@ -602,14 +610,19 @@ __global__ void k_halo_prim(double* __restrict__ W, float* __restrict__ W32, Geo
     double w[NW];
 #pragma unroll
     for (int v = 0; v < NW; ++v) w[v] = W[v * nc + scell];
-    halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
+    const bool valued = halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
 #pragma unroll
     for (int v = 0; v < NW; ++v) W[v * nc + cell] = w[v];
     if (MIXED) {
 #pragma unroll
       for (int v = 0; v < NW; ++v) split_hi_lo(w[v], W32[v * nc + cell], W32[(NW + v) * nc + cell]);
-      const double E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
-      W[NW * nc + cell] = E + w[4];
+      // as k_prim_bc: index-only maps keep the source's H, value maps recompute it
+      if (valued) {
+        const double E = w[4] * ph.igm1 + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        W[NW * nc + cell] = E + w[4];
+      } else {
+        W[NW * nc + cell] = W[NW * nc + scell];
+      }
     }
   }
 }
@@ -676,6 +689,36 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_final(const double* __restrict_
       else if (ctl->t + dt > t_end) dt = t_end - ctl->t;
     }
     ctl->dt = dt;
+  }
+}
+
+// Halo exchange of a block decomposition: element t of the buffer [5][3][e2][e1] (t1 < t2 the axes
+// other than A; e_b = p_b below A, n_b above A, starting at 0 resp. h_b) and the padded cell it
+// maps to: layer l of face (A, side) is h + l / n + l (interior layers, packed) or l / h + n + l
+// (halo layers, unpacked).
+__global__ void k_halo_copy(double* __restrict__ U, double* __restrict__ buf, Geo g, int A,
+                            int side, int unpack, long long total) {
+  const int t1 = A == 0 ? 1 : 0, t2 = A == 2 ? 1 : 2;
+  const int e1 = t1 < A ? g.p[t1] : g.n[t1], o1 = t1 < A ? 0 : g.h[t1];
+  const int e2 = t2 < A ? g.p[t2] : g.n[t2], o2 = t2 < A ? 0 : g.h[t2];
+  const int h = g.h[A], n = g.n[A];
+  const int l0 = unpack ? (side == 0 ? 0 : h + n) : (side == 0 ? h : n);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    const int i1 = (int)(r % e1);
+    r /= e1;
+    const int i2 = (int)(r % e2);
+    r /= e2;
+    const int l = (int)(r % 3);
+    const int v = (int)(r / 3);
+    int c[3];
+    c[A] = l0 + l;
+    c[t1] = o1 + i1;
+    c[t2] = o2 + i2;
+    const long long cell = (long long)v * g.ncell + c[0] + (long long)c[1] * g.sy + (long long)c[2] * g.sz;
+    if (unpack) U[cell] = buf[t];
+    else buf[t] = U[cell];
   }
 }
 
@@ -849,6 +892,21 @@ cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, con
   if (total <= 0) return cudaSuccess;
   if (W32) (k_halo_prim<true><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total), ++t_launches);
   else (k_halo_prim<false><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total), ++t_launches);
+  return cudaGetLastError();
+}
+
+size_t halo_count(const Geo& g, int A) {
+  size_t cnt = 5 * 3;
+  for (int b = 0; b < 3; ++b)
+    if (b != A) cnt *= (size_t)(b < A ? g.p[b] : g.n[b]);
+  return cnt;
+}
+
+cudaError_t launch_halo_copy(double* U, double* buf, const Geo& g, int A, int side, bool unpack,
+                             cudaStream_t st) {
+  const long long total = (long long)halo_count(g, A);
+  (k_halo_copy<<<grid_for(total, 256), 256, 0, st>>>(U, buf, g, A, side, unpack ? 1 : 0, total),
+   ++t_launches);
   return cudaGetLastError();
 }
 

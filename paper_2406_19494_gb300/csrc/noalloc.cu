@@ -9,7 +9,9 @@
 // The scratch array below is reserved in every process that loads the library, on every GPU the
 // process uses, until the process exits.  Host code must not use its name as a device pointer
 // (in host code the symbol is only a host-side shadow); the device address is looked up once per
-// device with cudaGetSymbolAddress and cached.
+// device with cudaGetSymbolAddress and cached.  The cache belongs to the device's primary context:
+// after cudaDeviceReset the array has a new address, which the cache does not know, so a process
+// that resets a device must not call this entry point on it again.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -141,11 +143,21 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
     return FLUID_ENOTSUP;
   }
   for (int a = 0; a < c.ndim; ++a)
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 2; ++s) {
       if (c.bc[a][s] == FLUID_BC_INFLOW) {
         put_msg(errbuf, errlen, "inflow faces need a profile: use fluid_create/fluid_set_inflow");
         return FLUID_ENOTSUP;
       }
+      if (c.bc[a][s] == FLUID_BC_EXCHANGE) {
+        put_msg(errbuf, errlen, "sub-domain (exchange) faces need fluid_create");
+        return FLUID_ENOTSUP;
+      }
+    }
+  for (int a = 0; a < 3; ++a)
+    if (c.global_n[a] != 0) {
+      put_msg(errbuf, errlen, "blocks of a decomposed grid (global_n) need fluid_create");
+      return FLUID_ENOTSUP;
+    }
 
   fl::Geo g{};
   g.ndim = c.ndim;
@@ -180,9 +192,9 @@ extern "C" int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, d
   if (off > kScratchDoubles) {
     char msg[256];
     std::snprintf(msg, sizeof msg,
-                  "grid needs %zu scratch doubles, the fixed array holds %zu (16 MiB): about "
-                  "15 doubles per padded cell, e.g. at most 44^3 interior cells in 3-D",
-                  off, kScratchDoubles);
+                  "grid needs %zu scratch doubles (%d per padded cell for %zu padded cells, plus "
+                  "metrics), the fixed array holds %zu (16 MiB)",
+                  off, fl::NW + (visc ? fl::NG : 0), nc, kScratchDoubles);
     put_msg(errbuf, errlen, msg);
     return FLUID_EINVAL;
   }

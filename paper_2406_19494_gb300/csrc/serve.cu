@@ -342,6 +342,9 @@ int fluid_serve_submit(fluid_server* s, const fluid_request* req, uint64_t* tick
   if (!s || !req || !ticket || req->struct_size != sizeof(fluid_request)) return FLUID_EINVAL;
   if (!req->U0_host || req->nsteps < 0) return FLUID_EINVAL;
   if (fl::config_error(&req->cfg)) return FLUID_EINVAL;
+  for (int a = 0; a < req->cfg.ndim; ++a)
+    for (int sd = 0; sd < 2; ++sd)
+      if (req->cfg.bc[a][sd] == FLUID_BC_EXCHANGE) return FLUID_EINVAL;   // one solve, one block
   auto j = std::make_shared<Job>();
   j->cfg = req->cfg;
   j->nsteps = req->nsteps;

@@ -15,7 +15,8 @@ STATUS_NAMES = {0: "FLUID_OK", 1: "FLUID_EINVAL", 2: "FLUID_ENOMEM", 3: "FLUID_E
                 4: "FLUID_ENONFINITE", 5: "FLUID_ETIMEOUT", 6: "FLUID_EBUSY", 7: "FLUID_EBUDGET",
                 8: "FLUID_ENOTSUP"}
 
-BC = {"periodic": 0, "zero_gradient": 1, "wall": 2, "adiabatic": 3, "porous": 4, "inflow": 5}
+BC = {"periodic": 0, "zero_gradient": 1, "wall": 2, "adiabatic": 3, "porous": 4, "inflow": 5,
+      "exchange": 6}
 STRETCH = {"uniform": 0, "tanh2": 1, "tanh1": 2}
 VISC = {"none": 0, "constant": 1, "power": 2, "sutherland": 3}
 WENO = {"js": 0, "z": 1, "teno6a": 2}
@@ -40,6 +41,10 @@ SIGNATURES = {
     "fluid_adjoint_rhs": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fluid_adjoint_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fluid_wall_heat_loss": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "fluid_halo_count": (_i, [_vp, _i, ctypes.POINTER(_sz)]),
+    "fluid_pack_halo": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "fluid_unpack_halo": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "fluid_rk3_stage": (_i, [_vp, _i, _vp, _vp, _vp, _d, _vp]),
     "fluid_get_time": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
     "fluid_set_time": (_i, [_vp, _d, _vp]),
     "fluid_check": (_i, [_vp, _vp]),
@@ -98,6 +103,8 @@ class FluidConfig(ctypes.Structure):
         ("porous_phi0", ctypes.c_double),
         ("adjoint", ctypes.c_int32),
         ("visc_order", ctypes.c_int32),
+        ("global_n", ctypes.c_int32 * 3),
+        ("offset", ctypes.c_int32 * 3),
     ]
 
 
@@ -157,6 +164,9 @@ def config_from_case(case, precision="fp64", adjoint=False):
     c.precision = PRECISION[precision]
     c.adjoint = 1 if adjoint else 0
     c.visc_order = int(case.get("visc_order", 4))
+    for a in range(3):
+        c.global_n[a] = int(case.get("global_n", (0, 0, 0))[a])
+        c.offset[a] = int(case.get("offset", (0, 0, 0))[a])
     pz = case.get("porous", None)
     if pz:
         c.porous_axis, c.porous_side = int(pz["axis"]), int(pz["side"])

@@ -98,6 +98,36 @@ class Solver:
                                         _stream(stream)))
         return U
 
+    def rk3_stage(self, stage, Un, Us, Ud, dt, stream=None):
+        """One RK3 stage with the given dt (fluid_rk3_stage); Ud may be Us or Un."""
+        self._check(self.lib.fluid_rk3_stage(self.handle, int(stage), self._state(Un, "Un"),
+                                             self._state(Us, "Us"), self._state(Ud, "Ud"),
+                                             float(dt), _stream(stream)))
+        return Ud
+
+    def halo_count(self, axis):
+        n = ctypes.c_size_t()
+        self._check(self.lib.fluid_halo_count(self.handle, int(axis), ctypes.byref(n)))
+        return n.value
+
+    def pack_halo(self, U, axis, side, buf=None, stream=None):
+        """The three interior layers of U next to face (axis, side) packed into buf (fluid_pack_halo)."""
+        if buf is None:
+            buf = torch.empty(self.halo_count(axis), dtype=torch.float64, device=U.device)
+        elif buf.numel() != self.halo_count(axis):
+            raise ValueError("halo buffer of axis %d must hold %d doubles" % (axis, self.halo_count(axis)))
+        self._check(self.lib.fluid_pack_halo(self.handle, self._state(U), int(axis), int(side),
+                                             _ptr(buf), _stream(stream)))
+        return buf
+
+    def unpack_halo(self, U, axis, side, buf, stream=None):
+        """buf (a neighbour's packed layers) into the halo layers of U at face (axis, side)."""
+        if buf.numel() != self.halo_count(axis):
+            raise ValueError("halo buffer of axis %d must hold %d doubles" % (axis, self.halo_count(axis)))
+        self._check(self.lib.fluid_unpack_halo(self.handle, self._state(U), int(axis), int(side),
+                                               _ptr(buf), _stream(stream)))
+        return U
+
     def step_stages(self, U, U1, U2, stream=None):
         self._check(self.lib.fluid_step_stages(self.handle, self._state(U), self._state(U1, "U1"),
                                                self._state(U2, "U2"), _stream(stream)))

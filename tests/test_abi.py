@@ -61,6 +61,13 @@ def _create(lib, cfg):
     (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
     (lambda c: c.n.__setitem__(0, (1 << 20) + 1), "3 <= n"),
     (lambda c: (c.n.__setitem__(0, 20000), c.n.__setitem__(1, 20000)), "32-bit"),
+    (lambda c: c.global_n.__setitem__(0, 4), "inside the global grid"),
+    (lambda c: (c.global_n.__setitem__(0, 20), c.offset.__setitem__(0, 13)), "inside the global grid"),
+    (lambda c: c.offset.__setitem__(1, 2), "offset needs global_n"),
+    (lambda c: c.global_n.__setitem__(2, 1), "inactive axes cannot be split"),
+    (lambda c: (c.bc[0].__setitem__(0, native.BC["exchange"]), c.bc[0].__setitem__(1, native.BC["exchange"]),
+                setattr(c, "adjoint", 1)), "exchange"),
+    (lambda c: c.bc[1].__setitem__(0, 7), "unknown boundary kind"),
 ])
 def test_invalid_configs_are_rejected_before_any_gpu_call(lib, mutate, needle):
     cfg = native.config_from_case(wl.random_box(2, (8, 8, 1)))
