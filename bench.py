@@ -8,8 +8,11 @@ FP64 state and arithmetic.  Synthetic: the textbook closed-form initial conditio
 
 Prints one JSON line.  `value` = interior cells x steps x ranks / (max over ranks of the summed
 CUDA-event time of the K timed steps); L2 is flushed before every timed step.  With N > 1 (launched
-by torch.distributed.run) every rank advances its own independent replica of the workload.
-`--impl reference` times the CPU oracle on a bounded sample of the same workload instead.
+by torch.distributed.run) the ranks share one solve: the workload's grid is extended N times along
+z and split into z-slabs of the workload's size, one per rank (weak scaling), with a halo exchange
+over NCCL before every RK3 stage and the time step minimised over the ranks (Section 2.2's block
+decomposition).  `--impl reference` times the CPU oracle on a bounded sample of the same workload
+instead.
 """
 import argparse
 import datetime
@@ -211,6 +214,106 @@ def one_call_ms(s, U, steps, flush, stream):
     return a.elapsed_time(b) / steps
 
 
+def slab_case(base, ws):
+    """The workload extended ws times along z (its z-periodic state repeats), to be split into ws
+    z-slabs of the workload's own size."""
+    n, lo, hi = base["n"], base["lo"], base["hi"]
+    return dict(base, n=(n[0], n[1], n[2] * ws), hi=(hi[0], hi[1], lo[2] + (hi[2] - lo[2]) * ws),
+                name=base["name"] + "_zslabs%d" % ws)
+
+
+def run_decomposed(args, ws, rank, local):
+    """N > 1: one solve split into z-slabs, one per rank, NCCL halo exchange per RK3 stage."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_19494_gb300 import build, decomp
+
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    base = WORKLOADS[args.workload]()
+    case = slab_case(base, ws)
+    blk = decomp.BlockSolver(case, (1, 1, ws), rank, decomp.TorchComm())
+    s = blk.solver
+    cen = [s.grid(a)[0][3:-3] for a in range(3)]
+    W = np.pad(initial_prims(case, cen), [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U0 = s.prim_to_cons(torch.from_numpy(W).cuda())
+    s.autotune_faces(U0)
+    ncell = base["n"][0] * base["n"][1] * base["n"][2]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    U = U0.clone()
+    clk = ClockSampler(local)
+    clk.__enter__()
+    blk.step(U, args.warmup)
+    s.check()
+    torch.cuda.synchronize()
+    dist.barrier()
+    s.profile(True)
+    s.profile_read(reset=True)
+    clk.mark_start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        blk.step(U, 1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk.mark_end()
+    clk.__exit__(None, None, None)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    s.check()
+    per_step = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(per_step), "cuda")
+    launches = sum(n for _, n in prof.values())
+    # end to end: the rank's slab from pinned host memory, one step, back to the host
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    Ue = torch.empty_like(U0)
+    e_ms = []
+    for k in range(4):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Ue.copy_(Uh, non_blocking=True)
+        blk.step(Ue, 1)
+        Uout.copy_(Ue, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e_ms.append(a.elapsed_time(b))
+    e2e_ms = max_over_ranks(sum(e_ms) / len(e_ms), "cuda")
+    face_ms = sum(v[0] for k, v in prof.items() if k.startswith("face_"))
+    face_calls = 3 * 3 * args.steps
+    t_face = face_ms / face_calls * 1e-3 if face_ms > 0 else None
+    peak64 = 152 * 2 * 2 * 2.07e9 / 1e12
+    achieved = accounting.cell_axis_flops(3, case["weno"], case["visc"]) * ncell / t_face / 1e12 if t_face else None
+    nbytes = Uh.numel() * 8
+    result = {
+        "metric": METRIC, "value": whole_job_rate(ncell, args.steps, ws, total_ms), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_median": statistics.median(per_step), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(describe(args.workload, base), grid=list(case["n"]),
+                       parallelism="z-slabs x%d: one %dx%dx%d slab per GPU, NCCL halo exchange (3 layers) "
+                                   "before every RK3 stage, dt min-reduced" % ((ws,) + tuple(base["n"]))),
+        "e2e": {"value": ncell * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_face (x, y, z) with its seam kernel, FP64", "achieved": achieved,
+                     "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64 if achieved else None,
+                     "traffic": None},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    dist.destroy_process_group()
+
+
 def run_fluid(args):
     import torch
     import torch.distributed as dist
@@ -221,7 +324,7 @@ def run_fluid(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return run_decomposed(args, ws, rank, local)
     build.build()
     case = WORKLOADS[args.workload]()
     s = Solver(case)
@@ -239,13 +342,8 @@ def run_fluid(args):
 
     # ---- timed region (FP64 path): K steps, barrier + synchronize on both sides ----------------
     U = U0.clone()
-    if ws > 1:
-        dist.barrier()
     total_ms, prof, clk = timed_steps(s, U, args.steps, args.warmup, flush, stream, clock_gpu=local)
     median_ms = statistics.median(timed_steps.last_per_step)
-    if ws > 1:
-        dist.barrier()
-    total_ms = max_over_ranks(total_ms, "cuda")
     launches = sum(n for _, n in prof.values())
 
     # ---- the mixed FP32-flux / FP64-state path on the same workload ------------------------------
@@ -321,14 +419,14 @@ def run_fluid(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "ms_per_step_median": median_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(describe(args.workload, case), parallelism="replicas x%d" % ws if ws > 1 else "1 GPU"),
+        "config": dict(describe(args.workload, case), parallelism="1 GPU"),
         "e2e": {"value": ncell * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_face (x, y, z) with its seam kernel, FP64", "achieved": achieved, "peak": peak64,
                      "unit": "TFLOP/s", "frac": achieved / peak64 if achieved else None,
                      "traffic": face_traffic(ncell),
-                     "traffic_note": "bytes per launch: ncu dram read+write of the benchmark workload's x, y, z face launches (mean), profiles/k_face_tgv128_traffic.md",
+                     "traffic_note": "bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of the x, y and z face launches of this workload (mean), null when the kernel sources changed since that capture",
                      "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); "
                                     "measured by the FMA probe as fp64_fma_probe_tflops",
                      "fp64_fma_probe_tflops": fp64_probe / 1e3 if fp64_probe else None,
@@ -358,12 +456,9 @@ def run_fluid(args):
         "pid_s": {"per_cell": total_ms * 1e-3 / args.steps / ncell,
                   "per_dof": total_ms * 1e-3 / args.steps / (5 * ncell)},
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, case, samples=1)
-    if rank == 0:
-        print(json.dumps(result), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    print(json.dumps(result), flush=True)
 
 
 def mixed_vs_fp64(s64, s32, U64, U32, case, steps):

@@ -1,6 +1,7 @@
-"""The multi-GPU mode of the benchmark is replicas only (one independent solve per rank, no
-data-path collective): the job time is the slowest rank's and the rate counts every rank's cells.
-Checked here with two gloo ranks on the CPU."""
+"""Host logic of the benchmark's multi-GPU mode: every rank advances one z-slab of a solve that is
+the workload extended N times along z (weak scaling), the job time is the slowest rank's and the
+rate counts every rank's cells.  Checked here with two gloo ranks on the CPU; the slabs' halo
+exchange itself is covered by test_decomposition_host.py (gloo) and test_gpu_decomposition.py."""
 import os
 import socket
 
@@ -30,7 +31,7 @@ def _rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_replicas_take_the_slowest_rank_and_count_all_cells():
+def test_two_ranks_take_the_slowest_rank_and_count_all_cells():
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
@@ -45,3 +46,15 @@ def test_one_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5, "cpu") == 12.5
     assert bench.whole_job_rate(100, 10, 1, 1000.0) == pytest.approx(1000.0)
+
+
+def test_slab_case_extends_the_workload_along_z():
+    import bench
+    from paper_2406_19494_gb300 import decomp
+    base = bench.WORKLOADS["tgv64"]()
+    c = bench.slab_case(base, 4)
+    assert c["n"] == (64, 64, 256) and c["hi"][2] == pytest.approx(4 * base["hi"][2])
+    for r in range(4):
+        lay = decomp.Layout(c, (1, 1, 4), r)
+        assert lay.n == [64, 64, 64] and lay.offset[2] == 64 * r
+        assert lay.local_case()["bc"][2] == ("exchange", "exchange")

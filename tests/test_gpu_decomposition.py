@@ -68,7 +68,7 @@ def _setup(name):
     from paper_2406_19494_gb300.solver import Solver
     make, splits, prec = CASES[name]
     c = make()
-    case, grid, U0 = padded_state(c, seed=5)
+    case, grid, U0 = _initial(c)
     extra = {}
     if c.get("porous"):
         extra["phi"] = wl.porous_phi(c, seed=1)
@@ -79,6 +79,19 @@ def _setup(name):
     glob = Solver(c, prec)
     _configure(glob, extra, None)
     return c, splits, prec, U0, glob, extra
+
+
+def _initial(c):
+    """Seeded random state; the boundary layer starts from its inflow profile (a random state of
+    order one is far from the Ma 6 gas and would mirror to negative wall ghost temperatures)."""
+    if c.get("porous"):
+        from oracle import ns_fv as nf
+        case = nf.Case(c)
+        grid = nf.Grid(case)
+        xc = grid.axes[0].xc[3:3 + case.n[0]]
+        yc = grid.axes[1].xc[3:3 + case.n[1]]
+        return padded_state(c, prims=wl.porous_bl_prims(c, xc, yc))
+    return padded_state(c, seed=5)
 
 
 def _configure(solver, extra, layout):
@@ -173,7 +186,7 @@ def _rank_main(rank, world, port, name, out_dir):
         from paper_2406_19494_gb300 import decomp
         make, splits, prec = CASES[name]
         c = make()
-        _, _, U0 = padded_state(c, seed=5)
+        _, _, U0 = _initial(c)
         b = decomp.BlockSolver(c, splits, rank, decomp.TorchComm(), prec)
         U = _block_state(b.layout, U0)
         b.step(U, 3)
