@@ -99,7 +99,9 @@ enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
  *   porous_*       porous strip on face (porous_axis, porous_side), which must have kind
  *                  FLUID_BC_POROUS: wall cells porous_begin .. porous_begin + porous_count - 1 along
  *                  the first other active axis carry v_w,i = (A / phi0) phi_i sin(2 pi kappa x_i)
- *                  (Section 3.2's disturbance v = A sin(2 pi kappa x) when phi_i = phi0)
+ *                  (Section 3.2's disturbance v = A sin(2 pi kappa x) when phi_i = phi0); where
+ *                  that axis has an exchange face the strip may extend into its 3 halo cells (the
+ *                  neighbouring block's wall cells, which the block's corner ghost cells need)
  *   adjoint        nonzero: allocate the adjoint scratch (about 92 doubles per padded cell) so
  *                  that the fluid_adjoint_* entry points and fluid_wall_heat_loss can be used
  */

@@ -222,7 +222,10 @@ const char* validate(const fluid_config* c) {
       return "porous_axis/porous_side must name the porous face";
     if (c->ndim < 2) return "a porous wall needs ndim >= 2";
     const int t1 = a == 0 ? 1 : 0;
-    if (c->porous_count < 1 || c->porous_begin < 0 || c->porous_begin + c->porous_count > c->n[t1])
+    // a block's strip may reach into its exchange halos along the wall (the neighbours' wall cells)
+    const int lo = c->bc[t1][0] == FLUID_BC_EXCHANGE ? -FLUID_HALO : 0;
+    const int hi = c->n[t1] + (c->bc[t1][1] == FLUID_BC_EXCHANGE ? FLUID_HALO : 0);
+    if (c->porous_count < 1 || c->porous_begin < lo || c->porous_begin + c->porous_count > hi)
       return "porous strip outside the wall";
     if (!(c->porous_phi0 != 0)) return "porous_phi0 must be nonzero";
   }

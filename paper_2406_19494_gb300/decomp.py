@@ -86,9 +86,10 @@ class Layout:
             if bc[A][side] != "porous":
                 c["porous"] = None                       # this block does not touch the wall
             else:
+                # the wall cells of the block and of its exchange halos along the wall: the corner
+                # ghost cells next to an exchange face mirror the neighbour's wall cells
                 t1 = 1 if A == 0 else 0
-                lo = max(int(pz["begin"]), self.offset[t1])
-                hi = min(int(pz["begin"]) + int(pz["count"]), self.offset[t1] + self.n[t1])
+                lo, hi = self._strip(t1, bc)
                 if hi <= lo:
                     bc[A][side] = "wall"                 # no porous cell here: v_w = 0 everywhere
                     c["porous"] = None
@@ -97,8 +98,19 @@ class Layout:
         c["bc"] = tuple(tuple(p) for p in bc)
         return c
 
+    def _strip(self, t1, bc):
+        """Global cell range [lo, hi) of the porous strip on this block's wall, its exchange halos
+        along the wall included."""
+        pz = self.case["porous"]
+        ext_lo = HALO if bc[t1][0] == "exchange" else 0
+        ext_hi = HALO if bc[t1][1] == "exchange" else 0
+        lo = max(int(pz["begin"]), self.offset[t1] - ext_lo)
+        hi = min(int(pz["begin"]) + int(pz["count"]), self.offset[t1] + self.n[t1] + ext_hi)
+        return lo, hi
+
     def phi_slice(self, phi):
-        """The block's part of the global porous parameters (None when it has no porous cell)."""
+        """The block's part of the global porous parameters (its strip, halos included; None when
+        it has no porous cell)."""
         pz = self.case.get("porous")
         loc = self.local_case().get("porous")
         if not pz or not loc:

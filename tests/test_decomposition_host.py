@@ -53,9 +53,11 @@ def test_porous_strip_and_inflow_are_cut_per_block():
     cases = [l.local_case() for l in lays]
     assert [lc["bc"][0] for lc in cases] == [("inflow", "exchange"), ("exchange", "exchange"),
                                              ("exchange", "zero_gradient")]
-    assert [(lc["porous"]["begin"], lc["porous"]["count"]) for lc in cases] == [(11, 1), (0, 12), (0, 1)]
+    # each block's strip covers its wall cells and the neighbours' wall cells in its exchange
+    # halos (3 on each exchange side): global cells 11..14, 11..24 and 21..24
+    assert [(lc["porous"]["begin"], lc["porous"]["count"]) for lc in cases] == [(11, 4), (-1, 14), (-3, 4)]
     phi = np.arange(14.0)
-    assert np.concatenate([l.phi_slice(phi) for l in lays]).tolist() == phi.tolist()
+    assert [l.phi_slice(phi).tolist() for l in lays] == [phi[0:4].tolist(), phi.tolist(), phi[10:14].tolist()]
     c2 = dict(c, porous=dict(c["porous"], begin=2, count=6))          # strip inside block 0 only
     l1 = decomp.Layout(c2, (3, 1, 1), 1)
     assert l1.local_case()["bc"][1] == ("wall", "zero_gradient") and l1.local_case()["porous"] is None
