@@ -2,8 +2,9 @@
 multiple-data over devices, each exchanging data with exactly one neighbour per permutation),
 emulated with two gloo ranks on the CPU.
 
-The library's multi-GPU mode is replicas only (no data-path collective); this test checks the
-decomposition itself on the oracle.  Two ranks hold z-slabs of a periodic Taylor-Green box.  At
+This test checks the decomposition on the oracle (the library's own blocks are checked in
+test_gpu_decomposition.py and test_decomposition_host.py).  Two ranks hold z-slabs of a periodic
+Taylor-Green box.  At
 every right-hand side a rank fills its x and y halos locally, then receives its z halos from the
 neighbouring rank: the three boundary layers over the whole x-y plane (halos included), which is
 what the single-domain z pass reads.  The time step is the minimum over ranks of the local CFL
