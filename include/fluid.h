@@ -364,22 +364,34 @@ int fluid_rhs_noalloc(const fluid_config* cfg, const double* U_dev, double* R_de
 /* ---- serving: continuous batching of many independent solves (a design sweep) -------------------
  * A server owns one GPU and a scheduler thread.  Requests are admitted first-fit in arrival order
  * as soon as their device footprint (fluid_serve_footprint) fits the HBM budget next to the solves
- * already running and a slot is free; each running solve keeps its state on the device, runs on
- * its own stream in chunks of steps replayed from a CUDA graph captured for it, and overlaps with
- * the others; finished solves are copied back and their memory admits waiting requests.  The
- * first solve of each grid shape times the face kernels' launch shapes (fluid_tune_faces) and the
- * shape is kept for the bucket.  Results do not depend on the mix: every solve computes exactly
- * what fluid_step computes alone. */
+ * already running and a slot is free; each running solve keeps its state on the device.  With
+ * cfg.batch, compatible solves join a bucket and advance together, chunk by chunk: every kernel of
+ * a chunk is one launch over all the bucket's solves (a table in device memory lists them; the
+ * launches' blocks walk every solve's own launch grid), the chunk is a CUDA graph captured once
+ * per bucket, and between chunks the table is rewritten as solves join (admission) and leave
+ * (retirement), so a request that arrives while others run waits at most one chunk.  Solves that
+ * cannot be batched run on their own stream in chunks replayed from a graph captured per solve, the
+ * first of each grid shape timing the face kernels' launch shapes.  Buckets and single solves
+ * overlap on the device; finished solves are copied back and their memory admits waiting
+ * requests.  Results do not depend on the mix: every solve computes exactly what fluid_step
+ * computes alone. */
 typedef struct fluid_server fluid_server;
 
 typedef struct fluid_serve_config {
   uint32_t struct_size;        /* sizeof(fluid_serve_config) */
   int32_t device;              /* CUDA device of the server */
-  int32_t max_active;          /* concurrently running solves (streams), >= 1 */
+  int32_t max_active;          /* concurrently running solves, >= 1 */
   int32_t chunk_steps;         /* RK3 steps per graph replay, >= 1 */
-  int32_t use_graphs;          /* capture a CUDA graph per solve */
-  int32_t autotune;            /* time launch shapes once per grid shape */
+  int32_t use_graphs;          /* capture CUDA graphs (per bucket, or per solve when not batched) */
+  int32_t autotune;            /* time launch shapes once per grid shape (solves that run alone) */
   uint64_t hbm_budget_bytes;   /* admission budget for all running solves */
+  int32_t batch;               /* nonzero: solves with WENO5 and fourth-order (or no) dissipative
+                                  stencils run batched -- one launch per kernel advances every
+                                  solve of a bucket (same precision, reconstruction and viscous
+                                  flag; any grid size, 2-D with 3-D), at most 64 per bucket, a
+                                  chunk of steps captured once per bucket as a CUDA graph.  Other
+                                  solves run alone on their own stream and graph */
+  int32_t pad;
 } fluid_serve_config;
 
 typedef struct fluid_request {

@@ -376,6 +376,35 @@ int no_exchange(fluid_solver* s, const char* what) {
 
 namespace fl {
 const char* config_error(const fluid_config* c) { return validate(c); }
+
+bool batch_slot_of(fluid_solver* s, double* U, double t_end, BatchSlot& out) {
+  if (!s || s->exchange || s->ph.weno == FLUID_TENO6A || s->ph.visc_order == 6) return false;
+  out = BatchSlot{};
+  out.g = s->geo;
+  out.ph = s->ph;
+  out.bc = s->bc;
+  out.U = U;
+  out.A = s->A;
+  out.R = s->R;
+  out.W = s->W;
+  out.G = s->G;
+  out.W32 = s->W32;
+  out.G32 = s->G32;
+  out.partial = s->partial;
+  out.nparts = s->ph.dt_fixed > 0.0 ? 0 : s->nparts;
+  out.ctl = s->ctl;
+  out.t_end = t_end;
+  for (int D = 0; D < 3; ++D) {
+    out.seg[D] = 1;
+    out.FB[D] = nullptr;
+    if (D >= s->geo.ndim || s->mixed) continue;
+    int block = 128, seg = s->face_seg_d[D], grid = 0;
+    face_shape(D, s->geo, block, seg, grid);
+    out.seg[D] = seg;
+    out.FB[D] = seam_buffer(D, s->geo, seg, SeamBuf{s->FB, s->fb_cap});
+  }
+  return true;
+}
 }  // namespace fl
 
 extern "C" {

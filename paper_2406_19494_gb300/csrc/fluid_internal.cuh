@@ -7,6 +7,8 @@
 #include "../../include/fluid.h"
 #include "fast_math.cuh"
 
+struct fluid_solver;
+
 namespace fl {
 
 constexpr int NV = 5;   // conservative variables (rho, rho u, rho v, rho w, E)
@@ -200,5 +202,75 @@ cudaError_t launch_halo_copy(double* U, double* buf, const Geo& g, int A, int si
 cudaError_t launch_wall_velocity(const double* phi, double* vw, const double* xc, int p, int h,
                                  int begin, int count, double amp, double two_pi_kappa,
                                  cudaStream_t st);
+
+// ---- batched launches of the serving loop ------------------------------------------------------
+// One launch advances every solve of a bucket: the kernel's blocks walk the "virtual blocks" of all
+// solves (each solve's own launch grid of that kernel, laid end to end), and every virtual block
+// runs the standalone kernel's body with the solve's data and its own block index and grid size,
+// so each solve computes exactly what its standalone launches compute.  Solves of any grid size
+// (and 2-D with 3-D) share a bucket; the grids of the launches are fixed, so a chunk of steps is
+// captured once per bucket in a CUDA graph and the table below, in device memory, is rewritten
+// between chunks as solves are admitted and retire.
+constexpr int kBatchMax = 64;   // solves per bucket
+enum BatchKernel {
+  BK_PRIM = 0, BK_DTP, BK_DTF, BK_GRAD, BK_FACE0, BK_FACE1, BK_FACE2, BK_SEAM0, BK_SEAM1, BK_SEAM2,
+  BK_STAGEP, BK_HALO, BK_STAGE, BK_COUNT
+};
+struct BatchSlot {
+  Geo g;
+  Phys ph;
+  BC bc;
+  double* U;          // state (advanced in place)
+  double* A;          // stage state
+  double* R;          // right-hand side
+  double* W;          // primitives (mixed: plus the H row)
+  double* G;          // FP64 gradients (FP64 viscous)
+  float* W32;         // FP32 split (mixed)
+  float* G32;         // FP32 gradients (mixed viscous)
+  double* FB[3];      // seam buffer per axis (null: none)
+  double* partial;    // CFL partial maxima
+  int nparts;         // their count (0 with a fixed dt)
+  Ctl* ctl;
+  double t_end;
+  int seg[3];         // FP64 face segment length per axis
+  int steps;          // steps of the current chunk; the solve idles at later steps
+  int vgrid[BK_COUNT][3];
+};
+struct BatchTable {
+  int nslots;
+  int pad;
+  long long prefix[BK_COUNT][kBatchMax + 1];   // virtual blocks before each solve, per kernel
+  BatchSlot slot[kBatchMax];
+};
+// the solve of virtual block vb of kernel k (binary search of the prefix)
+__device__ __forceinline__ int batch_slot(const BatchTable* __restrict__ t, int k, long long vb) {
+  int lo = 0, hi = t->nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t->prefix[k][mid] <= vb) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ uint3 batch_bid(const int vg[3], long long lb) {
+  uint3 b;
+  b.x = (unsigned)(lb % vg[0]);
+  b.y = (unsigned)((lb / vg[0]) % vg[1]);
+  b.z = (unsigned)(lb / ((long long)vg[0] * vg[1]));
+  return b;
+}
+// a solver's part of a batch (its geometry, physics, boundaries and scratch, state U, t_end); false
+// when its configuration has no batched kernels (TENO6-A, sixth-order stencils, exchange faces)
+bool batch_slot_of(fluid_solver* s, double* U, double t_end, BatchSlot& out);
+// fill slot.vgrid and the prefixes for the solves of t (their Geo, Phys, seg and FB set)
+void batch_plan(BatchTable& t, bool mixed);
+// enqueue the batched kernels of `chunk` RK3 steps (what fluid_step(U, chunk) does for every solve)
+cudaError_t launch_batch_chunk(const BatchTable* dev, int chunk, bool mixed, int weno, bool visc,
+                               cudaStream_t st);
+// the mixed path's batched gradient and CFL kernels, and its face kernels (kernels_mixed.cu)
+enum { BMX_GRAD = 0, BMX_DTP = 2 };
+cudaError_t launch_batch_mixed(const BatchTable* dev, int kind, int D, int step, cudaStream_t st);
+cudaError_t launch_batch_mixed_faces(const BatchTable* dev, int D, int step, int weno, bool visc,
+                                     cudaStream_t st);
 
 }  // namespace fl

@@ -26,6 +26,8 @@
 // scratch with the same padded layout.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "flux_math.cuh"
 #include "fluid_internal.cuh"
 
@@ -166,12 +168,13 @@ __device__ __forceinline__ void split_hi_lo(double x, float& hi, float& lo) {
 // MIXED: the primitives also go to W32 = [2 NW][ncell] floats as the split (hi, lo) above, and
 // H = E + p to the FP64 row W[NW]; the FP32 face kernels form their cell differences from the pairs.
 template <bool MIXED>
-__global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
-                          float* __restrict__ W32, Geo g, Phys ph, BC bc, Ctl* ctl) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void k_prim_bc_body(const double* __restrict__ U, double* __restrict__ W,
+                          float* __restrict__ W32, Geo g, Phys ph, BC bc, Ctl* ctl,
+    uint3 bid, uint3 gdim) {
+  const int i = bid.x * blockDim.x + threadIdx.x;
   if (i >= g.p[0]) return;
-  for (int k = blockIdx.z; k < g.p[2]; k += gridDim.z)
-    for (int j = blockIdx.y; j < g.p[1]; j += gridDim.y) {
+  for (int k = bid.z; k < g.p[2]; k += gdim.z)
+    for (int j = bid.y; j < g.p[1]; j += gdim.y) {
       const int own[3] = {i, j, k};
       const int cell = i + j * g.sy + k * g.sz;
       double w[NW];
@@ -190,6 +193,12 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
     }
 }
 
+template <bool MIXED>
+__global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
+                          float* __restrict__ W32, Geo g, Phys ph, BC bc, Ctl* ctl) {
+  k_prim_bc_body<MIXED>(U, W, W32, g, ph, bc, ctl, blockIdx, gridDim);
+}
+
 // ------------------------------------------------------------------------------------------------
 // centre gradients G[c*3+b] = d u_c / d x_b, only where the cell is interior along b (the only
 // places the face fluxes read it), for the cells the face stencils reach along the other axes:
@@ -197,7 +206,8 @@ __global__ void k_prim_bc(const double* __restrict__ U, double* __restrict__ W,
 //   order 6: (45 (f[+1] - f[-1]) - 9 (f[+2] - f[-2]) + (f[+3] - f[-3])) * (mc / 60)
 // ------------------------------------------------------------------------------------------------
 template <int ORDER>
-__global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo g) {
+__device__ __forceinline__ void k_grad_body(const double* __restrict__ W, double* __restrict__ G, Geo g,
+    uint3 bid, uint3 gdim) {
   constexpr int M = ORDER / 2;
   int lo[3], ext[3];
   for (int a = 0; a < 3; ++a) {
@@ -206,7 +216,7 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
     ext[a] = g.n[a] + 2 * m;
   }
   const int total = ext[0] * ext[1] * ext[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = bid.x * blockDim.x + threadIdx.x; t < total; t += gdim.x * blockDim.x) {
     int c[3];
     c[0] = lo[0] + t % ext[0];
     const int r = t / ext[0];
@@ -222,15 +232,21 @@ __global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo
         double d = 0.0;
         if (inb) {
           const double* f = W + (1 + comp) * g.ncell + cell;
+          // explicit fused multiply-adds: every kernel inlining this rounds alike
           if (ORDER == 4)
-            d = ((f[-2 * s] - f[2 * s]) + 8.0 * (f[s] - f[-s])) * cm;
+            d = fma(8.0, f[s] - f[-s], f[-2 * s] - f[2 * s]) * cm;
           else
-            d = (45.0 * (f[s] - f[-s]) - 9.0 * (f[2 * s] - f[-2 * s]) + (f[3 * s] - f[-3 * s])) * cm;
+            d = fma(45.0, f[s] - f[-s], fma(-9.0, f[2 * s] - f[-2 * s], f[3 * s] - f[-3 * s])) * cm;
         }
         G[(comp * 3 + b) * g.ncell + cell] = d;
       }
     }
   }
+}
+
+template <int ORDER>
+__global__ void k_grad(const double* __restrict__ W, double* __restrict__ G, Geo g) {
+  k_grad_body<ORDER>(W, G, g, blockIdx, gridDim);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -318,10 +334,11 @@ __device__ __forceinline__ void update_r(double* dst, double F, double Fp, doubl
 // segment, which is the flux at that segment's a0-1/2.  Every face is then formed once; without FB
 // each segment forms the face before its first cell as well.  Both give the same bits.
 template <int D, int SCHEME, int VORD>
-__global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
+__device__ __forceinline__ void k_face_body(const double* __restrict__ W,
                                               const double* __restrict__ G, double* __restrict__ R,
                                               double* __restrict__ FB, Geo g, Phys ph,
-                                              int accumulate, int seg) {
+                                              int accumulate, int seg,
+    uint3 bid, uint3 gdim) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
@@ -330,8 +347,8 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
   const long long total = lines * nseg;
   const int s = D == 0 ? 1 : (D == 1 ? g.sy : g.sz);
   const int nc = g.ncell;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = bid.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gdim.x * blockDim.x) {
     const int i1 = (int)(t % n1);
     const long long r = t / n1;
     const int i2 = (int)(r % n2);
@@ -374,12 +391,21 @@ __global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
   }
 }
 
+template <int D, int SCHEME, int VORD>
+__global__ void __launch_bounds__(128) k_face(const double* __restrict__ W,
+                                              const double* __restrict__ G, double* __restrict__ R,
+                                              double* __restrict__ FB, Geo g, Phys ph,
+                                              int accumulate, int seg) {
+  k_face_body<D, SCHEME, VORD>(W, G, R, FB, g, ph, accumulate, seg, blockIdx, gridDim);
+}
+
 // The first cell a0 of every segment after the first: the same update as the face kernel that
 // filled FB, from the two fluxes its neighbouring segments left there (FUSED: the TENO kernel's
 // form, R = fma(-1/dx, F+ - F-, R))
 template <int D, bool FUSED>
-__global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ R, Geo g,
-                            int accumulate, int seg) {
+__device__ __forceinline__ void k_face_seam_body(const double* __restrict__ FB, double* __restrict__ R, Geo g,
+                            int accumulate, int seg,
+    uint3 bid, uint3 gdim) {
   constexpr int A1 = (D == 0) ? 1 : 0;
   constexpr int A2 = (D == 2) ? 1 : 2;
   const int n1 = g.n[A1], n2 = g.n[A2], nd = g.n[D];
@@ -387,8 +413,8 @@ __global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ 
   const long long lines = (long long)n1 * n2;
   const long long total = lines * nseg;
   const int nc = g.ncell;
-  for (long long t = lines + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = lines + bid.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gdim.x * blockDim.x) {
     const int i1 = (int)(t % n1);
     const long long r = t / n1;
     const int i2 = (int)(r % n2);
@@ -413,6 +439,12 @@ __global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ 
   }
 }
 
+template <int D, bool FUSED>
+__global__ void k_face_seam(const double* __restrict__ FB, double* __restrict__ R, Geo g,
+                            int accumulate, int seg) {
+  k_face_seam_body<D, FUSED>(FB, R, g, accumulate, seg, blockIdx, gridDim);
+}
+
 // ------------------------------------------------------------------------------------------------
 // source, stage combination, dt
 // ------------------------------------------------------------------------------------------------
@@ -433,16 +465,17 @@ __global__ void k_source(double* __restrict__ R, const double* __restrict__ W, G
     R[nc + c] += ph.f[0];
     R[2 * nc + c] += ph.f[1];
     R[3 * nc + c] += ph.f[2];
-    R[4 * nc + c] += ph.f[0] * u + ph.f[1] * v + ph.f[2] * w;
+    R[4 * nc + c] += fma(ph.f[0], u, fma(ph.f[1], v, ph.f[2] * w));
   }
 }
 
 // stage 1: Ud = Un + dt r; stage 2: Ud = 3/4 Un + 1/4 (Us + dt r); stage 3: Ud = 1/3 Un + 2/3 (Us + dt r)
-__global__ void k_stage(int stage, const double* Un, const double* Us, const double* __restrict__ R,
+__device__ __forceinline__ void k_stage_body(int stage, const double* Un, const double* Us, const double* __restrict__ R,
                         double* Ud, const double* __restrict__ W, Geo g, Phys ph, Ctl* ctl,
-                        double t_end, double dt_arg) {
+                        double t_end, double dt_arg,
+    uint3 bid, uint3 gdim) {
   const double dt = dt_arg > 0.0 ? dt_arg : ctl->dt;
-  if (stage == 3 && dt_arg <= 0.0 && blockIdx.x == 0 && threadIdx.x == 0 && dt > 0.0) {
+  if (stage == 3 && dt_arg <= 0.0 && bid.x == 0 && threadIdx.x == 0 && dt > 0.0) {
     const double tn = ctl->t + dt;
     ctl->t = (t_end > 0.0 && !(tn < t_end)) ? t_end : tn;
   }
@@ -450,7 +483,7 @@ __global__ void k_stage(int stage, const double* Un, const double* Us, const dou
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
   bool bad = false;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = bid.x * blockDim.x + threadIdx.x; t < total; t += gdim.x * blockDim.x) {
     const int c = interior_cell(t, g);
     double r[5];
 #pragma unroll
@@ -460,24 +493,30 @@ __global__ void k_stage(int stage, const double* Un, const double* Us, const dou
       r[1] += ph.f[0];
       r[2] += ph.f[1];
       r[3] += ph.f[2];
-      r[4] += ph.f[0] * u + ph.f[1] * v + ph.f[2] * w;
+      r[4] += fma(ph.f[0], u, fma(ph.f[1], v, ph.f[2] * w));
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double un = Un[v * nc + c];
       double out;
       if (stage == 1) {
-        out = un + dt * r[v];
+        out = fma(dt, r[v], un);
       } else {
         const double us = Us[v * nc + c];
-        out = stage == 2 ? 0.75 * un + 0.25 * (us + dt * r[v])
-                         : (1.0 / 3.0) * un + (2.0 / 3.0) * (us + dt * r[v]);
+        out = stage == 2 ? fma(0.75, un, 0.25 * fma(dt, r[v], us))
+                         : fma(1.0 / 3.0, un, (2.0 / 3.0) * fma(dt, r[v], us));
       }
       bad |= !finite_bits(out);
       Ud[v * nc + c] = out;
     }
   }
   if (bad) atomicOr(&ctl->flags, FLAG_NONFINITE);
+}
+
+__global__ void k_stage(int stage, const double* Un, const double* Us, const double* __restrict__ R,
+                        double* Ud, const double* __restrict__ W, Geo g, Phys ph, Ctl* ctl,
+                        double t_end, double dt_arg) {
+  k_stage_body(stage, Un, Us, R, Ud, W, g, ph, ctl, t_end, dt_arg, blockIdx, gridDim);
 }
 
 // One RK3 stage fused with the primitives of its result (the next right-hand side's first pass):
@@ -487,24 +526,25 @@ __global__ void k_stage(int stage, const double* Un, const double* Us, const dou
 // velocities of the stage's input state) and rewritten only at the thread's own cell.  A third
 // stage with dt <= 0 leaves Un unwritten and converts it as it is.
 template <bool MIXED>
-__global__ void k_stage_prim(int stage, const double* Un, const double* Us, const double* __restrict__ R,
+__device__ __forceinline__ void k_stage_prim_body(int stage, const double* Un, const double* Us, const double* __restrict__ R,
                              double* Ud, double* W, float* __restrict__ W32, Geo g, Phys ph, Ctl* ctl,
-                             double t_end) {
+                             double t_end,
+    uint3 bid, uint3 gdim) {
   const double dt = ctl->dt;
   const bool hold = stage == 3 && !(dt > 0.0);
-  if (stage == 3 && !hold && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+  if (stage == 3 && !hold && bid.x == 0 && bid.y == 0 && bid.z == 0 && threadIdx.x == 0) {
     const double tn = ctl->t + dt;
     ctl->t = (t_end > 0.0 && !(tn < t_end)) ? t_end : tn;
   }
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bid.x * blockDim.x + threadIdx.x;
   if (i >= g.n[0]) return;
   const int nc = g.ncell;
   // two cells per thread, rows j and j + J2, with every load of both issued before any store, so
   // that the two conversions' FP64 chains overlap
   const int J2 = (g.n[1] + 1) >> 1;
   bool bad = false;
-  for (int k = blockIdx.z; k < g.n[2]; k += gridDim.z)
-    for (int j = blockIdx.y; j < J2; j += gridDim.y) {
+  for (int k = bid.z; k < g.n[2]; k += gdim.z)
+    for (int j = bid.y; j < J2; j += gdim.y) {
       const int base = (i + g.h[0]) + (k + g.h[2]) * g.sz;
       const bool two = j + J2 < g.n[1];
       const int c[2] = {base + (j + g.h[1]) * g.sy, base + (j + J2 + g.h[1]) * g.sy};
@@ -540,16 +580,16 @@ __global__ void k_stage_prim(int stage, const double* Un, const double* Us, cons
             r[1] += ph.f[0];
             r[2] += ph.f[1];
             r[3] += ph.f[2];
-            r[4] += ph.f[0] * vel[q][0] + ph.f[1] * vel[q][1] + ph.f[2] * vel[q][2];
+            r[4] += fma(ph.f[0], vel[q][0], fma(ph.f[1], vel[q][1], ph.f[2] * vel[q][2]));
           }
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             double out;
             if (stage == 1) {
-              out = un[q][v] + dt * r[v];
+              out = fma(dt, r[v], un[q][v]);
             } else {
-              out = stage == 2 ? 0.75 * un[q][v] + 0.25 * (us[q][v] + dt * r[v])
-                               : (1.0 / 3.0) * un[q][v] + (2.0 / 3.0) * (us[q][v] + dt * r[v]);
+              out = stage == 2 ? fma(0.75, un[q][v], 0.25 * fma(dt, r[v], us[q][v]))
+                               : fma(1.0 / 3.0, un[q][v], (2.0 / 3.0) * fma(dt, r[v], us[q][v]));
             }
             bad |= !finite_bits(out);
             Ud[v * nc + c[q]] = out;
@@ -570,15 +610,23 @@ __global__ void k_stage_prim(int stage, const double* Un, const double* Us, cons
   if (bad) atomicOr(&ctl->flags, FLAG_NONFINITE);
 }
 
+template <bool MIXED>
+__global__ void k_stage_prim(int stage, const double* Un, const double* Us, const double* __restrict__ R,
+                             double* Ud, double* W, float* __restrict__ W32, Geo g, Phys ph, Ctl* ctl,
+                             double t_end) {
+  k_stage_prim_body<MIXED>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end, blockIdx, gridDim);
+}
+
 // Halo cells only, from the interior primitives already in W: the maps of k_prim_bc applied to the
 // source cell's primitives.  Cells are enumerated by their highest halo axis a: axes above a
 // interior, axis a one of its 2 h[a] halo layers, axes below a anywhere in the padded range.
 template <bool MIXED>
-__global__ void k_halo_prim(double* __restrict__ W, float* __restrict__ W32, Geo g, Phys ph, BC bc,
-                            Ctl* ctl, long long total) {
+__device__ __forceinline__ void k_halo_prim_body(double* __restrict__ W, float* __restrict__ W32, Geo g, Phys ph, BC bc,
+                            Ctl* ctl, long long total,
+    uint3 bid, uint3 gdim) {
   const int nc = g.ncell;
-  for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < total;
-       t0 += (long long)gridDim.x * blockDim.x) {
+  for (long long t0 = bid.x * (long long)blockDim.x + threadIdx.x; t0 < total;
+       t0 += (long long)gdim.x * blockDim.x) {
     long long t = t0;
     int own[3] = {0, 0, 0};
     for (int a = 2; a >= 0; --a) {
@@ -627,17 +675,24 @@ __global__ void k_halo_prim(double* __restrict__ W, float* __restrict__ W32, Geo
   }
 }
 
+template <bool MIXED>
+__global__ void k_halo_prim(double* __restrict__ W, float* __restrict__ W32, Geo g, Phys ph, BC bc,
+                            Ctl* ctl, long long total) {
+  k_halo_prim_body<MIXED>(W, W32, g, ph, bc, ctl, total, blockIdx, gridDim);
+}
+
 constexpr int kDtBlock = 256;
 
 // CFL: dt = cfl * min over cells and axes of dx / (|u| + c) and dx^2 / (k nu), taken as
 // cfl / max of the rates (|u| + c) / dx and k nu / dx^2 so that a cell costs no division.
 // Per-block maxima of the rate go to `partial`.
-__global__ void __launch_bounds__(kDtBlock) k_dt_partial(const double* __restrict__ W, Geo g, Phys ph,
-                                                         double* __restrict__ partial) {
+__device__ __forceinline__ void k_dt_partial_body(const double* __restrict__ W, Geo g, Phys ph,
+                                                         double* __restrict__ partial,
+    uint3 bid, uint3 gdim) {
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
   double best = 0.0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = bid.x * blockDim.x + threadIdx.x; t < total; t += gdim.x * blockDim.x) {
     const int i = t % g.n[0];
     const int r = t / g.n[0];
     const int j = r % g.n[1];
@@ -662,15 +717,21 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial(const double* __restric
   if (threadIdx.x < 32) {
     best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, o));
-    if (threadIdx.x == 0) partial[blockIdx.x] = best;
+    if (threadIdx.x == 0) partial[bid.x] = best;
   }
+}
+
+__global__ void __launch_bounds__(kDtBlock) k_dt_partial(const double* __restrict__ W, Geo g, Phys ph,
+                                                         double* __restrict__ partial) {
+  k_dt_partial_body(W, g, ph, partial, blockIdx, gridDim);
 }
 
 // dt = cfl / max(partial rates) (or dt_fixed); clip_to_ctl: clip so that t does not pass t_end and
 // store in ctl->dt; otherwise write *dt_out.
-__global__ void __launch_bounds__(kDtBlock) k_dt_final(const double* __restrict__ partial, int nparts,
+__device__ __forceinline__ void k_dt_final_body(const double* __restrict__ partial, int nparts,
                                                        Phys ph, Ctl* ctl, double* dt_out, int clip,
-                                                       double t_end) {
+                                                       double t_end,
+    uint3 bid, uint3 gdim) {
   double best = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) best = fmax(best, partial[i]);
   __shared__ double sm[kDtBlock / 32];
@@ -690,6 +751,12 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_final(const double* __restrict_
     }
     ctl->dt = dt;
   }
+}
+
+__global__ void __launch_bounds__(kDtBlock) k_dt_final(const double* __restrict__ partial, int nparts,
+                                                       Phys ph, Ctl* ctl, double* dt_out, int clip,
+                                                       double t_end) {
+  k_dt_final_body(partial, nparts, ph, ctl, dt_out, clip, t_end, blockIdx, gridDim);
 }
 
 // Halo exchange of a block decomposition: element t of the buffer [5][3][e2][e1] (t1 < t2 the axes
@@ -776,7 +843,207 @@ cudaError_t launch_face_s(int D, const double* W, const double* G, double* R, co
   return launch_face_sv<SCHEME, 4>(D, W, G, R, g, ph, accumulate, block, seg, fb, st);
 }
 
+// ------------------------------------------------------------------------------------------------
+// batched kernels of the serving loop (see BatchTable): each block walks virtual blocks of all the
+// bucket's solves and runs the standalone body with the solve's data, block index and grid size
+// ------------------------------------------------------------------------------------------------
+#define FL_BATCH_LOOP(K)                                                        \
+  const long long total_ = t->prefix[K][t->nslots];                             \
+  for (long long vb = blockIdx.x; vb < total_; vb += gridDim.x) {                \
+    const int si_ = batch_slot(t, K, vb);                                       \
+    const BatchSlot& S = t->slot[si_];                                          \
+    const uint3 bid = batch_bid(S.vgrid[K], vb - t->prefix[K][si_]);            \
+    const uint3 gdim = make_uint3(S.vgrid[K][0], S.vgrid[K][1], S.vgrid[K][2]);
+#define FL_BATCH_END \
+    __syncthreads(); \
+  }
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) kb_prim(const BatchTable* __restrict__ t) {
+  FL_BATCH_LOOP(BK_PRIM)
+  if (S.steps > 0) k_prim_bc_body<MIXED>(S.U, S.W, S.W32, S.g, S.ph, S.bc, S.ctl, bid, gdim);
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(kDtBlock) kb_dtp(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_DTP)
+  if (step < S.steps) k_dt_partial_body(S.W, S.g, S.ph, S.partial, bid, gdim);
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(kDtBlock) kb_dtf(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_DTF)
+  if (step < S.steps) k_dt_final_body(S.partial, S.nparts, S.ph, S.ctl, nullptr, 1, S.t_end, bid, gdim);
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(256) kb_grad(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_GRAD)
+  if (step < S.steps) k_grad_body<4>(S.W, S.G, S.g, bid, gdim);
+  FL_BATCH_END
+}
+
+template <int D, int SCHEME, int VORD>
+__global__ void __launch_bounds__(128) kb_face(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_FACE0 + D)
+  if (step < S.steps)
+    k_face_body<D, SCHEME, VORD>(S.W, S.G, S.R, S.FB[D], S.g, S.ph, D > 0, S.seg[D], bid, gdim);
+  FL_BATCH_END
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) kb_seam(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_SEAM0 + D)
+  if (step < S.steps) k_face_seam_body<D, false>(S.FB[D], S.R, S.g, D > 0, S.seg[D], bid, gdim);
+  FL_BATCH_END
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) kb_stage_prim(const BatchTable* __restrict__ t, int stage, int step) {
+  FL_BATCH_LOOP(BK_STAGEP)
+  if (step < S.steps)
+    k_stage_prim_body<MIXED>(stage, S.U, stage == 1 ? S.U : S.A, S.R, stage == 3 ? S.U : S.A, S.W,
+                             S.W32, S.g, S.ph, S.ctl, S.t_end, bid, gdim);
+  FL_BATCH_END
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) kb_halo(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_HALO)
+  if (step < S.steps) {
+    const long long total = (long long)S.g.p[0] * S.g.p[1] * S.g.p[2] -
+                            (long long)S.g.n[0] * S.g.n[1] * S.g.n[2];
+    k_halo_prim_body<MIXED>(S.W, S.W32, S.g, S.ph, S.bc, S.ctl, total, bid, gdim);
+  }
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(256) kb_stage(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_STAGE)
+  if (step < S.steps) k_stage_body(3, S.U, S.A, S.R, S.U, S.W, S.g, S.ph, S.ctl, S.t_end, 0.0, bid, gdim);
+  FL_BATCH_END
+}
+
+// blocks of a batched launch: as many as fit the GPU at once (each walks virtual blocks)
+template <class K>
+int batch_grid(K kernel, int block, size_t smem = 0) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+template <int SCHEME, int VORD>
+cudaError_t launch_batch_faces(const BatchTable* dev, int step, cudaStream_t st) {
+  static const int g0 = batch_grid(kb_face<0, SCHEME, VORD>, 128);
+  static const int g1 = batch_grid(kb_face<1, SCHEME, VORD>, 128);
+  static const int g2 = batch_grid(kb_face<2, SCHEME, VORD>, 128);
+  static const int gs = batch_grid(kb_seam<0>, 256);
+  (kb_face<0, SCHEME, VORD><<<g0, 128, 0, st>>>(dev, step), ++t_launches);
+  (kb_seam<0><<<gs, 256, 0, st>>>(dev, step), ++t_launches);
+  (kb_face<1, SCHEME, VORD><<<g1, 128, 0, st>>>(dev, step), ++t_launches);
+  (kb_seam<1><<<gs, 256, 0, st>>>(dev, step), ++t_launches);
+  (kb_face<2, SCHEME, VORD><<<g2, 128, 0, st>>>(dev, step), ++t_launches);
+  (kb_seam<2><<<gs, 256, 0, st>>>(dev, step), ++t_launches);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+void batch_plan(BatchTable& t, bool mixed) {
+  auto ceil_div = [](long long a, long long b) { return (a + b - 1) / b; };
+  for (int k = 0; k < BK_COUNT; ++k) t.prefix[k][0] = 0;
+  for (int i = 0; i < t.nslots; ++i) {
+    BatchSlot& S = t.slot[i];
+    const Geo& g = S.g;
+    for (int k = 0; k < BK_COUNT; ++k) S.vgrid[k][0] = S.vgrid[k][1] = S.vgrid[k][2] = 1;
+    auto set = [&](int k, long long x, long long y = 1, long long z = 1) {
+      S.vgrid[k][0] = (int)x;
+      S.vgrid[k][1] = (int)y;
+      S.vgrid[k][2] = (int)z;
+    };
+    const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long npad = (long long)g.p[0] * g.p[1] * g.p[2];
+    set(BK_PRIM, ceil_div(g.p[0], 128), std::min(g.p[1], 65535), std::min(g.p[2], 65535));
+    set(BK_DTP, S.nparts > 0 ? S.nparts : 0);
+    set(BK_DTF, 1);
+    const bool visc = S.ph.visc != FLUID_VISC_NONE;
+    long long gt = 1;
+    for (int a = 0; a < 3; ++a) gt *= g.n[a] + (a < g.ndim ? 4 : 0);   // order-4 stencils, both paths
+    set(BK_GRAD, visc ? ceil_div(gt, 256) : 0);
+    for (int D = 0; D < 3; ++D) {
+      const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];
+      if (D >= g.ndim) {
+        set(BK_FACE0 + D, 0);
+        set(BK_SEAM0 + D, 0);
+        continue;
+      }
+      if (mixed) {
+        if (D == 0) set(BK_FACE0, ceil_div(g.n[0], 31), ceil_div(lines, 4));
+        else set(BK_FACE0 + D, ceil_div(g.n[0], 32), ceil_div(g.n[D], 15), g.n[D == 1 ? 2 : 1]);
+        set(BK_SEAM0 + D, 0);
+      } else {
+        const long long nseg = ceil_div(g.n[D], S.seg[D]);
+        set(BK_FACE0 + D, ceil_div(lines * nseg, 128));
+        set(BK_SEAM0 + D, S.FB[D] ? ceil_div(lines * (nseg - 1), 256) : 0);
+      }
+    }
+    set(BK_STAGEP, ceil_div(g.n[0], 128), std::min((g.n[1] + 1) / 2, 65535), std::min(g.n[2], 65535));
+    set(BK_HALO, ceil_div(npad - nint, 256));
+    set(BK_STAGE, ceil_div(nint, 256));
+    for (int k = 0; k < BK_COUNT; ++k)
+      t.prefix[k][i + 1] = t.prefix[k][i] + (long long)S.vgrid[k][0] * S.vgrid[k][1] * S.vgrid[k][2];
+  }
+}
+
+cudaError_t launch_batch_chunk(const BatchTable* dev, int chunk, bool mixed, int weno, bool visc,
+                               cudaStream_t st) {
+  static const int gp = batch_grid(kb_prim<false>, 128), gpm = batch_grid(kb_prim<true>, 128);
+  static const int gd = batch_grid(kb_dtp, kDtBlock), gf = batch_grid(kb_dtf, kDtBlock);
+  static const int gg = batch_grid(kb_grad, 256);
+  static const int gsp = batch_grid(kb_stage_prim<false>, 128), gspm = batch_grid(kb_stage_prim<true>, 128);
+  static const int gh = batch_grid(kb_halo<false>, 256), ghm = batch_grid(kb_halo<true>, 256);
+  static const int gs = batch_grid(kb_stage, 256);
+  cudaError_t e;
+  if (mixed) (kb_prim<true><<<gpm, 128, 0, st>>>(dev), ++t_launches);
+  else (kb_prim<false><<<gp, 128, 0, st>>>(dev), ++t_launches);
+  for (int k = 0; k < chunk; ++k) {
+    if (mixed) {
+      if ((e = launch_batch_mixed(dev, BMX_DTP, 0, k, st)) != cudaSuccess) return e;
+    } else {
+      (kb_dtp<<<gd, kDtBlock, 0, st>>>(dev, k), ++t_launches);
+    }
+    (kb_dtf<<<gf, kDtBlock, 0, st>>>(dev, k), ++t_launches);
+    for (int stage = 1; stage <= 3; ++stage) {
+      if (mixed) {
+        if (visc && (e = launch_batch_mixed(dev, BMX_GRAD, 0, k, st)) != cudaSuccess) return e;
+        for (int D = 0; D < 3; ++D)
+          if ((e = launch_batch_mixed_faces(dev, D, k, weno, visc, st)) != cudaSuccess) return e;
+      } else {
+        if (visc) (kb_grad<<<gg, 256, 0, st>>>(dev, k), ++t_launches);
+        if (weno == FLUID_WENO_JS)
+          e = visc ? launch_batch_faces<FLUID_WENO_JS, 4>(dev, k, st) : launch_batch_faces<FLUID_WENO_JS, 0>(dev, k, st);
+        else
+          e = visc ? launch_batch_faces<FLUID_WENO_Z, 4>(dev, k, st) : launch_batch_faces<FLUID_WENO_Z, 0>(dev, k, st);
+        if (e != cudaSuccess) return e;
+      }
+      if (stage < 3 || k + 1 < chunk) {
+        if (mixed) {
+          (kb_stage_prim<true><<<gspm, 128, 0, st>>>(dev, stage, k), ++t_launches);
+          (kb_halo<true><<<ghm, 256, 0, st>>>(dev, k), ++t_launches);
+        } else {
+          (kb_stage_prim<false><<<gsp, 128, 0, st>>>(dev, stage, k), ++t_launches);
+          (kb_halo<false><<<gh, 256, 0, st>>>(dev, k), ++t_launches);
+        }
+      } else {
+        (kb_stage<<<gs, 256, 0, st>>>(dev, k), ++t_launches);
+      }
+    }
+  }
+  return cudaGetLastError();
+}
 
 double* seam_buffer(int D, const Geo& g, int seg, SeamBuf fb) {
   const long long lines = (long long)g.n[D == 0 ? 1 : 0] * g.n[D == 2 ? 1 : 2];

@@ -62,7 +62,7 @@ struct PhysF {
   int visc;
 };
 
-PhysF phys_f(const Phys& ph) {
+__host__ __device__ inline PhysF phys_f(const Phys& ph) {
   PhysF f;
   f.gamma = (float)ph.gamma; f.gm1 = (float)ph.gm1; f.igm1 = (float)ph.igm1;
   f.gg = (float)(ph.gamma * ph.igm1);
@@ -346,18 +346,19 @@ constexpr int kXCells = 31;
 constexpr int kXRows = 4;
 
 template <int SCHEME, bool VISC>
-__global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(MixedIn in, double* __restrict__ R,
-                                                              Geo g, PhysF pf, int accumulate) {
+__device__ __forceinline__ void k_face_mixed_x_body(MixedIn in, double* __restrict__ R,
+                                                              Geo g, PhysF pf, int accumulate,
+    uint3 bid, uint3 gdim) {
   constexpr int NVW = VISC ? 6 : 5;
   constexpr int ND = kXCells + 5;               // D_j for j in [x0-3, x0+kXCells+1]
   __shared__ float sD[kXRows][6][ND];
   __shared__ double sF[kXRows][5][kXCells + 1];
   const int lane = threadIdx.x, row = threadIdx.y;
   const int n0 = g.n[0], h0 = g.h[0];
-  const int line = blockIdx.y * kXRows + row;
+  const int line = bid.y * kXRows + row;
   const bool live = line < g.n[1] * g.n[2];
   const int j1 = live ? line % g.n[1] : 0, j2 = live ? line / g.n[1] : 0;
-  const int x0 = h0 + blockIdx.x * kXCells;      // first interior cell of the tile (padded index)
+  const int x0 = h0 + bid.x * kXCells;      // first interior cell of the tile (padded index)
   const int nc = g.ncell;
   const int rowbase = (j1 + g.h[1]) * g.sy + (j2 + g.h[2]) * g.sz;
   const int xend = h0 + n0;                      // one past the last interior cell
@@ -393,6 +394,12 @@ __global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(MixedIn in, double
   }
 }
 
+template <int SCHEME, bool VISC>
+__global__ void __launch_bounds__(32 * kXRows) k_face_mixed_x(MixedIn in, double* __restrict__ R,
+                                                              Geo g, PhysF pf, int accumulate) {
+  k_face_mixed_x_body<SCHEME, VISC>(in, R, g, pf, accumulate, blockIdx, gridDim);
+}
+
 // y / z variant: lanes map to 32 consecutive x columns (coalesced loads); a block of NWARP warps
 // covers FPW NWARP - 1 cells along the face axis D (FPW NWARP faces) of those columns at one index
 // of the remaining axis.  The cell differences along D are staged in shared memory; warp w computes
@@ -406,8 +413,9 @@ constexpr size_t t_smem() {
 }
 
 template <int D, int SCHEME, bool VISC, int NWARP, int FPW>
-__global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn in, double* __restrict__ R,
-                                                                       Geo g, PhysF pf, int accumulate) {
+__device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restrict__ R,
+                                                                       Geo g, PhysF pf, int accumulate,
+    uint3 bid, uint3 gdim) {
   static_assert(D == 1 || D == 2, "tiles along y or z");
   constexpr int kTFaces = FPW;
   constexpr int kTCells = kTFaces * NWARP - 1;
@@ -420,11 +428,11 @@ __global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn
   double (*sF)[5][32] =
       reinterpret_cast<double (*)[5][32]>(smem_raw + sizeof(float) * 6 * ND * 32);      // [NWARP][5][32]
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x = g.h[0] + blockIdx.x * 32 + lane;
+  const int x = g.h[0] + bid.x * 32 + lane;
   const bool xok = x < g.h[0] + g.n[0];
-  const int d0 = g.h[D] + blockIdx.y * kTCells;             // first cell of the tile along D
+  const int d0 = g.h[D] + bid.y * kTCells;             // first cell of the tile along D
   const int dend = g.h[D] + g.n[D];
-  const int o = g.h[OTHER] + blockIdx.z;
+  const int o = g.h[OTHER] + bid.z;
   const int s = D == 1 ? g.sy : g.sz;
   const int so = OTHER == 1 ? g.sy : g.sz;
   const int nc = g.ncell;
@@ -469,9 +477,16 @@ __global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn
   }
 }
 
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW>
+__global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn in, double* __restrict__ R,
+                                                                       Geo g, PhysF pf, int accumulate) {
+  k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW>(in, R, g, pf, accumulate, blockIdx, gridDim);
+}
+
 
 // centre velocity gradients in FP32 from the FP32 primitives (fourth-order central)
-__global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
+__device__ __forceinline__ void k_grad32_body(const float* __restrict__ W32, float* __restrict__ G32, Geo g,
+    uint3 bid, uint3 gdim) {
   int lo[3], ext[3];
   for (int a = 0; a < 3; ++a) {
     const int m = a < g.ndim ? 2 : 0;
@@ -479,7 +494,7 @@ __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32,
     ext[a] = g.n[a] + 2 * m;
   }
   const int total = ext[0] * ext[1] * ext[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = bid.x * blockDim.x + threadIdx.x; t < total; t += gdim.x * blockDim.x) {
     int c[3];
     c[0] = lo[0] + t % ext[0];
     const int r = t / ext[0];
@@ -502,17 +517,22 @@ __global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32,
   }
 }
 
+__global__ void k_grad32(const float* __restrict__ W32, float* __restrict__ G32, Geo g) {
+  k_grad32_body(W32, G32, g, blockIdx, gridDim);
+}
+
 constexpr int kDtBlock = 256;
 
 // CFL partial maxima of the rates (|u| + c) / dx and k nu / dx^2 (the inverse time steps, as in
 // the FP64 kernel) from the FP32 primitives: the time step needs no more than FP32 accuracy
-__global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, PhysF pf,
-                                                           double* __restrict__ partial) {
+__device__ __forceinline__ void k_dt_partial32_body(const float* __restrict__ W32, Geo g, PhysF pf,
+                                                           double* __restrict__ partial,
+    uint3 bid, uint3 gdim) {
   const int total = g.n[0] * g.n[1] * g.n[2];
   const int nc = g.ncell;
   float best = 0.0f;
   const float gam = pf.gamma, k = pf.dt_visc_k;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (int t = bid.x * blockDim.x + threadIdx.x; t < total; t += gdim.x * blockDim.x) {
     const int i = t % g.n[0];
     const int r = t / g.n[0];
     const int j = r % g.n[1];
@@ -537,8 +557,90 @@ __global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restri
   if (threadIdx.x < 32) {
     best = threadIdx.x < kDtBlock / 32 ? sm[threadIdx.x] : 0.0f;
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
-    if (threadIdx.x == 0) partial[blockIdx.x] = (double)best;
+    if (threadIdx.x == 0) partial[bid.x] = (double)best;
   }
+}
+
+__global__ void __launch_bounds__(kDtBlock) k_dt_partial32(const float* __restrict__ W32, Geo g, PhysF pf,
+                                                           double* __restrict__ partial) {
+  k_dt_partial32_body(W32, g, pf, partial, blockIdx, gridDim);
+}
+
+// ---- batched kernels of the serving loop (see BatchTable in fluid_internal.cuh) -----------------
+#define FL_BATCH_LOOP(K)                                                        \
+  const long long total_ = t->prefix[K][t->nslots];                             \
+  for (long long vb = blockIdx.x; vb < total_; vb += gridDim.x) {                \
+    const int si_ = batch_slot(t, K, vb);                                       \
+    const BatchSlot& S = t->slot[si_];                                          \
+    const uint3 bid = batch_bid(S.vgrid[K], vb - t->prefix[K][si_]);            \
+    const uint3 gdim = make_uint3(S.vgrid[K][0], S.vgrid[K][1], S.vgrid[K][2]);
+#define FL_BATCH_END \
+    __syncthreads(); \
+  }
+
+__device__ __forceinline__ MixedIn batch_in(const BatchSlot& S) {
+  return MixedIn{S.W, S.W32, S.W32 + (size_t)NW * S.g.ncell, S.G32};
+}
+
+template <int SCHEME, bool VISC>
+__global__ void __launch_bounds__(32 * kXRows) kbm_face_x(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_FACE0)
+  if (step < S.steps) k_face_mixed_x_body<SCHEME, VISC>(batch_in(S), S.R, S.g, phys_f(S.ph), 0, bid, gdim);
+  FL_BATCH_END
+}
+
+template <int D, int SCHEME, bool VISC>
+__global__ void __launch_bounds__(128, 8) kbm_face_t(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_FACE0 + D)
+  if (step < S.steps)
+    k_face_mixed_t_body<D, SCHEME, VISC, 4, 4>(batch_in(S), S.R, S.g, phys_f(S.ph), 1, bid, gdim);
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(256) kbm_grad(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_GRAD)
+  if (step < S.steps) k_grad32_body(S.W32, S.G32, S.g, bid, gdim);
+  FL_BATCH_END
+}
+
+__global__ void __launch_bounds__(kDtBlock) kbm_dtp(const BatchTable* __restrict__ t, int step) {
+  FL_BATCH_LOOP(BK_DTP)
+  if (step < S.steps) k_dt_partial32_body(S.W32, S.g, phys_f(S.ph), S.partial, bid, gdim);
+  FL_BATCH_END
+}
+
+template <class K>
+int batch_grid_m(K kernel, int block, size_t smem = 0) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+template <int SCHEME, bool VISC>
+cudaError_t batch_face_m(const BatchTable* dev, int D, int step, cudaStream_t st) {
+  constexpr size_t smem = t_smem<4, 4>();
+  if (D == 0) {
+    static const int gx = batch_grid_m(kbm_face_x<SCHEME, VISC>, 32 * kXRows);
+    (kbm_face_x<SCHEME, VISC><<<gx, dim3(32, kXRows), 0, st>>>(dev, step), ++t_launches);
+    return cudaGetLastError();
+  }
+  static bool init = false;
+  static int g1 = 0, g2 = 0;
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(kbm_face_t<1, SCHEME, VISC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kbm_face_t<2, SCHEME, VISC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g1 = batch_grid_m(kbm_face_t<1, SCHEME, VISC>, 128, smem);
+    g2 = batch_grid_m(kbm_face_t<2, SCHEME, VISC>, 128, smem);
+    init = true;
+  }
+  if (D == 1) (kbm_face_t<1, SCHEME, VISC><<<g1, dim3(32, 4), smem, st>>>(dev, step), ++t_launches);
+  else (kbm_face_t<2, SCHEME, VISC><<<g2, dim3(32, 4), smem, st>>>(dev, step), ++t_launches);
+  return cudaGetLastError();
 }
 
 template <int D, int SCHEME, bool VISC>
@@ -613,6 +715,28 @@ cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const fl
                 : launch_sv<FLUID_WENO_JS, false>(D, in, R, g, pf, accumulate, block, seg, st);
   return visc ? launch_sv<FLUID_WENO_Z, true>(D, in, R, g, pf, accumulate, block, seg, st)
               : launch_sv<FLUID_WENO_Z, false>(D, in, R, g, pf, accumulate, block, seg, st);
+}
+
+cudaError_t launch_batch_mixed(const BatchTable* dev, int kind, int D, int step, cudaStream_t st) {
+  static const int gg = batch_grid_m(kbm_grad, 256);
+  static const int gd = batch_grid_m(kbm_dtp, kDtBlock);
+  if (kind == BMX_GRAD) {
+    (kbm_grad<<<gg, 256, 0, st>>>(dev, step), ++t_launches);
+    return cudaGetLastError();
+  }
+  if (kind == BMX_DTP) {
+    (kbm_dtp<<<gd, kDtBlock, 0, st>>>(dev, step), ++t_launches);
+    return cudaGetLastError();
+  }
+  // the bucket key fixes the scheme and the viscosity, read from the first solve on the host side
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_mixed_faces(const BatchTable* dev, int D, int step, int weno, bool visc,
+                                     cudaStream_t st) {
+  if (weno == FLUID_WENO_JS)
+    return visc ? batch_face_m<FLUID_WENO_JS, true>(dev, D, step, st) : batch_face_m<FLUID_WENO_JS, false>(dev, D, step, st);
+  return visc ? batch_face_m<FLUID_WENO_Z, true>(dev, D, step, st) : batch_face_m<FLUID_WENO_Z, false>(dev, D, step, st);
 }
 
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st) {

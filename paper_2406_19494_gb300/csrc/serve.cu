@@ -3,11 +3,20 @@
 // One scheduler thread owns the device.  Submitted requests wait in arrival order; a request is
 // admitted (first fit) as soon as its exact device footprint fits the HBM budget next to the
 // solves already running and a slot is free.  Every admitted solve keeps its state and solver
-// scratch on the device, runs on its own stream, and advances in chunks of steps replayed from a
-// CUDA graph captured once for the solve; the chunks of different solves overlap on the GPU.
-// When a solve finishes, its state is copied back, its memory released, and waiting requests are
-// admitted in its place.  The first solve of each grid shape ("bucket") times the face kernels'
-// launch shapes on a scratch copy of its state and the bucket keeps the fastest.
+// scratch on the device.
+//
+// Batched solves (WENO5 with fourth-order or no dissipative stencils, with cfg.batch) join the
+// bucket of their precision, reconstruction and viscous flag -- any grid size, 2-D with 3-D.  A
+// bucket advances chunk by chunk: every kernel of a chunk is one launch over all its solves (the
+// launches read a table of the solves in device memory and their blocks walk every solve's own
+// launch grid, see BatchTable), and the chunk is a CUDA graph captured once per bucket.  Between
+// chunks the scheduler rewrites the table: solves admitted meanwhile join, finished ones leave
+// (their state is copied back and their memory released).  Each solve runs as many steps of a
+// chunk as it has left and idles for the rest.
+//
+// Other solves run alone: their own stream, chunks replayed from a graph captured once per solve,
+// and the first solve of each grid shape times the face kernels' launch shapes on a scratch copy of
+// its state (the shape is kept for that shape).  Buckets and single solves overlap on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,6 +62,31 @@ struct Slot {
   int graph_steps = 0;
   int steps_done = 0;
   bool copying_out = false;
+};
+
+// a solve of a bucket
+struct BSlot {
+  std::shared_ptr<Job> job;
+  fluid_solver* solver = nullptr;
+  double* U = nullptr;
+  cudaEvent_t ev_out = nullptr;   // its copy-out, once it has finished
+  int steps_done = 0;
+  int chunk_steps = 0;            // steps of the chunk in flight
+  bool leaving = false;
+};
+
+// solves advanced together by batched launches
+struct Bucket {
+  int mixed = 0, weno = 0, visc = 0;
+  std::vector<BSlot> slots;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;                 // end of the chunk in flight
+  fl::BatchTable* host = nullptr;           // pinned
+  fl::BatchTable* dev = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_chunk = 0;
+  bool busy = false;
+  bool broken = false;                      // set-up failed: no new solves join
 };
 
 struct BucketKey {
@@ -101,8 +135,9 @@ struct fluid_server {
   std::condition_variable cv_done, cv_work;
   std::deque<std::shared_ptr<Job>> pending;
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
-  std::vector<Slot> active;                 // owned by the scheduler thread only
-  std::atomic<int64_t> n_active{0};         // its size, for other threads
+  std::vector<Slot> active;                 // solves running alone (scheduler thread only)
+  std::vector<std::unique_ptr<Bucket>> buckets;   // batched solves (scheduler thread only)
+  std::atomic<int64_t> n_active{0};         // running solves, for other threads
   std::map<BucketKey, std::pair<int, int>> tuned;   // bucket -> (block, seg)
   uint64_t next_ticket = 1;
   size_t used = 0, peak = 0;
@@ -114,16 +149,187 @@ struct fluid_server {
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
-  void finish(Slot& s, int status) {
+  void finish(Job& job, int steps_done, int status) {
     std::lock_guard<std::mutex> lk(mu);
-    s.job->res.status = status;
-    s.job->res.steps_done = s.steps_done;
-    s.job->res.finish_s = now();
-    s.job->done = true;
-    used -= s.job->bytes;
+    job.res.status = status;
+    job.res.steps_done = steps_done;
+    job.res.finish_s = now();
+    job.done = true;
+    used -= job.bytes;
     ++completed;
-    cell_updates += (double)s.steps_done * s.job->cfg.n[0] * s.job->cfg.n[1] * s.job->cfg.n[2];
+    cell_updates += (double)steps_done * job.cfg.n[0] * job.cfg.n[1] * job.cfg.n[2];
     cv_done.notify_all();
+  }
+  void finish(Slot& s, int status) { finish(*s.job, s.steps_done, status); }
+
+  int64_t running() const {
+    int64_t n = (int64_t)active.size();
+    for (auto& b : buckets) n += (int64_t)b->slots.size();
+    return n;
+  }
+
+  void fail_job(const std::shared_ptr<Job>& j, int status) {
+    std::lock_guard<std::mutex> lk(mu);
+    j->res.status = status;
+    j->res.finish_s = now();
+    j->done = true;
+    used -= j->bytes;
+    cv_done.notify_all();
+  }
+
+  // ---- batched solves ----------------------------------------------------------------------
+  static bool batchable(const fluid_config& c) {
+    return (c.weno == FLUID_WENO_JS || c.weno == FLUID_WENO_Z) && c.visc_order != 6;
+  }
+
+  Bucket* bucket_for(const fluid_config& c) {
+    const int mixed = c.precision == FLUID_PREC_MIXED, visc = c.visc_law != FLUID_VISC_NONE;
+    for (auto& b : buckets)
+      if (b->mixed == mixed && b->weno == c.weno && b->visc == visc && !b->broken &&
+          (int)b->slots.size() < fl::kBatchMax)
+        return b.get();
+    auto b = std::make_unique<Bucket>();
+    b->mixed = mixed;
+    b->weno = c.weno;
+    b->visc = visc;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&b->host, sizeof(fl::BatchTable)) != cudaSuccess ||
+        cudaMalloc(&b->dev, sizeof(fl::BatchTable)) != cudaSuccess) {
+      drop_bucket(*b);
+      cudaGetLastError();
+      return nullptr;
+    }
+    std::memset(b->host, 0, sizeof(fl::BatchTable));
+    // an empty table, and one uncaptured chunk over it (no work: the launches' one-time set-up
+    // happens outside any capture)
+    cudaMemcpyAsync(b->dev, b->host, sizeof(fl::BatchTable), cudaMemcpyHostToDevice, b->stream);
+    if (fl::launch_batch_chunk(b->dev, 1, mixed, c.weno, visc, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+      drop_bucket(*b);
+      cudaGetLastError();
+      return nullptr;
+    }
+    buckets.push_back(std::move(b));
+    return buckets.back().get();
+  }
+
+  void drop_bucket(Bucket& b) {
+    if (b.stream) cudaStreamSynchronize(b.stream);
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    if (b.ev) cudaEventDestroy(b.ev);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    cudaFreeHost(b.host);
+    cudaFree(b.dev);
+    b.graph = nullptr;
+    b.ev = nullptr;
+    b.stream = nullptr;
+    b.host = nullptr;
+    b.dev = nullptr;
+  }
+
+  void release(BSlot& s) {
+    if (s.ev_out) cudaEventDestroy(s.ev_out);
+    cudaFree(s.U);
+    fluid_destroy(s.solver);
+    s = BSlot{};
+  }
+
+  bool admit_batched(const std::shared_ptr<Job>& j) {
+    Bucket* b = bucket_for(j->cfg);
+    if (!b) return false;                     // runs alone instead
+    BSlot s;
+    s.job = j;
+    if (fluid_create(&j->cfg, &s.solver) != FLUID_OK) {
+      fail_job(j, FLUID_EINVAL);
+      return true;
+    }
+    if (cudaMalloc(&s.U, j->nstate * sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      release(s);
+      fail_job(j, FLUID_ENOMEM);
+      return true;
+    }
+    // ordered before the bucket's next chunk on its stream
+    cudaMemcpyAsync(s.U, j->staging, j->nstate * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      j->res.start_s = now();
+    }
+    b->slots.push_back(s);
+    return true;
+  }
+
+  // one bucket: collect the finished chunk, retire solves, start the next chunk
+  bool step_bucket(Bucket& b) {
+    bool busy = false;
+    if (b.busy) {
+      if (cudaEventQuery(b.ev) == cudaErrorNotReady) return false;
+      b.busy = false;
+      busy = true;
+      for (BSlot& s : b.slots) {
+        s.steps_done += s.chunk_steps;
+        s.chunk_steps = 0;
+      }
+    }
+    // finished solves (also those admitted with no step to run) copy their state out
+    for (BSlot& s : b.slots)
+      if (!s.leaving && s.steps_done >= s.job->nsteps) {
+        cudaMemcpyAsync(s.job->staging, s.U, s.job->nstate * sizeof(double), cudaMemcpyDeviceToHost, b.stream);
+        cudaEventRecord(s.ev_out, b.stream);
+        s.leaving = true;
+        busy = true;
+      }
+    // solves whose copy-out has completed leave the bucket
+    for (size_t i = 0; i < b.slots.size();) {
+      BSlot& s = b.slots[i];
+      if (!s.leaving || cudaEventQuery(s.ev_out) == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      const int st = fluid_check(s.solver, nullptr);
+      if (s.job->U_out_host) std::memcpy(s.job->U_out_host, s.job->staging, s.job->nstate * sizeof(double));
+      double t = 0.0;
+      fluid_get_time(s.solver, &t, nullptr, nullptr);
+      s.job->res.t_final = t;
+      finish(*s.job, s.steps_done, st);
+      release(s);
+      b.slots.erase(b.slots.begin() + i);
+      busy = true;
+    }
+    if (b.busy) return busy;
+    // the next chunk over every solve with steps left
+    const int chunk = std::max(1, cfg.chunk_steps);
+    fl::BatchTable& t = *b.host;
+    t.nslots = 0;
+    for (BSlot& s : b.slots) {
+      const int left = s.job->nsteps - s.steps_done;
+      if (s.leaving || left <= 0) continue;
+      fl::BatchSlot& d = t.slot[t.nslots];
+      if (!fl::batch_slot_of(s.solver, s.U, s.job->t_end, d)) continue;
+      d.steps = std::min(chunk, left);
+      s.chunk_steps = d.steps;
+      ++t.nslots;
+    }
+    if (t.nslots == 0) return busy;
+    fl::batch_plan(t, b.mixed);
+    cudaMemcpyAsync(b.dev, b.host, sizeof(fl::BatchTable), cudaMemcpyHostToDevice, b.stream);
+    if (cfg.use_graphs && !b.graph) {
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const cudaError_t e = fl::launch_batch_chunk(b.dev, chunk, b.mixed, b.weno, b.visc, b.stream);
+        if (cudaStreamEndCapture(b.stream, &gr) == cudaSuccess && e == cudaSuccess &&
+            cudaGraphInstantiate(&b.graph, gr, 0) == cudaSuccess)
+          b.graph_chunk = chunk;
+        if (gr) cudaGraphDestroy(gr);
+      }
+      cudaGetLastError();
+    }
+    if (b.graph) cudaGraphLaunch(b.graph, b.stream);
+    else fl::launch_batch_chunk(b.dev, chunk, b.mixed, b.weno, b.visc, b.stream);
+    cudaEventRecord(b.ev, b.stream);
+    b.busy = true;
+    return true;
   }
 
   void release(Slot& s) {
@@ -222,7 +428,6 @@ struct fluid_server {
       cudaGetLastError();
     }
     active.push_back(s);
-    n_active.store((int64_t)active.size());
     return true;
   }
 
@@ -252,7 +457,7 @@ struct fluid_server {
         std::shared_ptr<Job> j;
         {
           std::lock_guard<std::mutex> lk(mu);
-          if ((int)active.size() >= cfg.max_active) break;   // active is only resized by this thread
+          if ((int)running() >= cfg.max_active) break;   // only this thread changes the running set
           for (auto it = pending.begin(); it != pending.end(); ++it)
             if (used + (*it)->bytes <= cfg.hbm_budget_bytes) {
               j = *it;
@@ -264,9 +469,15 @@ struct fluid_server {
             }
         }
         if (!j) break;
-        if (admit(j)) advance(active.back());
+        if (cfg.batch && batchable(j->cfg) && admit_batched(j)) {
+          // joins its bucket's next chunk
+        } else if (admit(j)) {
+          advance(active.back());
+        }
+        n_active.store(running());
         busy = true;
       }
+      for (auto& b : buckets) busy |= step_bucket(*b);
       // progress of the running solves
       for (size_t i = 0; i < active.size();) {
         Slot& s = active[i];
@@ -285,7 +496,7 @@ struct fluid_server {
           finish(s, st);
           release(s);
           active.erase(active.begin() + i);
-          n_active.store((int64_t)active.size());
+          n_active.store(running());
           continue;
         }
         if (!advance(s)) {
@@ -306,6 +517,16 @@ struct fluid_server {
       release(s);
     }
     active.clear();
+    for (auto& b : buckets) {
+      if (b->stream) cudaStreamSynchronize(b->stream);
+      for (BSlot& s : b->slots) {
+        finish(*s.job, s.steps_done + s.chunk_steps, FLUID_EBUSY);
+        release(s);
+      }
+      b->slots.clear();
+      drop_bucket(*b);
+    }
+    buckets.clear();
   }
 };
 

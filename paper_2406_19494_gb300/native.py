@@ -112,7 +112,7 @@ class FluidServeConfig(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32),
                 ("max_active", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_uint64)]
+                ("hbm_budget_bytes", ctypes.c_uint64), ("batch", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class FluidRequest(ctypes.Structure):

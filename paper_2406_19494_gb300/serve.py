@@ -14,12 +14,12 @@ class Server:
     """Continuous-batching server for independent solves on one GPU."""
 
     def __init__(self, budget_bytes=150e9, max_active=16, chunk_steps=20, graphs=True, autotune=True,
-                 device=0):
+                 device=0, batch=True):
         self.lib = native.lib()
         c = native.FluidServeConfig(struct_size=ctypes.sizeof(native.FluidServeConfig), device=device,
                                     max_active=max_active, chunk_steps=chunk_steps,
                                     use_graphs=1 if graphs else 0, autotune=1 if autotune else 0,
-                                    hbm_budget_bytes=int(budget_bytes))
+                                    hbm_budget_bytes=int(budget_bytes), batch=1 if batch else 0)
         h = ctypes.c_void_p()
         st = self.lib.fluid_serve_create(ctypes.byref(c), ctypes.byref(h))
         if st != native.FLUID_OK:

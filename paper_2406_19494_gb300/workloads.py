@@ -14,6 +14,7 @@ Cases (the configurations the solver is exercised and measured on):
   tgv          3-D compressible Taylor-Green vortex, 128^3, Ma 0.1, Re 1600, Pr 0.71, power-law mu
   channel      3-D compressible channel, Ma_b 1.5, Re_b 3000, 192x128x128, tanh-stretched walls
   porous_bl    2-D Ma 6 laminar boundary layer, 512x128, disturbance/porous strip on the wall
+  e2           2-D Ma 2.25 laminar boundary layer, 300x200, adiabatic wall, similarity inlet
   random_box   small random states on any boundary mix, for parity tests
   serving      a stream of independent solves of uneven sizes (isentropic vortices, four-quadrant
                Riemann problems, Taylor-Green vortices) with Poisson arrival times
@@ -225,6 +226,134 @@ def porous_bl_prims(case, xc, yc):
 def porous_bl_inflow(case, yc_padded):
     """Inflow profile on the west face plane: primitives shaped (5, 1, py) over padded y."""
     W = porous_bl_prims(case, np.array([case["lo"][0]]), yc_padded)   # (5, 1, py, 1)
+    return np.ascontiguousarray(W[:, :, :, 0])
+
+
+# ------------------------------------------------------------------------------------------------
+# compressible laminar boundary layer (Section 3.2's validation case): the similarity solution that
+# the inlet imposes and that the outlet profile is compared with
+# ------------------------------------------------------------------------------------------------
+E2_MA, E2_PR, E2_RE_UNIT, E2_TE_KELVIN = 2.25, 0.72, 1.0e4, 300.0
+
+
+def similarity_bl(Ma, Pr, gamma=1.4, suth=None, wall="adiabatic", g_wall=None, eta_max=12.0, n=2401):
+    """Similarity solution of the compressible laminar flat-plate boundary layer in the
+    Illingworth-Levy variables eta = u_e / sqrt(2 rho_e mu_e u_e x) int_0^y rho dy (Section 3.2):
+
+        (C f'')' + f f'' = 0,    (C / Pr g')' + f g' + (gamma - 1) Ma^2 C f''^2 = 0,
+
+    u / u_e = f'(eta), g = T / T_e = rho_e / rho (constant pressure), C = rho mu / (rho_e mu_e) =
+    mu(g) / g with Sutherland's law mu / mu_e = g^{3/2} (1 + s) / (g + s), s = S / T_e (suth), or
+    C = 1 (suth None).  f(0) = f'(0) = 0, f'(inf) = 1, g(inf) = 1, and at the wall g'(0) = 0
+    (adiabatic) or g(0) = g_wall (isothermal).  Shooting on the two unknown wall values (C f''(0)
+    and g(0), or C f''(0) and C g'(0) / Pr) with classical RK4 on a uniform eta grid and Newton's
+    method with a finite-difference Jacobian.
+
+    Returns a dict of arrays over eta: eta, f, fp (f'), fpp (f''), g, and Y = int_0^eta g, which maps
+    eta to the wall distance y = sqrt(2 x / Re_x_unit) Y(eta) in units of the edge state."""
+    h = eta_max / (n - 1)
+    gm = (gamma - 1.0) * Ma * Ma
+
+    def C(g):
+        if suth is None:
+            return np.ones_like(g)
+        return np.sqrt(g) * (1.0 + suth) / (g + suth)
+
+    def rhs(y):
+        f, fp, tau, g, q = y
+        c = C(g)
+        fpp = tau / c
+        gp = q * Pr / c
+        return np.array([fp, fpp, -f * fpp, gp, -f * gp - gm * c * fpp * fpp])
+
+    def shoot(u0, u1, record=False):
+        # unknowns: tau(0) = C f''(0) and g(0) (adiabatic, q(0) = 0) or q(0) (isothermal)
+        u0 = np.atleast_1d(u0).astype(np.float64)
+        u1 = np.atleast_1d(u1).astype(np.float64)
+        z = np.zeros_like(u0)
+        if wall == "adiabatic":
+            y = np.array([z, z, u0, u1, z])
+        else:
+            y = np.array([z, z, u0, np.full_like(u0, g_wall), u1])
+        rows = [y.copy()] if record else None
+        for _ in range(n - 1):
+            k1 = rhs(y)
+            k2 = rhs(y + 0.5 * h * k1)
+            k3 = rhs(y + 0.5 * h * k2)
+            k4 = rhs(y + h * k3)
+            y = y + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+            if record:
+                rows.append(y.copy())
+        return (np.array(rows) if record else y)
+
+    u = np.array([0.47, 1.0 + 0.85 * 0.5 * gm if wall == "adiabatic" else 0.0])
+    if wall != "adiabatic":
+        u[1] = -0.2 * (g_wall - 1.0)
+    for _ in range(40):
+        e = 1e-7 * np.maximum(1.0, np.abs(u))
+        y = shoot([u[0], u[0] + e[0], u[0]], [u[1], u[1], u[1] + e[1]])
+        res = np.array([y[1] - 1.0, y[3] - 1.0])            # f'(inf) - 1, g(inf) - 1 for the 3 runs
+        J = np.array([(res[:, 1] - res[:, 0]) / e[0], (res[:, 2] - res[:, 0]) / e[1]]).T
+        du = np.linalg.solve(J, -res[:, 0])
+        u = u + du
+        if np.max(np.abs(res[:, 0])) < 1e-12 and np.max(np.abs(du)) < 1e-12:
+            break
+    rows = shoot(u[0], u[1], record=True)[:, :, 0]
+    eta = np.linspace(0.0, eta_max, n)
+    f, fp, tau, g, q = rows.T
+    Y = np.concatenate([[0.0], np.cumsum(0.5 * h * (g[1:] + g[:-1]))])
+    return dict(eta=eta, f=f, fp=fp, fpp=tau / C(g), g=g, Y=Y)
+
+
+def e2_case(nx=300, ny=200, beta=2.2):
+    """Compressible laminar boundary layer of Section 3.2 (the no-disturbance validation): Ma 2.25,
+    Pr 0.72, gamma 1.4, [1, 1.5] x [0, 0.4] with 300 x 200 cells, uniform in x and tanh-stretched
+    towards the wall in y (beta = 2.2), adiabatic no-slip wall at the south, zero gradient at the
+    north and east, the similarity solution imposed at the west inlet, Re per unit length 1e4,
+    Sutherland viscosity (S = 110.4 K over an edge temperature of 300 K, this build's reading).
+    Nondimensional rho_e = u_e = T_e = 1, R = 1 / (gamma Ma^2), mu_e = 1 / Re."""
+    g = 1.4
+    Z = ("zero_gradient", "zero_gradient")
+    return _base(2, (nx, ny, 1), (1.0, 0.0, 0.0), (1.5, 0.4, 1.0),
+                 (("inflow", "zero_gradient"), ("adiabatic", "zero_gradient"), ("periodic", "periodic")),
+                 stretch=("uniform", "tanh1", "uniform"), beta=(0.0, beta, 0.0), gamma=g,
+                 R=1.0 / (g * E2_MA ** 2), Pr=E2_PR, visc="sutherland", mu_ref=1.0 / E2_RE_UNIT,
+                 T_ref=1.0, suth_S=110.4 / E2_TE_KELVIN, weno="z", name="e2_bl%dx%d" % (nx, ny))
+
+
+def e2_similarity(case):
+    """The similarity solution of the case's edge state (adiabatic wall, its Sutherland constant)."""
+    return similarity_bl(E2_MA, case["Pr"], case["gamma"], suth=case["suth_S"])
+
+
+def similarity_field(case, sim, x, y):
+    """Primitives (rho, u, v, w, p) of the self-similar boundary layer at stations x (1-D) and wall
+    distances y (1-D), shaped (5, 1, len(y), len(x)): u = f'(eta), T = g(eta), v = (f' Y - g f) /
+    sqrt(2 Re_x) (from the stream function sqrt(2 xi) f(eta)), uniform pressure p = R T_e rho_e."""
+    Re = 1.0 / case["mu_ref"]
+    y2, x2 = np.meshgrid(y, x, indexing="ij")
+    scale = np.sqrt(2.0 * x2 / Re)
+    Ysim = np.abs(y2) / scale
+    eta = np.interp(Ysim, sim["Y"], sim["eta"], right=np.nan)
+    far = np.isnan(eta)
+    Ymax, eta_max = sim["Y"][-1], sim["eta"][-1]
+    eta = np.where(far, eta_max + (Ysim - Ymax), eta)        # beyond the table: g = 1, f' = 1
+    fp = np.interp(eta, sim["eta"], sim["fp"], right=1.0)
+    g = np.interp(eta, sim["eta"], sim["g"], right=1.0)
+    f = np.interp(eta, sim["eta"], sim["f"], right=np.nan)
+    f = np.where(np.isnan(f), sim["f"][-1] + (eta - eta_max), f)
+    Yv = np.where(far, Ysim, np.interp(eta, sim["eta"], sim["Y"]))
+    v = (fp * Yv - g * f) / np.sqrt(2.0 * Re * x2)
+    p = case["R"] * 1.0
+    rho = p / (case["R"] * g)
+    z = np.zeros_like(fp)
+    return np.stack([rho, fp, v, z, np.full_like(fp, p)])[:, None]
+
+
+def e2_inflow(case, sim, yc_padded):
+    """Inlet profile on the west face plane (x = lo): primitives shaped (5, 1, py) over padded y
+    (ghost rows below the wall take the profile at |y|; the wall map replaces them)."""
+    W = similarity_field(case, sim, np.array([case["lo"][0]]), yc_padded)
     return np.ascontiguousarray(W[:, :, :, 0])
 
 
