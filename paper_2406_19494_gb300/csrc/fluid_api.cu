@@ -17,7 +17,30 @@ using fl::Ctl;
 using fl::Geo;
 using fl::Phys;
 
+// Device memory of a solver: cudaMalloc (fluid_create), or stream-ordered on one stream for the
+// solvers the serving loop owns, so that admitting and retiring a solve never waits for the device.
+struct SolverAlloc {
+  cudaStream_t st = nullptr;
+  bool async = false;
+  cudaError_t malloc(void** p, size_t n) const {
+    return async ? cudaMallocAsync(p, n, st) : cudaMalloc(p, n);
+  }
+  void free(void* p) const {
+    if (!p) return;
+    if (async) cudaFreeAsync(p, st);
+    else cudaFree(p);
+  }
+  cudaError_t h2d(void* d, const void* h, size_t n) const {
+    return async ? cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st)
+                 : cudaMemcpy(d, h, n, cudaMemcpyHostToDevice);
+  }
+  cudaError_t memset(void* d, int v, size_t n) const {
+    return async ? cudaMemsetAsync(d, v, n, st) : cudaMemset(d, v, n);
+  }
+};
+
 struct fluid_solver {
+  SolverAlloc alloc;
   fluid_config cfg;
   Geo geo;
   Phys ph;
@@ -416,13 +439,17 @@ const char* fluid_last_error(const fluid_solver* s) {
   return s ? s->err.c_str() : g_create_error.c_str();
 }
 
-int fluid_create(const fluid_config* cfg, fluid_solver** out) {
+}  // extern "C"
+
+namespace {
+int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
   if (!out) return fail(nullptr, FLUID_EINVAL, "out is NULL");
   *out = nullptr;
   if (const char* why = validate(cfg)) return fail(nullptr, FLUID_EINVAL, why);
   fluid_solver* s = new (std::nothrow) fluid_solver();
   if (!s) return fail(nullptr, FLUID_ENOMEM, "host allocation failed");
   s->cfg = *cfg;
+  s->alloc = al;
   const fluid_config& c = *cfg;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e != cudaSuccess) {
@@ -477,30 +504,30 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
     fluid_destroy(s);
     return fail(nullptr, err == cudaErrorMemoryAllocation ? FLUID_ENOMEM : FLUID_ECUDA, m);
   };
-  if ((e = cudaMalloc(&s->metric, nmetric * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc metric");
+  if ((e = al.malloc((void**)&s->metric, nmetric * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc metric");
   s->mixed = c.precision == FLUID_PREC_MIXED;
   // the mixed path keeps H = E + p in one more FP64 row of W
-  if ((e = cudaMalloc(&s->W, (fl::NW + (s->mixed ? 1 : 0)) * nc * sizeof(double))) != cudaSuccess)
+  if ((e = al.malloc((void**)&s->W, (fl::NW + (s->mixed ? 1 : 0)) * nc * sizeof(double))) != cudaSuccess)
     return bail(e, "cudaMalloc W");
   if (s->mixed) {
-    if ((e = cudaMalloc(&s->W32, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
-    if ((e = cudaMalloc(&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
+    if ((e = al.malloc((void**)&s->W32, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    if ((e = al.malloc((void**)&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
     if (c.visc_law != FLUID_VISC_NONE)
-      if ((e = cudaMalloc(&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
+      if ((e = al.malloc((void**)&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
   } else if (c.visc_law != FLUID_VISC_NONE) {
-    if ((e = cudaMalloc(&s->G, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G");
+    if ((e = al.malloc((void**)&s->G, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G");
   }
-  if ((e = cudaMalloc(&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
-  if ((e = cudaMalloc(&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
+  if ((e = al.malloc((void**)&s->A, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc A");
+  if ((e = al.malloc((void**)&s->R, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc R");
   if (!s->mixed) {
     s->fb_cap = fl::seam_capacity(g);
-    if ((e = cudaMalloc(&s->FB, 10 * (size_t)s->fb_cap * sizeof(double))) != cudaSuccess)
+    if ((e = al.malloc((void**)&s->FB, 10 * (size_t)s->fb_cap * sizeof(double))) != cudaSuccess)
       return bail(e, "cudaMalloc FB");
   }
-  if ((e = cudaMalloc(&s->partial, s->nparts * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc partial");
-  if ((e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
+  if ((e = al.malloc((void**)&s->partial, s->nparts * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc partial");
+  if ((e = al.malloc((void**)&s->ctl, sizeof(Ctl))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
   Ctl c0{};
-  if ((e = cudaMemcpy(s->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "ctl init");
+  if ((e = al.h2d(s->ctl, &c0, sizeof(Ctl))) != cudaSuccess) return bail(e, "ctl init");
 
   std::vector<double> all;
   all.reserve(nmetric);
@@ -515,7 +542,7 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       all.insert(all.end(), m[k].begin(), m[k].end());
     }
   }
-  if ((e = cudaMemcpy(s->metric, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = al.h2d(s->metric, all.data(), all.size() * sizeof(double))) != cudaSuccess)
     return bail(e, "metric upload");
   if (s->mixed) {
     std::vector<float> mf32;
@@ -524,7 +551,7 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       off32[a] = mf32.size();
       for (int k = 0; k < g.p[a]; ++k) mf32.push_back((float)all[off[a][4] + k]);
     }
-    if ((e = cudaMemcpy(s->mf32, mf32.data(), mf32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = al.h2d(s->mf32, mf32.data(), mf32.size() * sizeof(float))) != cudaSuccess)
       return bail(e, "metric upload");
     for (int a = 0; a < 3; ++a) g.mf32[a] = s->mf32 + off32[a];
   }
@@ -549,8 +576,8 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       if (a < c.ndim && c.bc[a][sd] == FLUID_BC_INFLOW) {
         const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
         const size_t cnt = 5 * (size_t)g.p[t1] * g.p[t2];
-        if ((e = cudaMalloc(&s->inflow[a][sd], cnt * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc inflow");
-        if ((e = cudaMemset(s->inflow[a][sd], 0, cnt * sizeof(double))) != cudaSuccess) return bail(e, "inflow init");
+        if ((e = al.malloc((void**)&s->inflow[a][sd], cnt * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc inflow");
+        if ((e = al.memset(s->inflow[a][sd], 0, cnt * sizeof(double))) != cudaSuccess) return bail(e, "inflow init");
         s->inflow_count[a][sd] = cnt;
         bc.inflow[a][sd] = s->inflow[a][sd];
       }
@@ -564,17 +591,17 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
         bc.porous_side = sd;
         bc.porous_t1 = a == 0 ? 1 : 0;
         const int t1 = bc.porous_t1;
-        if ((e = cudaMalloc(&s->vw, g.p[t1] * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc vw");
-        if ((e = cudaMalloc(&s->phi, c.porous_count * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc phi");
+        if ((e = al.malloc((void**)&s->vw, g.p[t1] * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc vw");
+        if ((e = al.malloc((void**)&s->phi, c.porous_count * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc phi");
         std::vector<double> phi0(c.porous_count, c.porous_phi0);
-        if ((e = cudaMemcpy(s->phi, phi0.data(), phi0.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        if ((e = al.h2d(s->phi, phi0.data(), phi0.size() * sizeof(double))) != cudaSuccess)
           return bail(e, "phi init");
         bc.vw = s->vw;
         if ((e = fl::launch_wall_velocity(s->phi, s->vw, g.xc[t1], g.p[t1], g.h[t1], c.porous_begin,
                                           c.porous_count, c.porous_A / c.porous_phi0,
-                                          2.0 * M_PI * c.porous_kappa, 0)) != cudaSuccess)
+                                          2.0 * M_PI * c.porous_kappa, al.st)) != cudaSuccess)
           return bail(e, "wall velocity");
-        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "wall velocity sync");
+        if (!al.async && (e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "wall velocity sync");
       }
   if (c.adjoint) {
     if (c.precision != FLUID_PREC_FP64) {
@@ -582,22 +609,22 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       return fail(nullptr, FLUID_ENOTSUP, "the adjoint is built for FLUID_PREC_FP64");
     }
     const bool visc = c.visc_law != FLUID_VISC_NONE;
-    if ((e = cudaMalloc(&s->gW, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gW");
-    if ((e = cudaMalloc(&s->CW, 36 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CW");
+    if ((e = al.malloc((void**)&s->gW, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gW");
+    if ((e = al.malloc((void**)&s->CW, 36 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CW");
     if (visc) {
-      if ((e = cudaMalloc(&s->gG, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gG");
-      if ((e = cudaMalloc(&s->CG, 16 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
+      if ((e = al.malloc((void**)&s->gG, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gG");
+      if ((e = al.malloc((void**)&s->CG, 16 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
     }
-    if ((e = cudaMalloc(&s->Wn, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wn");
-    if ((e = cudaMalloc(&s->W1, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W1");
+    if ((e = al.malloc((void**)&s->Wn, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wn");
+    if ((e = al.malloc((void**)&s->W1, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W1");
     if (visc) {
-      if ((e = cudaMalloc(&s->Gn, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Gn");
-      if ((e = cudaMalloc(&s->G1, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G1");
+      if ((e = al.malloc((void**)&s->Gn, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Gn");
+      if ((e = al.malloc((void**)&s->G1, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc G1");
     }
     double** bufs[] = {&s->S1, &s->S2, &s->MU, &s->L1, &s->L2, &s->GT};
     for (double** b : bufs) {
-      if ((e = cudaMalloc(b, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc adjoint state");
-      if ((e = cudaMemset(*b, 0, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "adjoint init");
+      if ((e = al.malloc((void**)b, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc adjoint state");
+      if ((e = al.memset(*b, 0, fl::NV * nc * sizeof(double))) != cudaSuccess) return bail(e, "adjoint init");
     }
     // wall columns: every face plane of the grid is covered by the largest padded plane
     size_t plane = 0;
@@ -606,13 +633,26 @@ int fluid_create(const fluid_config* cfg, fluid_solver** out) {
       plane = std::max(plane, (size_t)g.p[t1] * g.p[t2]);
     }
     s->gvw_count = plane;
-    if ((e = cudaMalloc(&s->gvw, plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gvw");
-    if ((e = cudaMalloc(&s->gT2, 2 * plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gT2");
+    if ((e = al.malloc((void**)&s->gvw, plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gvw");
+    if ((e = al.malloc((void**)&s->gT2, 2 * plane * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gT2");
     s->nloss = 1024;
-    if ((e = cudaMalloc(&s->parts, s->nloss * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc parts");
+    if ((e = al.malloc((void**)&s->parts, s->nloss * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc parts");
   }
   *out = s;
   return FLUID_OK;
+}
+}  // namespace
+
+namespace fl {
+int solver_create_async(const fluid_config* cfg, cudaStream_t st, fluid_solver** out) {
+  return create_impl(cfg, out, SolverAlloc{st, true});
+}
+}  // namespace fl
+
+extern "C" {
+
+int fluid_create(const fluid_config* cfg, fluid_solver** out) {
+  return create_impl(cfg, out, SolverAlloc{});
 }
 
 void fluid_destroy(fluid_solver* s) {
@@ -620,25 +660,27 @@ void fluid_destroy(fluid_solver* s) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(s->device);
-  cudaDeviceSynchronize();
-  cudaFree(s->metric);
-  cudaFree(s->W);
-  cudaFree(s->G);
-  cudaFree(s->W32);
-  cudaFree(s->mf32);
-  cudaFree(s->G32);
+  // stream-ordered memory is released after the work already on its stream, without waiting
+  if (!s->alloc.async) cudaDeviceSynchronize();
+  const SolverAlloc& al = s->alloc;
+  al.free(s->metric);
+  al.free(s->W);
+  al.free(s->G);
+  al.free(s->W32);
+  al.free(s->mf32);
+  al.free(s->G32);
   for (double* p : {s->gW, s->gG, s->CW, s->CG, s->S1, s->S2, s->MU, s->L1, s->L2, s->GT, s->gvw,
                     s->parts, s->gT2, s->Wn, s->Gn, s->W1, s->G1})
-    cudaFree(p);
-  cudaFree(s->A);
-  cudaFree(s->R);
-  cudaFree(s->FB);
-  cudaFree(s->partial);
-  cudaFree(s->ctl);
-  cudaFree(s->vw);
-  cudaFree(s->phi);
+    al.free(p);
+  al.free(s->A);
+  al.free(s->R);
+  al.free(s->FB);
+  al.free(s->partial);
+  al.free(s->ctl);
+  al.free(s->vw);
+  al.free(s->phi);
   for (int a = 0; a < 3; ++a)
-    for (int sd = 0; sd < 2; ++sd) cudaFree(s->inflow[a][sd]);
+    for (int sd = 0; sd < 2; ++sd) al.free(s->inflow[a][sd]);
   for (auto* v : {&s->prof_pending, &s->prof_pool})
     for (auto& ev : *v) {
       cudaEventDestroy(ev.a);

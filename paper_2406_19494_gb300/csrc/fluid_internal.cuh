@@ -259,6 +259,9 @@ __device__ __forceinline__ uint3 batch_bid(const int vg[3], long long lb) {
   b.z = (unsigned)(lb / ((long long)vg[0] * vg[1]));
   return b;
 }
+// fluid_create with stream-ordered allocations on st (cudaMallocAsync): set-up copies are enqueued
+// on st and nothing synchronises; fluid_destroy of such a solver frees on st without waiting
+int solver_create_async(const fluid_config* cfg, cudaStream_t st, fluid_solver** out);
 // a solver's part of a batch (its geometry, physics, boundaries and scratch, state U, t_end); false
 // when its configuration has no batched kernels (TENO6-A, sixth-order stencils, exchange faces)
 bool batch_slot_of(fluid_solver* s, double* U, double t_end, BatchSlot& out);

@@ -69,6 +69,7 @@ struct BSlot {
   std::shared_ptr<Job> job;
   fluid_solver* solver = nullptr;
   double* U = nullptr;
+  cudaStream_t stream = nullptr;  // the bucket's (its memory is ordered on it)
   cudaEvent_t ev_out = nullptr;   // its copy-out, once it has finished
   int steps_done = 0;
   int chunk_steps = 0;            // steps of the chunk in flight
@@ -230,8 +231,8 @@ struct fluid_server {
 
   void release(BSlot& s) {
     if (s.ev_out) cudaEventDestroy(s.ev_out);
-    cudaFree(s.U);
-    fluid_destroy(s.solver);
+    if (s.U) cudaFreeAsync(s.U, s.stream);
+    fluid_destroy(s.solver);            // stream-ordered: frees after the solve's work
     s = BSlot{};
   }
 
@@ -240,11 +241,13 @@ struct fluid_server {
     if (!b) return false;                     // runs alone instead
     BSlot s;
     s.job = j;
-    if (fluid_create(&j->cfg, &s.solver) != FLUID_OK) {
+    // stream-ordered memory on the bucket's stream: admission does not wait for the device
+    if (fl::solver_create_async(&j->cfg, b->stream, &s.solver) != FLUID_OK) {
       fail_job(j, FLUID_EINVAL);
       return true;
     }
-    if (cudaMalloc(&s.U, j->nstate * sizeof(double)) != cudaSuccess ||
+    s.stream = b->stream;
+    if (cudaMallocAsync((void**)&s.U, j->nstate * sizeof(double), b->stream) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming) != cudaSuccess) {
       release(s);
       fail_job(j, FLUID_ENOMEM);
@@ -335,9 +338,9 @@ struct fluid_server {
   void release(Slot& s) {
     if (s.graph) cudaGraphExecDestroy(s.graph);
     if (s.ev) cudaEventDestroy(s.ev);
+    if (s.U) cudaFreeAsync(s.U, s.stream);
+    fluid_destroy(s.solver);            // stream-ordered on s.stream
     if (s.stream) cudaStreamDestroy(s.stream);
-    cudaFree(s.U);
-    fluid_destroy(s.solver);
     s = Slot{};
   }
 
@@ -357,7 +360,7 @@ struct fluid_server {
       float best = 1e30f;
       std::pair<int, int> pick{0, 0};
       cudaEvent_t a, b;
-      if (cudaMalloc(&tmp, s.job->nstate * sizeof(double)) == cudaSuccess &&
+      if (cudaMallocAsync((void**)&tmp, s.job->nstate * sizeof(double), s.stream) == cudaSuccess &&
           cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
         for (auto& cs : cand) {
           if (fluid_tune_faces(s.solver, cs.first, cs.second) != FLUID_OK) continue;
@@ -378,7 +381,7 @@ struct fluid_server {
         cudaEventDestroy(b);
         fluid_set_time(s.solver, 0.0, s.stream);
       }
-      cudaFree(tmp);
+      if (tmp) cudaFreeAsync(tmp, s.stream);
       it = tuned.emplace(key, pick).first;
     }
     fluid_tune_faces(s.solver, it->second.first, it->second.second);
@@ -387,17 +390,16 @@ struct fluid_server {
   bool admit(const std::shared_ptr<Job>& j) {
     Slot s;
     s.job = j;
-    if (fluid_create(&j->cfg, &s.solver) != FLUID_OK) {
-      std::lock_guard<std::mutex> lk(mu);
-      j->res.status = FLUID_EINVAL;
-      j->res.finish_s = now();
-      j->done = true;
-      used -= j->bytes;
-      cv_done.notify_all();
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fail_job(j, FLUID_ECUDA);
       return false;
     }
-    if (cudaMalloc(&s.U, j->nstate * sizeof(double)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    if (fl::solver_create_async(&j->cfg, s.stream, &s.solver) != FLUID_OK) {
+      cudaStreamDestroy(s.stream);
+      fail_job(j, FLUID_EINVAL);
+      return false;
+    }
+    if (cudaMallocAsync((void**)&s.U, j->nstate * sizeof(double), s.stream) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
       release(s);
       std::lock_guard<std::mutex> lk(mu);
@@ -545,6 +547,14 @@ int fluid_serve_create(const fluid_serve_config* cfg, fluid_server** out) {
   s->cfg = *cfg;
   s->device = cfg->device;
   s->t0 = Clock::now();
+  // the solves' stream-ordered memory returns to the device's pool and is reused without
+  // returning it to the driver in between (the HBM budget bounds what the server holds)
+  cudaMemPool_t pool;
+  if (cudaSetDevice(cfg->device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
+    uint64_t keep = cfg->hbm_budget_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   s->worker = std::thread([s] { s->loop(); });
   *out = s;
   return FLUID_OK;
@@ -556,6 +566,11 @@ void fluid_serve_destroy(fluid_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   for (auto& kv : s->jobs) cudaFreeHost(kv.second->staging);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+  }
   delete s;
 }
 
