@@ -1,8 +1,21 @@
 """Algorithmic work per unit of the FP64 path (used for roofline fractions).
 
-Counts are floating-point operations of the discretisation itself, as the kernels evaluate it:
-add, sub, mul, div, sqrt, min/max and pow count one each; a fused multiply-add counts two.  They
-are not instruction counts (a division or square root expands into several FP64 instructions).
+The algorithmic counts are measured, not estimated: the oracle's own right-hand side, RK3
+combination and CFL rates run on counting scalars (the graph of operations reachable from the
+results, so the unselected HLLC branches and discarded halo work do not count; add, sub, mul, div,
+sqrt and pow count one each), stored per workload and phase in profiles/oracle_op_counts.json.
+`measured_counts()` reads them; the functions below take the measured figure wherever it exists
+(3-D WENO5-JS / WENO5-Z with power-law or Sutherland viscosity or none, and TENO6-A with sixth-order
+dissipative fluxes) and fall back to the hand count of this module's table otherwise.
+
+The executed work of the kernels (FP64 instructions counted by ncu on the 64^3 Taylor-Green and
+96 x 64 x 64 channel workloads: flops = 2 DFMA + DADD + DMUL) is kept beside it in EXECUTED.  The
+kernels share WENO5 indicator sets between neighbouring faces, so they execute fewer flops than
+the definition needs; TENO6-A's definition as the oracle writes it evaluates its smoothness
+measures as full quadratic forms (each symmetric pair twice), which no implementation does, so for
+that kernel the executed count is the meaningful one.
+
+Hand counts (the fallback):
 
 Per face (one axis, one face, 3-D viscous WENO5-Z + HLLC):
   WENO5-Z reconstruction    73 per variable and side (JS: 69); 10 per face
@@ -15,6 +28,15 @@ Per cell and axis: one face + the flux difference (3 per variable) = face + 15.
 Per cell and stage: primitives 15, centre gradients 6 per component, stage combination about 20.
 Per cell and RK3 step: 3 stages + the CFL reduction (about 28).
 """
+
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+COUNTS = os.path.join(ROOT, "profiles", "oracle_op_counts.json")
+
+# executed FP64 flops per cell and axis (ncu op counters, 2 DFMA + DADD + DMUL) of the face kernels
+EXECUTED = {"k_face": 741, "k_face_teno": 1578}
 
 WENO = {"z": 73, "js": 69}
 TENO = 165
@@ -46,9 +68,44 @@ def face_flops(ndim, weno, visc, order=4):
     return recon_flops(weno) + HLLC + visc_face(ndim, visc, order)
 
 
+_measured = None
+
+
+def measured_counts():
+    """The oracle's counted work per workload (None if the file is missing)."""
+    global _measured
+    if _measured is None:
+        try:
+            with open(COUNTS) as f:
+                _measured = json.load(f)["workloads"]
+        except (OSError, ValueError, KeyError):
+            _measured = {}
+    return _measured
+
+
+def _key(ndim, weno, visc, order):
+    if ndim != 3:
+        return None
+    if weno == "teno6a":
+        return "teno6a_power_visc6" if (visc == "power" and order == 6) else None
+    base = {"z": "weno5z", "js": "weno5js"}.get(weno)
+    if base is None or order != 4:
+        return None
+    return {"power": base + "_power", "none": "weno5z_euler" if weno == "z" else None,
+            "sutherland": "weno5z_sutherland" if weno == "z" else None}.get(visc)
+
+
+def measured(ndim, weno, visc, unit, order=4):
+    """Counted flops of `unit` (cell_axis, cell_update, face, ...) or None."""
+    k = _key(ndim, weno, visc, order)
+    m = measured_counts().get(k) if k else None
+    return m[unit]["flops"] if m else None
+
+
 def cell_axis_flops(ndim, weno, visc, order=4):
     """One face flux plus the flux difference of one cell along one axis (a face-kernel unit)."""
-    return face_flops(ndim, weno, visc, order) + 15
+    m = measured(ndim, weno, visc, "cell_axis", order)
+    return m if m is not None else face_flops(ndim, weno, visc, order) + 15
 
 
 def cell_stage_flops(ndim, weno, visc, order=4):
@@ -58,7 +115,8 @@ def cell_stage_flops(ndim, weno, visc, order=4):
 
 def cell_update_flops(ndim, weno, visc, order=4):
     """Algorithmic FP64 flops of one cell over one TVD-RK3 step."""
-    return 3 * cell_stage_flops(ndim, weno, visc, order) + DT
+    m = measured(ndim, weno, visc, "cell_update", order)
+    return m if m is not None else 3 * cell_stage_flops(ndim, weno, visc, order) + DT
 
 
 def cell_update_bytes(nvar=5, word=8):
