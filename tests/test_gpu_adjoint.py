@@ -270,3 +270,32 @@ def test_long_trajectory_gradient_stays_bounded():
     Jm = wall_heat_loss(phi0 - h * d, s, torch.from_numpy(U0).cuda(), 150, 20, 1, 0).item()
     fd = (Jp - Jm) / (2 * h)
     assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
+
+
+@pytest.mark.slow
+def test_w4_gradient_against_complex_step_relative():
+    """The porous boundary-layer workload's gradient as the benchmark computes it: 512 x 128 cells,
+    256 porous wall cells, 400 steps with checkpoints every 20 (the oracle's complex-step run takes
+    about four minutes on one host core): the directional derivative of the autograd gradient along
+    a seeded random direction equals the complex-step derivative of the oracle's trajectory within
+    1e-6 of itself (relative, not scaled by the direction's size), and J equals the oracle's within
+    1e-10."""
+    from paper_2406_19494_gb300.adjoint import wall_heat_loss
+    c, case, grid, U0, prof = _bl_small(512, 128, 256)
+    nsteps, K = 400, 20
+    phi0 = wl.porous_phi(c, seed=0)
+    s = _solver(c, None, {(0, 0): prof})
+    phi = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    J = wall_heat_loss(phi, s, torch.from_numpy(U0).cuda(), nsteps, K, 1, 0)
+    J.backward()
+    g = phi.grad.cpu().numpy()
+    d = np.random.default_rng(7).uniform(-1.0, 1.0, len(phi0))
+    ph = phi0 + 1j * H * d
+    U = U0.astype(np.complex128)
+    for _ in range(nsteps):
+        U = nf.rk3_step(U, c["dt_fixed"], case, grid, ph, {(0, 0): prof})
+    Jc = nf.wall_heat_loss(U, case, grid, 1, 0, ph, {(0, 0): prof})
+    cs = Jc.imag / H
+    adj = float(np.dot(g, d))
+    assert abs(J.item() - Jc.real) <= 1e-10 * abs(Jc.real), (J.item(), Jc.real)
+    assert abs(adj - cs) <= 1e-6 * abs(cs), (adj, cs, abs(adj - cs) / abs(cs))
