@@ -352,6 +352,8 @@ def run_fluid(args):
     mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
     mixed_ms = max_over_ranks(mixed_ms, "cuda")
     mixed_err = mixed_vs_fp64(s, sm, U, Um, case, args.warmup + args.steps)
+    if not args.no_mixed_errors and args.workload == "tgv128":
+        mixed_err["stated_workloads"] = mixed_errors_stated()
     one_call = None
     if ws == 1:
         Uc = U0.clone()
@@ -499,6 +501,107 @@ def mixed_vs_fp64(s64, s32, U64, U32, case, steps):
             "state_max_rel": [float(v) for v in np.max(np.abs((a - b).reshape(5, -1)), axis=1) / scale],
             "kinetic_energy_rel": abs(ke_b - ke_a) / abs(ke_a),
             "kinetic_energy_rate_rel": abs(rate_b - rate_a) / abs(rate_a)}
+
+
+def mixed_errors_stated(tgv_steps=1000, channel_steps=50, bl_steps=200):
+    """Mixed precision against FP64 on the stated workloads, from the same initial states with the
+    same frozen time step (the FP64 CFL step of the initial state), so both compare at the same
+    times.  TGV 128^3 over its 1000 steps: the kinetic energy and its dissipation rate (from each
+    solver's own right-hand side) every 100 steps; channel 192x128x128: the wall heat flux and wall
+    shear of both walls (fluid_wall_fluxes) after channel_steps; porous boundary layer 512x128: the
+    same on its porous wall after bl_steps.  Host diagnostics on copies."""
+    import torch
+    from paper_2406_19494_gb300.solver import Solver
+
+    def setup(case, prims_of, extra=None):
+        s = Solver(case)
+        cen = [s.grid(a)[0] for a in range(3)]
+        h = [3 if a < case["ndim"] else 0 for a in range(3)]
+        cen = [cen[a][h[a]:len(cen[a]) - h[a]] for a in range(3)]
+        W = prims_of(case, cen)
+        pad = [(0, 0)] + [(h[a], h[a]) for a in (2, 1, 0)]
+        U0 = s.prim_to_cons(torch.from_numpy(np.ascontiguousarray(np.pad(W, pad, mode="edge"))).cuda())
+        dt = float(s.compute_dt(U0).item())
+        out = {}
+        for prec in ("fp64", "mixed"):
+            sp = Solver(dict(case, dt_fixed=dt), precision=prec)
+            if extra:
+                extra(sp)
+            out[prec] = sp
+        return out, U0, dt
+
+    def rel(a, b):
+        return abs(a - b) / abs(b) if b != 0 else abs(a - b)
+
+    res = {}
+    # Taylor-Green 128^3
+    case = workloads.tgv_case(128)
+    sv, U0, dt = setup(case, lambda c, cen: workloads.tgv_prims(c, *cen))
+    inner = (slice(None),) + tuple(slice(3, 3 + case["n"][a]) for a in (2, 1, 0))
+    vol = (2 * math.pi / 128) ** 3
+    U = {p: U0.clone() for p in sv}
+    samples = []
+    for k in range(0, tgv_steps + 1, 100):
+        if k:
+            for p in sv:
+                sv[p].step(U[p], 100)
+        ke, eps = {}, {}
+        for p in sv:
+            u = U[p].cpu().numpy()[inner]
+            r = sv[p].rhs(U[p]).cpu().numpy()[inner]
+            m2 = u[1] ** 2 + u[2] ** 2 + u[3] ** 2
+            ke[p] = float((0.5 * m2 / u[0]).sum()) * vol
+            eps[p] = -float(((u[1] * r[1] + u[2] * r[2] + u[3] * r[3]) / u[0] - 0.5 * m2 / u[0] ** 2 * r[0]).sum()) * vol
+        samples.append({"step": k, "t": k * dt, "ke_rel": rel(ke["mixed"], ke["fp64"]),
+                        "dissipation_rate_rel": rel(eps["mixed"], eps["fp64"]),
+                        "dissipation_rate_fp64": eps["fp64"]})
+    res["tgv128_1000_steps"] = {
+        "dt": dt, "samples": samples,
+        "max_dissipation_rate_rel": max(x["dissipation_rate_rel"] for x in samples),
+        "max_ke_rel": max(x["ke_rel"] for x in samples)}
+    del U, sv, U0
+    torch.cuda.empty_cache()
+    # channel 192x128x128: both walls
+    case = workloads.channel_case(192, 128, 128)
+    sv, U0, dt = setup(case, lambda c, cen: workloads.channel_prims(c, *cen, seed=0))
+    walls = {}
+    for p in sv:
+        U = U0.clone()
+        sv[p].step(U, channel_steps)
+        walls[p] = [tuple(x.cpu().numpy() for x in sv[p].wall_fluxes(U, 1, sd)) for sd in (0, 1)]
+    out = {"steps": channel_steps, "dt": dt}
+    for sd in (0, 1):
+        q64, t64 = walls["fp64"][sd]
+        q32, t32 = walls["mixed"][sd]
+        out["wall%d" % sd] = {"mean_heat_flux_rel": rel(q32.mean(), q64.mean()),
+                              "mean_wall_shear_rel": rel(t32.mean(), t64.mean()),
+                              "max_heat_flux_err_over_max": float(np.max(np.abs(q32 - q64)) / np.max(np.abs(q64))),
+                              "max_wall_shear_err_over_max": float(np.max(np.abs(t32 - t64)) / np.max(np.abs(t64)))}
+    res["channel192_walls"] = out
+    del sv, U0
+    torch.cuda.empty_cache()
+    # porous boundary layer 512x128
+    case = workloads.porous_bl_case(512, 128)
+    phi = torch.from_numpy(workloads.porous_phi(case, seed=0)).cuda()
+
+    def bl_extra(sp):
+        yc = sp.grid(1)[0]
+        sp.set_inflow(0, 0, torch.from_numpy(workloads.porous_bl_inflow(case, yc)).cuda())
+        sp.set_wall_params(phi)
+
+    sv, U0, dt = setup(case, lambda c, cen: workloads.porous_bl_prims(c, cen[0], cen[1]), bl_extra)
+    fx = {}
+    for p in sv:
+        U = U0.clone()
+        sv[p].step(U, bl_steps)
+        fx[p] = tuple(x.cpu().numpy() for x in sv[p].wall_fluxes(U, 1, 0))
+    res["porous_bl512_wall"] = {
+        "steps": bl_steps, "dt": dt,
+        "integrated_heat_flux_rel": rel(float(fx["mixed"][0].sum()), float(fx["fp64"][0].sum())),
+        "mean_wall_shear_rel": rel(float(fx["mixed"][1].mean()), float(fx["fp64"][1].mean())),
+        "max_heat_flux_err_over_max": float(np.max(np.abs(fx["mixed"][0] - fx["fp64"][0])) / np.max(np.abs(fx["fp64"][0]))),
+        "max_wall_shear_err_over_max": float(np.max(np.abs(fx["mixed"][1] - fx["fp64"][1])) / np.max(np.abs(fx["fp64"][1])))}
+    return res
 
 
 def measure_teno(flush, stream, args, steps=5):
@@ -893,6 +996,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-teno", action="store_true", help="skip the TENO6-A channel-scheme measurement")
+    ap.add_argument("--no-mixed-errors", action="store_true",
+                    help="skip the mixed-vs-FP64 errors on the stated workloads (TGV 1000 steps, walls)")
     ap.add_argument("--e2", action="store_true",
                     help="also run the Ma 2.25 boundary-layer validation to steady state (about 3 minutes)")
     args = ap.parse_args()

@@ -259,6 +259,16 @@ int fluid_unpack_halo(fluid_solver* s, double* U_dev, int axis, int side, const 
 int fluid_rk3_stage(fluid_solver* s, int stage, const double* Un_dev, const double* Us_dev,
                     double* Ud_dev, double dt, void* stream);
 
+/* Wall heat flux and wall shear on the isothermal or porous face (axis, side) of a 2-D or 3-D
+ * solve (Section 3.2's quantities of the boundary layer; also the channel walls): per wall cell,
+ * laid out [n_t2][n_t1] with t1 < t2 the other axes, q_w = -lambda(T_w) dT/dn and
+ * tau_w = mu(T_w) du_t1/dn (t1 the first other axis, derivatives along +axis) by the
+ * fourth-order face stencil through the mirrored ghost cells.  Written to qw_dev / tw_dev
+ * (device, either may be NULL).  Works for either precision (the primitives are formed in FP64).
+ * FLUID_EINVAL for another face kind or bad arguments. */
+int fluid_wall_fluxes(fluid_solver* s, const double* U_dev, int axis, int side, double* qw_dev,
+                      double* tw_dev, void* stream);
+
 /* Synchronise `stream` and read the solver time and the last step's dt (either may be NULL). */
 int fluid_get_time(fluid_solver* s, double* t, double* last_dt, void* stream);
 

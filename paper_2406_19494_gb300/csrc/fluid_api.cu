@@ -865,6 +865,22 @@ int fluid_adjoint_step(fluid_solver* s, const double* Un_dev, const double* U1_d
   return FLUID_OK;
 }
 
+int fluid_wall_fluxes(fluid_solver* s, const double* U_dev, int axis, int side, double* qw_dev,
+                      double* tw_dev, void* stream) {
+  if (!s) return FLUID_EINVAL;
+  if (int r = check_ptr(s, U_dev, "U_dev")) return r;
+  if (!qw_dev && !tw_dev) return fail(s, FLUID_EINVAL, "qw_dev and tw_dev are both NULL");
+  if (axis < 0 || axis >= s->geo.ndim || side < 0 || side > 1 || s->geo.ndim < 2)
+    return fail(s, FLUID_EINVAL, "bad wall face");
+  const int kind = s->bc.kind[axis][side];
+  if (kind != FLUID_BC_WALL && kind != FLUID_BC_POROUS)
+    return fail(s, FLUID_EINVAL, "wall fluxes need an isothermal or porous face");
+  cudaStream_t st = as_stream(stream);
+  FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
+  FL_CUDA(s, fl::launch_wall_fluxes(s->W, qw_dev, tw_dev, s->geo, s->ph, axis, side, s->bc.Tw[axis][side], st));
+  return FLUID_OK;
+}
+
 int fluid_wall_heat_loss(fluid_solver* s, const double* U_dev, int axis, int side, double* J_dev,
                          double* dJdU_dev, void* stream) {
   if (!s) return FLUID_EINVAL;

@@ -185,6 +185,8 @@ int wall_loss_parts(const Geo& g, int A);
 cudaError_t launch_wall_loss(const double* W, double* part, int nparts, double* J, double* gT2,
                              const Geo& g, const Phys& ph, int A, int side, double Tw,
                              cudaStream_t st);
+cudaError_t launch_wall_fluxes(const double* W, double* qw, double* tw, const Geo& g, const Phys& ph,
+                               int A, int side, double Tw, cudaStream_t st);
 cudaError_t launch_wall_loss_grad(const double* U, const double* gT2, double* dJdU, const Geo& g,
                                   const Phys& ph, int A, int side, cudaStream_t st);
 cudaError_t launch_lincomb(double* out, double c0, const double* x0, double c1, const double* x1,

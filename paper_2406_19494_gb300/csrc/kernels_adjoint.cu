@@ -447,6 +447,34 @@ __global__ void k_wall_loss(const double* __restrict__ W, double* __restrict__ p
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
 
+// Per wall cell of face (A, side): q_w = -lambda(T_w) dT/dn and tau_w = mu(T_w) du_t1/dn by the
+// fourth-order face stencil through the mirrored ghost cells (T_g = 2 T_w - T, u_g = -u), which in
+// the two wall-adjacent interior cells reads (54 f_0 - 2 f_1 - 52 f_w) / 24 * (d index / dn)
+__global__ void k_wall_fluxes(const double* __restrict__ W, double* __restrict__ qw,
+                              double* __restrict__ tw, Geo g, int A, int side, double Tw,
+                              double mu_w, double lam_w) {
+  const int t1 = A == 0 ? 1 : 0, t2 = 3 - A - t1;
+  const int n1 = g.n[t1], n2 = g.n[t2];
+  const int total = n1 * n2;
+  const int s = stride_of(g, A);
+  const int a0 = side == 0 ? g.h[A] : g.h[A] + g.n[A] - 1;
+  const int a1 = side == 0 ? a0 + 1 : a0 - 1;
+  const int af = side == 0 ? g.h[A] - 1 : g.h[A] + g.n[A] - 1;
+  const double m = (side == 0 ? 1.0 : -1.0) * k24th * g.mf[A][af];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int c[3];
+    c[t1] = g.h[t1] + t % n1;
+    c[t2] = g.h[t2] + t / n1;
+    c[A] = a0;
+    const int cell = c[0] + c[1] * g.sy + c[2] * g.sz;
+    const int cell1 = cell + (a1 - a0) * s;
+    const double T0 = W[5 * g.ncell + cell], T1 = W[5 * g.ncell + cell1];
+    const double u0 = W[(1 + t1) * g.ncell + cell], u1 = W[(1 + t1) * g.ncell + cell1];
+    if (qw) qw[t] = -lam_w * ((54.0 * T0 - 2.0 * T1 - 52.0 * Tw) * m);
+    if (tw) tw[t] = mu_w * ((54.0 * u0 - 2.0 * u1) * m);
+  }
+}
+
 __global__ void k_sum_parts(const double* __restrict__ part, int n, double* __restrict__ out) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double s = 0.0;
@@ -634,6 +662,16 @@ cudaError_t launch_wall_loss(const double* W, double* part, int nparts, double* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   (k_sum_parts<<<1, 32, 0, st>>>(part, nparts, J), ++t_launches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wall_fluxes(const double* W, double* qw, double* tw, const Geo& g, const Phys& ph,
+                               int A, int side, double Tw, cudaStream_t st) {
+  const int t1 = A == 0 ? 1 : 0, t2 = 3 - A - t1;
+  const long long total = (long long)g.n[t1] * g.n[t2];
+  const double mu_w = viscosity(Tw, ph);
+  (k_wall_fluxes<<<grid_for(total, 128), 128, 0, st>>>(W, qw, tw, g, A, side, Tw, mu_w, mu_w * ph.lam_fac),
+   ++t_launches);
   return cudaGetLastError();
 }
 

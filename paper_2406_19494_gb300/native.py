@@ -41,6 +41,7 @@ SIGNATURES = {
     "fluid_adjoint_rhs": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fluid_adjoint_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fluid_wall_heat_loss": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "fluid_wall_fluxes": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "fluid_halo_count": (_i, [_vp, _i, ctypes.POINTER(_sz)]),
     "fluid_pack_halo": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "fluid_unpack_halo": (_i, [_vp, _vp, _i, _i, _vp, _vp]),

@@ -152,6 +152,18 @@ class Solver:
                                                   ctypes.c_void_p(J.data_ptr()), _ptr(dJ), _stream(stream)))
         return (J, dJ) if grad else J
 
+    def wall_fluxes(self, U, axis, side, stream=None):
+        """(q_w, tau_w) per wall cell of the isothermal or porous face (axis, side), shaped
+        [n_t2, n_t1] (fluid_wall_fluxes)."""
+        t1 = 1 if axis == 0 else 0
+        t2 = 3 - axis - t1
+        n = self.case["n"]
+        qw = torch.zeros((n[t2], n[t1]), dtype=torch.float64, device="cuda")
+        tw = torch.zeros_like(qw)
+        self._check(self.lib.fluid_wall_fluxes(self.handle, self._state(U), int(axis), int(side),
+                                               _ptr(qw), _ptr(tw), _stream(stream)))
+        return qw, tw
+
     def time(self, stream=None):
         t, dt = ctypes.c_double(), ctypes.c_double()
         self._check(self.lib.fluid_get_time(self.handle, ctypes.byref(t), ctypes.byref(dt), _stream(stream)))

@@ -448,3 +448,31 @@ def test_longest_axis_one_dimensional():
     scale = np.max(np.abs(ref), axis=0)
     scale = np.where(scale > 0, scale, 1.0)
     assert np.all(np.max(np.abs(got - ref), axis=0) / scale <= TOL)
+
+
+@pytest.mark.parametrize("name", ["channel3d_walls_force", "bl2d_porous_inflow"])
+def test_wall_fluxes_parity(name):
+    """fluid_wall_fluxes (wall heat flux and wall shear per wall cell) against the oracle's
+    wall_fluxes at 1e-12 of their largest magnitude, on the isothermal / porous faces."""
+    c = CASES[name]()
+    case, grid, U = padded_state(c, seed=9)
+    s = Solver(c)
+    phi = None
+    inflow = inflows(c, case, grid)
+    for (a, sd), prof in inflow.items():
+        s.set_inflow(a, sd, torch.from_numpy(np.ascontiguousarray(prof)).cuda())
+    if c.get("porous"):
+        phi = wl.porous_phi(c, seed=3)
+        s.set_wall_params(torch.from_numpy(phi).cuda())
+    Ud = torch.from_numpy(U).cuda()
+    faces = [(a, sd) for a in range(case.ndim) for sd in range(2) if case.bc[a][sd] in ("wall", "porous")]
+    assert faces
+    for a, sd in faces:
+        qw, tw = s.wall_fluxes(Ud, a, sd)
+        q_ref, t_ref = nf.wall_fluxes(U.copy(), case, grid, a, sd, phi, inflow)
+        q_ref = np.squeeze(q_ref)
+        t_ref = np.squeeze(t_ref)
+        got_q, got_t = np.squeeze(qw.cpu().numpy()), np.squeeze(tw.cpu().numpy())
+        assert got_q.shape == q_ref.shape
+        assert np.max(np.abs(got_q - q_ref)) <= TOL * np.max(np.abs(q_ref)), (a, sd)
+        assert np.max(np.abs(got_t - t_ref)) <= TOL * np.max(np.abs(t_ref)), (a, sd)
