@@ -913,19 +913,60 @@ def ctypes_peak(s, kind):
 SLAB = 8   # interior z-planes of the sample
 
 
-def _oracle_sample(case_dict):
+def _oracle_sample(case_dict, k=0):
+    """The oracle's view of z-slab k (SLAB interior planes with their halos, cut from the filled
+    whole-domain state, wrapping around the periodic z axis), as an already filled block with the
+    slab's own z extent."""
     from oracle import ns_fv as nf
     case = nf.Case(case_dict)
     grid = nf.Grid(case)
     cen = [grid.axes[a].xc[3:-3] for a in range(3)]
     W = np.pad(initial_prims(case_dict, cen), [(0, 0)] + [(3, 3)] * 3, mode="edge")
     U = nf.fill_halos(nf.prim_to_cons(W, case), case, grid)
-    # a z-slab of SLAB interior planes with its halos, treated as an already filled block
-    sub = dict(case_dict, n=(case.n[0], case.n[1], SLAB))
+    nz = case.n[2]
+    z0 = (k * SLAB) % nz
+    idx = [(z0 + j) % nz + 3 for j in range(-3, SLAB + 3)]
+    lo, hi = case_dict["lo"][2], case_dict["hi"][2]
+    dz = (hi - lo) / nz
+    sub = dict(case_dict, n=(case.n[0], case.n[1], SLAB), lo=case_dict["lo"][:2] + (lo + z0 * dz,),
+               hi=case_dict["hi"][:2] + (lo + (z0 + SLAB) * dz,))
     sc = nf.Case(sub)
     sg = nf.Grid(sc)
-    Us = np.ascontiguousarray(U[:, 0:SLAB + 6])
+    Us = np.ascontiguousarray(U[:, idx])
     return nf, sc, sg, Us
+
+
+def _oracle_slab_worker(k, case_dict, reps, warm, barrier, queue):
+    """One process of the all-core oracle timing: its own slab, `warm` then `reps` steps' work
+    (three right-hand sides each) after every process has built its slab; reports wall times."""
+    nf, sc, sg, Us = _oracle_sample(case_dict, k)
+    for _ in range(warm):
+        nf.rhs_filled(Us, sc, sg)
+    barrier.wait()
+    t0 = time.time()
+    for _ in range(reps):
+        for _stage in range(3):
+            nf.rhs_filled(Us, sc, sg)
+    queue.put((t0, time.time(), sc.n[0] * sc.n[1] * sc.n[2]))
+
+
+def oracle_all_cores(case_dict, reps, warm=1, cores=None):
+    """The oracle on every host core: one process per core (started with spawn), each advancing
+    its own z-slab; (cell-updates/s over the makespan, cores, cells per step, seconds per step)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_slab_worker, args=(k, case_dict, reps, warm, barrier, queue))
+             for k in range(cores)]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    span = max(r[1] for r in res) - min(r[0] for r in res)
+    cells = sum(r[2] for r in res)
+    return cells * reps / span, cores, cells, span / reps
 
 
 def host_cpu():
@@ -944,6 +985,7 @@ def host_cpu():
 
 
 def cpu_baseline(args, case_dict, samples=1):
+    """The oracle on every host core (the reported value) and on one (beside it)."""
     nf, sc, sg, Us = _oracle_sample(case_dict)
     cells = sc.n[0] * sc.n[1] * sc.n[2]
     t0 = time.perf_counter()
@@ -951,9 +993,14 @@ def cpu_baseline(args, case_dict, samples=1):
         for _stage in range(3):
             nf.rhs_filled(Us, sc, sg)
     dt = (time.perf_counter() - t0) / samples
-    return dict({"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                 "sample": "3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the "
-                           "same state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2])}, **host_cpu())
+    value, cores, cells_all, s_step = oracle_all_cores(case_dict, reps=samples)
+    return dict({"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                 "sample": "3 oracle right-hand sides (one RK3 step's work) per process, one process per "
+                           "host core, each on its own %dx%dx%d z-slab of the same state (%d cells in "
+                           "all); numpy, spawned processes" % (sc.n[0], sc.n[1], SLAB, cells_all),
+                 "single_core": {"value": cells / dt, "cores": 1,
+                                 "sample": "the same work on one %dx%dx%d slab, one thread"
+                                           % (sc.n[0], sc.n[1], sc.n[2])}}, **host_cpu())
 
 
 def run_reference(args):
@@ -961,25 +1008,16 @@ def run_reference(args):
     if rank != 0:
         return
     case = WORKLOADS[args.workload]()
-    nf, sc, sg, Us = _oracle_sample(case)
-    cells = sc.n[0] * sc.n[1] * sc.n[2]
-    for _ in range(args.warmup):
-        nf.rhs_filled(Us, sc, sg)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for _stage in range(3):
-            nf.rhs_filled(Us, sc, sg)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = cells * args.steps / total
-    sample = ("each step: 3 oracle right-hand sides (one RK3 step's work) of a %dx%dx%d slab of the "
-              "%s state; numpy, single thread" % (sc.n[0], sc.n[1], sc.n[2], args.workload))
+    value, cores, cells, s_step = oracle_all_cores(case, reps=args.steps, warm=args.warmup)
+    total = s_step * args.steps
+    sample = ("each step: 3 oracle right-hand sides (one RK3 step's work) per process, one process per "
+              "host core, each on its own %dx%dx%d z-slab of the %s state (%d cells in all); numpy"
+              % (case["n"][0], case["n"][1], SLAB, args.workload, cells))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": describe(args.workload, case), "impl": "reference",
-           "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
                                 **host_cpu()),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
