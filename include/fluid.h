@@ -283,9 +283,11 @@ int fluid_check(fluid_solver* s, void* stream);
  * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8/4
  * that still fills the GPU), for every axis (fluid_autotune_faces picks one per axis).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
  * tiles of 2 warps (block 64) or 4 warps (otherwise) by default; seg < 0 selects the register-window
- * marching kernels with |seg| cells per segment and `block` threads instead.  FP64 results and
- * those of the two mixed tiles are bitwise the same for every shape; the mixed register-window
- * kernels agree with the tiles to FP32 rounding. */
+ * marching kernels with |seg| cells per segment and `block` threads instead.  With the tiles,
+ * fluid_step folds each RK3 stage (and the primitives of its result) into the last axis's tile
+ * kernel, with the same arithmetic as the separate stage kernel.  FP64 results and those of the two
+ * mixed tiles are bitwise the same for every shape; the mixed register-window kernels agree with
+ * the tiles to FP32 rounding. */
 int fluid_tune_faces(fluid_solver* s, int block, int seg);
 
 /* Time the FP64 face kernels (blocks of 128 threads with segments of 8 to 32 cells and the
@@ -342,6 +344,12 @@ int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* sqrt_dev, d
  * lib[i] = exp(e log x[i]) (CUDA's library), for n device values.  For tests. */
 int fluid_check_pow(const double* x_dev, double* fast_dev, double* lib_dev, int n, double e,
                     void* stream);
+
+
+/* Check of the FP32 -> FP64 widening the mixed face kernels build from the bit fields with integer
+ * operations: bits[i] = that widening of x[i], cvt[i] = the conversion instruction's result, for n
+ * device values.  For tests. */
+int fluid_check_widen(const float* x_dev, double* bits_dev, double* cvt_dev, int n, void* stream);
 
 
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fluid_internal.cuh"
@@ -52,6 +53,8 @@ struct fluid_solver {
   bool mixed = false;              // FLUID_PREC_MIXED: FP32 fluxes, FP64 state
   bool exchange = false;           // some face is FLUID_BC_EXCHANGE (a block of a decomposition)
   float* W32 = nullptr;            // FP32 (hi, lo) primitives, 2 NW * ncell (mixed)
+  double* Wb = nullptr;            // mixed: the second pair of primitive buffers (W with its H row,
+  float* W32b = nullptr;           // W32), written by a stage fused into the last face kernel
   float* mf32 = nullptr;           // FP32 face metrics of the three axes (mixed)
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
@@ -350,6 +353,31 @@ int stage_prim_into(fluid_solver* s, int stage, const double* Un, const double* 
   return FLUID_OK;
 }
 
+// Mixed path, one RK3 stage from the primitives of its input (in W / W32): the face kernels of the
+// axes before the last into R, then the last axis's face kernel fused with the stage combination
+// into Ud and the primitives of Ud into the second buffer pair (prims), whose halo cells follow;
+// the pairs then swap, so W / W32 hold the primitives of Ud.  Without prims (the last stage of a
+// call) only Ud is written.
+int stage_fused_into(fluid_solver* s, int stage, const double* Un, const double* Us, double* Ud,
+                     bool prims, double t_end, cudaStream_t st) {
+  const Geo& g = s->geo;
+  if (s->ph.visc != FLUID_VISC_NONE)
+    FL_TIMED(s, FLUID_KERNEL_GRAD, st, fl::launch_grad32(s->W32, s->G32, g, st));
+  for (int d = 0; d + 1 < g.ndim; ++d)
+    FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
+             fl::launch_face_mixed(d, s->W, s->W32, s->G32, s->R, g, s->ph, d > 0, s->face_block,
+                                   s->face_seg, st));
+  const fl::StageOut so{stage, prims ? 1 : 0, Un, Us, Ud, s->Wb, s->W32b, s->ctl, t_end};
+  FL_TIMED(s, FLUID_KERNEL_FACE_X + g.ndim - 1, st,
+           fl::launch_face_mixed_stage(s->W, s->W32, s->G32, s->R, g, s->ph, s->face_block, so, st));
+  if (prims) {
+    FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_halo_prim(s->Wb, s->W32b, g, s->ph, s->bc, s->ctl, st));
+    std::swap(s->W, s->Wb);
+    std::swap(s->W32, s->W32b);
+  }
+  return FLUID_OK;
+}
+
 // (dR/dX)^T mu on the interior into gX; (dR/dphi)^T mu added to gphi when given.  Wx / Gx: the
 // primitives and gradients of X when already formed (else computed into the solver's W / G).
 int rhs_vjp(fluid_solver* s, const double* X, const double* mu, double* gX, double* gphi,
@@ -511,6 +539,8 @@ int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
     return bail(e, "cudaMalloc W");
   if (s->mixed) {
     if ((e = al.malloc((void**)&s->W32, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    if ((e = al.malloc((void**)&s->Wb, (fl::NW + 1) * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wb");
+    if ((e = al.malloc((void**)&s->W32b, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32b");
     if ((e = al.malloc((void**)&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
     if (c.visc_law != FLUID_VISC_NONE)
       if ((e = al.malloc((void**)&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
@@ -667,6 +697,8 @@ void fluid_destroy(fluid_solver* s) {
   al.free(s->W);
   al.free(s->G);
   al.free(s->W32);
+  al.free(s->Wb);
+  al.free(s->W32b);
   al.free(s->mf32);
   al.free(s->G32);
   for (double* p : {s->gW, s->gG, s->CW, s->CG, s->S1, s->S2, s->MU, s->L1, s->L2, s->GT, s->gvw,
@@ -771,7 +803,16 @@ int fluid_step(fluid_solver* s, double* U_dev, int nsteps, double t_end, void* s
   // and the call's last stage, whose primitives nothing reads, is the plain combination.
   if (nsteps > 0)
     FL_TIMED(s, FLUID_KERNEL_PRIM_BC, st, fl::launch_prim_bc(U_dev, s->W, s->W32, s->geo, s->ph, s->bc, s->ctl, st));
+  // the mixed path on the y / z tile kernels folds each stage into the last axis's face kernel
+  const bool fused = s->mixed && fl::mixed_stage_fusable(s->geo, s->face_seg);
   for (int k = 0; k < nsteps; ++k) {
+    if (fused) {
+      if (int r = dt_into(s, nullptr, 1, t_end, st)) return r;
+      if (int r = stage_fused_into(s, 1, U_dev, U_dev, s->A, true, t_end, st)) return r;
+      if (int r = stage_fused_into(s, 2, U_dev, s->A, s->A, true, t_end, st)) return r;
+      if (int r = stage_fused_into(s, 3, U_dev, s->A, U_dev, k + 1 < nsteps, t_end, st)) return r;
+      continue;
+    }
     // stage 1: U1 = Un + dt R(Un) into A; dt from the primitives of Un
     if (int r = dt_into(s, nullptr, 1, t_end, st)) return r;
     if (int r = grad_faces(s, s->R, st)) return r;

@@ -66,6 +66,24 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
 }
 
+// Split x = hi + lo + r with |r| <= 2^-48 |x|, using integer operations only: hi keeps the sign,
+// the exponent and the leading 23 fraction bits of x (x truncated to FP32 precision, exact), lo the
+// remaining 29 fraction bits rounded to FP32.  Below 2^-73 lo is dropped (|r| < 2^-23 |x| <
+// 1.2e-29), below 2^-126 both are zero; |x| >= 2^128 or a non-finite x gives NaN, which the
+// non-finite check then reports.
+__device__ __forceinline__ void split_hi_lo(double x, float& hi, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);            // biased FP64 exponent
+  if (e < 1023 - 126) { hi = __int_as_float(sign); lo = 0.0f; return; }
+  if (e > 1023 + 127) { hi = __int_as_float(0x7fc00000); lo = hi; return; }
+  hi = __int_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // lo = (low 29 fraction bits) * 2^(e - 1075), with 2^(e - 1075) a normal float when e > 948
+  const int es = e - 1075 + 127;
+  const float m = (float)(lw & 0x1fffffffu);
+  lo = es > 0 ? __int_as_float(sign | __float_as_int(m * __int_as_float(es << 23))) : 0.0f;
+}
+
 __host__ __device__ __forceinline__ double viscosity(double T, const Phys& ph) {
   if (ph.visc == FLUID_VISC_CONSTANT) return ph.mu_ref;
   const double r = T * ph.iT_ref;
@@ -152,6 +170,10 @@ cudaError_t launch_stage(int stage, const double* Un, const double* Us, const do
 cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, const double* R,
                               double* Ud, double* W, float* W32, const Geo& g, const Phys& ph,
                               const BC& bc, Ctl* ctl, double t_end, cudaStream_t st);
+// the halo cells of W (and W32 / H when W32 is given) from its interior, as launch_stage_prim's
+// second pass
+cudaError_t launch_halo_prim(double* W, float* W32, const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
+                             cudaStream_t st);
 cudaError_t launch_dt_partial(const double* W, const Geo& g, const Phys& ph, double* partial,
                               int nparts, cudaStream_t st);
 cudaError_t launch_dt_final(const double* partial, int nparts, const Phys& ph, Ctl* ctl,
@@ -165,6 +187,29 @@ cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R,
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,
                               cudaStream_t st);
+// Stage output of the last axis's face kernel when the stage is fused into it: Ud = stage `stage`
+// of RK3 from Un, Us and the completed right-hand side, and the primitives of Ud (W: NW rows and
+// the H row; W32: the split) written to a second buffer pair, since the kernel still reads the
+// current one.  prims = false (the last stage of a call) writes Ud only.
+struct StageOut {
+  int stage;
+  int prims;
+  const double* Un;
+  const double* Us;
+  double* Ud;
+  double* W;
+  float* W32;
+  Ctl* ctl;
+  double t_end;
+};
+// whether launch_face_mixed_stage can take the last axis of this grid (the y / z tile kernels)
+bool mixed_stage_fusable(const Geo& g, int seg);
+// the face kernel of the last axis (ndim - 1) accumulating into R's values of the other axes,
+// fused with the stage combination and the primitives of its result (interior cells; the halo
+// cells of the new buffer follow with launch_halo_prim)
+cudaError_t launch_face_mixed_stage(const double* W, const float* W32, const float* G32,
+                                    const double* R, const Geo& g, const Phys& ph, int block,
+                                    const StageOut& so, cudaStream_t st);
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st);
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
                                 int nparts, cudaStream_t st);

@@ -146,24 +146,6 @@ __device__ __forceinline__ bool prim_cell(const double* __restrict__ U, const in
   return halo_maps(own, ghost, side, src, g, ph, bc, ctl, w);
 }
 
-// Split x = hi + lo + r with |r| <= 2^-48 |x|, using integer operations only: hi keeps the sign,
-// the exponent and the leading 23 fraction bits of x (x truncated to FP32 precision, exact), lo the
-// remaining 29 fraction bits rounded to FP32.  Below 2^-73 lo is dropped (|r| < 2^-23 |x| <
-// 1.2e-29), below 2^-126 both are zero; |x| >= 2^128 or a non-finite x gives NaN, which the
-// non-finite check then reports.
-__device__ __forceinline__ void split_hi_lo(double x, float& hi, float& lo) {
-  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
-  const unsigned sign = hw & 0x80000000u;
-  const int e = (int)((hw >> 20) & 0x7ffu);            // biased FP64 exponent
-  if (e < 1023 - 126) { hi = __int_as_float(sign); lo = 0.0f; return; }
-  if (e > 1023 + 127) { hi = __int_as_float(0x7fc00000); lo = hi; return; }
-  hi = __int_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
-  // lo = (low 29 fraction bits) * 2^(e - 1075), with 2^(e - 1075) a normal float when e > 948
-  const int es = e - 1075 + 127;
-  const float m = (float)(lw & 0x1fffffffu);
-  lo = es > 0 ? __int_as_float(sign | __float_as_int(m * __int_as_float(es << 23))) : 0.0f;
-}
-
 // One thread per padded cell: x from the thread index, y and z from the block index.
 // MIXED: the primitives also go to W32 = [2 NW][ncell] floats as the split (hi, lo) above, and
 // H = E + p to the FP64 row W[NW]; the FP32 face kernels form their cell differences from the pairs.
@@ -1155,6 +1137,11 @@ cudaError_t launch_stage_prim(int stage, const double* Un, const double* Us, con
   else (k_stage_prim<false><<<grid, block, 0, st>>>(stage, Un, Us, R, Ud, W, W32, g, ph, ctl, t_end), ++t_launches);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_halo_prim(W, W32, g, ph, bc, ctl, st);
+}
+
+cudaError_t launch_halo_prim(double* W, float* W32, const Geo& g, const Phys& ph, const BC& bc, Ctl* ctl,
+                             cudaStream_t st) {
   const long long total = (long long)g.p[0] * g.p[1] * g.p[2] - (long long)g.n[0] * g.n[1] * g.n[2];
   if (total <= 0) return cudaSuccess;
   if (W32) (k_halo_prim<true><<<grid_for(total, 256), 256, 0, st>>>(W, W32, g, ph, bc, ctl, total), ++t_launches);

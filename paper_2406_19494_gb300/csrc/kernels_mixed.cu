@@ -23,6 +23,7 @@
 //     FP64 path (each face value is computed once and shared by its two cells).
 #include <cuda_runtime.h>
 
+#include "flux_math.cuh"
 #include "fluid_internal.cuh"
 
 namespace fl {
@@ -265,18 +266,18 @@ __device__ __forceinline__ void face_flux_mixed(const MixedIn& in, int cell, int
     X[4] -= vf[0] * tau[0] + vf[1] * tau[1] + vf[2] * tau[2] + lam * dT;
   }
 
-  // FP64 cell-centre Euler flux of q_a plus the FP32 change
+  // FP64 cell-centre Euler flux of q_a plus the FP32 change (widened on the integer pipe)
   const double* W = in.W;
   const double r = W[cell], u0 = W[nc + cell], u1 = W[2 * nc + cell], u2 = W[3 * nc + cell];
   const double p = W[4 * nc + cell], H = W[NW * nc + cell];
   const double un = D == 0 ? u0 : (D == 1 ? u1 : u2);
   const double mn = r * un;
-  F[0] = mn + (double)X[0];
-  F[1] = fma(mn, u0, (double)X[1]);
-  F[2] = fma(mn, u1, (double)X[2]);
-  F[3] = fma(mn, u2, (double)X[3]);
+  F[0] = mn + fl_widen(X[0]);
+  F[1] = fma(mn, u0, fl_widen(X[1]));
+  F[2] = fma(mn, u1, fl_widen(X[2]));
+  F[3] = fma(mn, u2, fl_widen(X[3]));
   F[1 + D] += p;
-  F[4] = fma(un, H, (double)X[4]);
+  F[4] = fma(un, H, fl_widen(X[4]));
 }
 
 // R_v (+)= -(F_v - Fp_v) / dx in FP64
@@ -288,6 +289,57 @@ __device__ __forceinline__ void divergence(double* __restrict__ R, int nc, int c
     double* dst = R + v * nc + cell;
     *dst = accumulate ? fma(-id, dF, *dst) : -id * dF;
   }
+}
+
+// The stage of one interior cell once its right-hand side is complete: R_v = its value from the
+// other axes' kernels minus this axis's flux difference (the FP64 accumulation of divergence()),
+// then the arithmetic of k_stage_prim -- body force, the RK3 combination into Ud, the primitives of
+// Ud, their split and H = E + p -- into the second buffer pair.  Wold: the current primitives (the
+// body-force velocities of the stage's input state).
+__device__ __forceinline__ void stage_cell(const StageOut& so, const double* __restrict__ R,
+                                           const double* __restrict__ Wold, int nc, int cell, double id,
+                                           const double F[5], const double Fp[5], double dt, bool hold,
+                                           const Phys& ph, bool& bad) {
+  double u[5];
+  if (hold) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = so.Un[v * nc + cell];
+  } else {
+    double r[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] = fma(-id, F[v] - Fp[v], R[v * nc + cell]);
+    if (ph.has_force) {
+      const double vx = Wold[nc + cell], vy = Wold[2 * nc + cell], vz = Wold[3 * nc + cell];
+      r[1] += ph.f[0];
+      r[2] += ph.f[1];
+      r[3] += ph.f[2];
+      r[4] += fma(ph.f[0], vx, fma(ph.f[1], vy, ph.f[2] * vz));
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double un = so.Un[v * nc + cell];
+      double out;
+      if (so.stage == 1) {
+        out = fma(dt, r[v], un);
+      } else {
+        const double us = so.Us[v * nc + cell];
+        out = so.stage == 2 ? fma(0.75, un, 0.25 * fma(dt, r[v], us))
+                            : fma(1.0 / 3.0, un, (2.0 / 3.0) * fma(dt, r[v], us));
+      }
+      bad |= !finite_bits(out);
+      so.Ud[v * nc + cell] = out;
+      u[v] = out;
+    }
+  }
+  if (!so.prims) return;
+  double w[NW];
+  prim_from_cons(u, ph, w);
+#pragma unroll
+  for (int v = 0; v < NW; ++v) {
+    so.W[v * nc + cell] = w[v];
+    split_hi_lo(w[v], so.W32[v * nc + cell], so.W32[(NW + v) * nc + cell]);
+  }
+  so.W[NW * nc + cell] = u[4] + w[4];
 }
 
 template <int D, int SCHEME, bool VISC>
@@ -412,10 +464,10 @@ constexpr size_t t_smem() {
   return sizeof(float) * 6 * (FPW * NWARP + 4) * 32 + sizeof(double) * NWARP * 5 * 32;
 }
 
-template <int D, int SCHEME, bool VISC, int NWARP, int FPW>
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW, bool STAGE = false>
 __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restrict__ R,
                                                                        Geo g, PhysF pf, int accumulate,
-    uint3 bid, uint3 gdim) {
+    uint3 bid, uint3 gdim, const StageOut* sop = nullptr, const Phys* php = nullptr) {
   static_assert(D == 1 || D == 2, "tiles along y or z");
   constexpr int kTFaces = FPW;
   constexpr int kTCells = kTFaces * NWARP - 1;
@@ -437,6 +489,17 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
   const int so = OTHER == 1 ? g.sy : g.sz;
   const int nc = g.ncell;
   const int colbase = x + o * so;                           // cell index with D coordinate 0
+  // fused stage: dt of the step, the third stage's hold (dt <= 0) and its clock update
+  double dt = 0.0;
+  bool hold = false, bad = false;
+  if (STAGE) {
+    dt = sop->ctl->dt;
+    hold = sop->stage == 3 && !(dt > 0.0);
+    if (sop->stage == 3 && !hold && bid.x == 0 && bid.y == 0 && bid.z == 0 && lane == 0 && warp == 0) {
+      const double tn = sop->ctl->t + dt;
+      sop->ctl->t = (sop->t_end > 0.0 && !(tn < sop->t_end)) ? sop->t_end : tn;
+    }
+  }
   for (int k = warp; k < ND; k += kTWarps) {
     const int j = d0 - 3 + k;
     const bool ok = xok && j + 1 <= dend + 2;
@@ -460,6 +523,8 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
     if (f == f0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) sF[warp][v][lane] = F[v];
+    } else if (STAGE) {
+      stage_cell(*sop, R, in.W, nc, colbase + a * s, g.idx[D][a], F, Fp, dt, hold, *php, bad);
     } else {
       divergence(R, nc, colbase + a * s, g.idx[D][a], F, Fp, accumulate);   // cell a, faces a -+ 1/2
     }
@@ -473,14 +538,24 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
     double F[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] = sF[warp + 1][v][lane];
-    divergence(R, nc, colbase + a * s, g.idx[D][a], F, Fp, accumulate);
+    if (STAGE) stage_cell(*sop, R, in.W, nc, colbase + a * s, g.idx[D][a], F, Fp, dt, hold, *php, bad);
+    else divergence(R, nc, colbase + a * s, g.idx[D][a], F, Fp, accumulate);
   }
+  if (STAGE && bad) atomicOr(&sop->ctl->flags, FLAG_NONFINITE);
 }
 
 template <int D, int SCHEME, bool VISC, int NWARP, int FPW>
 __global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn in, double* __restrict__ R,
                                                                        Geo g, PhysF pf, int accumulate) {
   k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW>(in, R, g, pf, accumulate, blockIdx, gridDim);
+}
+
+// the last axis's tile kernel with the stage fused (StageOut): R is read, not written
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW, int MINB>
+__global__ void __launch_bounds__(32 * NWARP, MINB) k_face_mixed_ts(MixedIn in, const double* __restrict__ R,
+                                                                    Geo g, PhysF pf, StageOut so, Phys ph) {
+  k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW, true>(in, const_cast<double*>(R), g, pf, 1, blockIdx,
+                                                         gridDim, &so, &ph);
 }
 
 
@@ -702,7 +777,55 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
   return launch_tile<SCHEME, VISC, 4, 4>(D, in, R, g, pf, accumulate, st);
 }
 
+template <int SCHEME, bool VISC, int NWARP, int FPW, int MINB>
+cudaError_t launch_tile_stage(int D, const MixedIn& in, const double* R, const Geo& g, const PhysF& pf,
+                              const Phys& ph, const StageOut& so, cudaStream_t st) {
+  constexpr int cells = FPW * NWARP - 1;
+  constexpr size_t smem = t_smem<NWARP, FPW>();
+  const int other = D == 1 ? 2 : 1;
+  const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + cells - 1) / cells, g.n[other]);
+  if (D == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
+  }
+  return cudaGetLastError();
+}
+
+template <int SCHEME, bool VISC>
+cudaError_t launch_stage_sv(const MixedIn& in, const double* R, const Geo& g, const PhysF& pf, const Phys& ph,
+                            int block, const StageOut& so, cudaStream_t st) {
+  const int D = g.ndim - 1;
+  if (block == 64) return launch_tile_stage<SCHEME, VISC, 2, 4, 12>(D, in, R, g, pf, ph, so, st);
+  return launch_tile_stage<SCHEME, VISC, 4, 4, 6>(D, in, R, g, pf, ph, so, st);
+}
+
 }  // namespace
+
+bool mixed_stage_fusable(const Geo& g, int seg) {
+  if (g.ndim < 2 || seg < 0) return false;
+  const int other = g.ndim - 1 == 1 ? 2 : 1;
+  return g.n[other] <= 65535;
+}
+
+cudaError_t launch_face_mixed_stage(const double* W, const float* W32, const float* G32,
+                                    const double* R, const Geo& g, const Phys& ph, int block,
+                                    const StageOut& so, cudaStream_t st) {
+  const bool visc = ph.visc != FLUID_VISC_NONE;
+  const MixedIn in{W, W32, W32 + (size_t)NW * g.ncell, G32};
+  const PhysF pf = phys_f(ph);
+  if (ph.weno == FLUID_WENO_JS)
+    return visc ? launch_stage_sv<FLUID_WENO_JS, true>(in, R, g, pf, ph, block, so, st)
+                : launch_stage_sv<FLUID_WENO_JS, false>(in, R, g, pf, ph, block, so, st);
+  return visc ? launch_stage_sv<FLUID_WENO_Z, true>(in, R, g, pf, ph, block, so, st)
+              : launch_stage_sv<FLUID_WENO_Z, false>(in, R, g, pf, ph, block, so, st);
+}
 
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,

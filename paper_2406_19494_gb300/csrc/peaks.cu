@@ -104,6 +104,25 @@ extern "C" int fluid_check_sqrt(const double* y_dev, double* rsqrt_dev, double* 
   return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
 }
 
+namespace {
+__global__ void k_check_widen(const float* __restrict__ x, double* __restrict__ bits,
+                              double* __restrict__ cvt, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bits[i] = fl::fl_widen(x[i]);
+    cvt[i] = (double)x[i];
+  }
+}
+}  // namespace
+
+extern "C" int fluid_check_widen(const float* x_dev, double* bits_dev, double* cvt_dev, int n,
+                                 void* stream) {
+  if (!x_dev || !bits_dev || !cvt_dev || n < 0) return FLUID_EINVAL;
+  if (n == 0) return FLUID_OK;
+  k_check_widen<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0,
+                  reinterpret_cast<cudaStream_t>(stream)>>>(x_dev, bits_dev, cvt_dev, n);
+  return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
+}
+
 extern "C" int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n,
                                void* stream) {
   if (!y_dev || !fast_dev || !ieee_dev || n < 0) return FLUID_EINVAL;

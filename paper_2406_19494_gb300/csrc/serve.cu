@@ -107,9 +107,11 @@ size_t footprint(const fluid_config& c) {
   }
   const bool visc = c.visc_law != FLUID_VISC_NONE;
   size_t b = 8 * (nc * (fl::NW + 3 * fl::NV) + metric + 4096);   // W, A, R, the state U, metrics
-  // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients and face metrics
+  // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients and face metrics, and the
+  // second pair of primitive buffers (W with its H row, W32)
   if (c.precision == FLUID_PREC_MIXED) {
     b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
+    b += 8 * nc * (fl::NW + 1) + 4 * nc * 2 * fl::NW;
   } else {
     if (visc) b += 8 * nc * fl::NG;
     // seam buffer of the face kernels: 10 doubles per segment of kSeamMinSeg cells, on the axis

@@ -108,3 +108,32 @@ def test_power_law_within_a_few_ulp(e):
         assert np.max(np.abs(f[near] - l[near]) / np.spacing(l[near])) <= 3.0
     # elsewhere the library expression itself
     assert np.array_equal(f[~inside], l[~inside])
+
+
+def test_integer_widening_equals_the_conversion_instruction():
+    """The mixed face kernels widen their FP32 flux changes to FP64 from the bit fields; the result
+    must be the exact widening (numpy's) and the conversion instruction's, bit for bit, over
+    random bit patterns, the subnormal range, signed zeros and infinities (NaN stays NaN)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19494_gb300 import build, native
+    build.build()
+    lib = native.lib()
+    rng = np.random.default_rng(2)
+    pats = rng.integers(0, 2 ** 32, 400000, dtype=np.uint64).astype(np.uint32)
+    sub = rng.integers(1, 2 ** 23, 20000, dtype=np.uint64).astype(np.uint32)
+    x = np.concatenate([pats.view(np.float32), sub.view(np.float32), -sub.view(np.float32),
+                        np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, 1.1754942e-38, 1.1754944e-38,
+                                  3.4028235e38, 1.0, -2.5], np.float32)])
+    xd = torch.from_numpy(x).cuda()
+    bits = torch.empty(len(x), dtype=torch.float64, device="cuda")
+    cvt = torch.empty_like(bits)
+    st = lib.fluid_check_widen(*(ctypes.c_void_p(t.data_ptr()) for t in (xd, bits, cvt)), len(x),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    b, c = bits.cpu().numpy(), cvt.cpu().numpy()
+    ref = x.astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.all(np.isnan(b[nan])) and np.all(np.isnan(c[nan]))
+    assert np.array_equal(b[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+    assert np.array_equal(c[~nan].view(np.uint64), ref[~nan].view(np.uint64))
