@@ -106,9 +106,10 @@ FL_HD void weno5_vjp(const double qin[5], double eps, double g_out, double gq[5]
 
 // One side from the shared set: the value offset out (= face value - q_i), the cotangents gC of the
 // candidates C (times 6, offsets from q_i) and gb of the (times 4) indicators for a unit cotangent.
+// rho[k] = r[k] iv[k] (WENO5-Z) is the cell's, shared by both sides.
 template <int SCHEME>
-FL_HD void weno5_side_vjp(const double f[3], const double r[3], const double iv[3], double sg,
-                          double d0, double d1, double d2, const double C[3], double& out,
+FL_HD void weno5_side_vjp(const double f[3], const double r[3], const double iv[3], const double rho[3],
+                          double sg, double d0, double d1, double d2, const double C[3], double& out,
                           double gC[3], double gb[3]) {
   const double a0 = d0 * f[0], a1 = d1 * f[1], a2 = d2 * f[2];
   const double S = a0 + a1 + a2;
@@ -126,17 +127,24 @@ FL_HD void weno5_side_vjp(const double f[3], const double r[3], const double iv[
     gb[1] = -2.0 * ga1 * a1 * r[1];
     gb[2] = -2.0 * ga2 * a2 * r[2];
   } else {
-    // a_k = d_k (1 + r_k^2), r_k = tau / e_k
+    // a_k = d_k (1 + r_k^2), r_k = tau / e_k: d a_k / d e_k = -2 d_k r_k^2 / e_k, d a_k / d tau =
+    // 2 d_k r_k / e_k
     const double gr0 = ga0 * (2.0 * d0) * r[0], gr1 = ga1 * (2.0 * d1) * r[1], gr2 = ga2 * (2.0 * d2) * r[2];
     const double gtau = sg * fma(gr2, iv[2], fma(gr1, iv[1], gr0 * iv[0]));
-    gb[0] = fma(-gr0 * r[0], iv[0], gtau);
-    gb[1] = -gr1 * r[1] * iv[1];
-    gb[2] = fma(-gr2 * r[2], iv[2], -gtau);
+    gb[0] = fma(-gr0, rho[0], gtau);
+    gb[1] = -gr1 * rho[1];
+    gb[2] = fma(-gr2, rho[2], -gtau);
   }
 }
 
 // up / dn select the values formed; each gradient J (unit cotangent, over q_{i-2..i+2}) sums to
 // one, so its centre entry follows from the other four.
+//
+// With 4 beta_k = (13/3) t_k^2 + s_k^2, d(4 beta_k)/dt_k = T t_k (T = 26/3) and d/ds_k = 2 s_k, and
+// t_k, s_k are fixed combinations of the q's, so the indicator part of J is
+// sum_k gb_k (T t_k dt_k/dq + 2 s_k ds_k/dq): per stencil point a combination gb_k P_k with
+// P_k = T t_k c + 2 s_k c' -- the same six P's for both sides (A: the outer points of stencils 0
+// and 2, B: their inner points and stencil 1's two sides), formed once per cell.
 template <int SCHEME>
 FL_HD void weno5_vjp_cell(const double qin[5], double eps4, bool up, bool dn, double& v_up,
                           double J_up[5], double& v_dn, double J_dn[5]) {
@@ -150,7 +158,7 @@ FL_HD void weno5_vjp_cell(const double qin[5], double eps4, bool up, bool dn, do
   const double b0 = fma(K4 * t0, t0, s0 * s0);
   const double b1 = fma(K4 * t1, t1, s1 * s1);
   const double b2 = fma(K4 * t2, t2, s2 * s2);
-  double iv[3], r[3], f[3], sg = 1.0;
+  double iv[3], r[3], f[3], rho[3], sg = 1.0;
   iv[0] = fl_rcp(b0 + eps4);
   iv[1] = fl_rcp(b1 + eps4);
   iv[2] = fl_rcp(b2 + eps4);
@@ -158,6 +166,7 @@ FL_HD void weno5_vjp_cell(const double qin[5], double eps4, bool up, bool dn, do
     for (int k = 0; k < 3; ++k) {
       r[k] = iv[k];
       f[k] = iv[k] * iv[k];
+      rho[k] = 0.0;
     }
   } else {
     const double db = b0 - b2;
@@ -166,35 +175,39 @@ FL_HD void weno5_vjp_cell(const double qin[5], double eps4, bool up, bool dn, do
     for (int k = 0; k < 3; ++k) {
       r[k] = tau * iv[k];
       f[k] = fma(r[k], r[k], 1.0);
+      rho[k] = r[k] * iv[k];
     }
   }
   constexpr double T = 2.0 * K4;
+  // t0 = q0 - 2 q1, s0 = q0 - 4 q1; t1 = q1 + q3, s1 = q1 - q3; t2 = q4 - 2 q3, s2 = q4 - 4 q3
+  const double A0 = fma(T, t0, 2.0 * s0);            // point i-2 (stencil 0)
+  const double B0 = fma(-2.0 * T, t0, -8.0 * s0);    // point i-1 (stencil 0)
+  const double A1 = fma(T, t1, 2.0 * s1);            // point i-1 (stencil 1)
+  const double B1 = fma(T, t1, -2.0 * s1);           // point i+1 (stencil 1)
+  const double B2 = fma(-2.0 * T, t2, -8.0 * s2);    // point i+1 (stencil 2)
+  const double A2 = fma(T, t2, 2.0 * s2);            // point i+2 (stencil 2)
   if (up) {
     // candidates at i+1/2 times 6: 2 q0 - 7 q1 + 11 q2, -q1 + 5 q2 + 2 q3, 2 q2 + 5 q3 - q4
     const double C[3] = {fma(2.0, q0, -7.0 * q1), fma(2.0, q3, -q1), fma(5.0, q3, -q4)};
     double out, gC[3], gb[3];
-    weno5_side_vjp<SCHEME>(f, r, iv, sg, 0.1, 0.6, 0.3, C, out, gC, gb);
+    weno5_side_vjp<SCHEME>(f, r, iv, rho, sg, 0.1, 0.6, 0.3, C, out, gC, gb);
     v_up = out + qin[2];
-    const double u0 = gb[0] * t0, v0 = gb[0] * s0, u1 = gb[1] * t1, v1 = gb[1] * s1;
-    const double u2 = gb[2] * t2, v2 = gb[2] * s2;
-    J_up[0] = fma(2.0, gC[0], fma(T, u0, 2.0 * v0));
-    J_up[1] = fma(-7.0, gC[0], -gC[1]) + fma(-2.0 * T, u0, fma(-8.0, v0, fma(T, u1, 2.0 * v1)));
-    J_up[3] = fma(2.0, gC[1], 5.0 * gC[2]) + fma(T, u1, fma(-2.0, v1, fma(-2.0 * T, u2, -8.0 * v2)));
-    J_up[4] = -gC[2] + fma(T, u2, 2.0 * v2);
+    J_up[0] = fma(2.0, gC[0], gb[0] * A0);
+    J_up[1] = fma(-7.0, gC[0], fma(-1.0, gC[1], fma(gb[0], B0, gb[1] * A1)));
+    J_up[3] = fma(2.0, gC[1], fma(5.0, gC[2], fma(gb[1], B1, gb[2] * B2)));
+    J_up[4] = fma(gb[2], A2, -gC[2]);
     J_up[2] = 1.0 - ((J_up[0] + J_up[1]) + (J_up[3] + J_up[4]));
   }
   if (dn) {
     // candidates at i-1/2 times 6: -q0 + 5 q1 + 2 q2, 2 q1 + 5 q2 - q3, 11 q2 - 7 q3 + 2 q4
     const double C[3] = {fma(5.0, q1, -q0), fma(2.0, q1, -q3), fma(2.0, q4, -7.0 * q3)};
     double out, gC[3], gb[3];
-    weno5_side_vjp<SCHEME>(f, r, iv, sg, 0.3, 0.6, 0.1, C, out, gC, gb);
+    weno5_side_vjp<SCHEME>(f, r, iv, rho, sg, 0.3, 0.6, 0.1, C, out, gC, gb);
     v_dn = out + qin[2];
-    const double u0 = gb[0] * t0, v0 = gb[0] * s0, u1 = gb[1] * t1, v1 = gb[1] * s1;
-    const double u2 = gb[2] * t2, v2 = gb[2] * s2;
-    J_dn[0] = -gC[0] + fma(T, u0, 2.0 * v0);
-    J_dn[1] = fma(5.0, gC[0], 2.0 * gC[1]) + fma(-2.0 * T, u0, fma(-8.0, v0, fma(T, u1, 2.0 * v1)));
-    J_dn[3] = fma(-7.0, gC[2], -gC[1]) + fma(T, u1, fma(-2.0, v1, fma(-2.0 * T, u2, -8.0 * v2)));
-    J_dn[4] = fma(2.0, gC[2], fma(T, u2, 2.0 * v2));
+    J_dn[0] = fma(gb[0], A0, -gC[0]);
+    J_dn[1] = fma(5.0, gC[0], fma(2.0, gC[1], fma(gb[0], B0, gb[1] * A1)));
+    J_dn[3] = fma(-7.0, gC[2], fma(-1.0, gC[1], fma(gb[1], B1, gb[2] * B2)));
+    J_dn[4] = fma(2.0, gC[2], gb[2] * A2);
     J_dn[2] = 1.0 - ((J_dn[0] + J_dn[1]) + (J_dn[3] + J_dn[4]));
   }
 }
@@ -348,18 +361,20 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
   const double gX = ct > 0.0 ? 0.5 * gct * fl_rcp(ct) : 0.0;
   const double gHt = ph.gm1 * gX;
   for (int c = 0; c < 3; ++c) gut[c] -= ph.gm1 * gX * ut[c];
-  // Ht = (sL HL + sR HR) isum
-  double gsL = gHt * HL * isum, gsR = gHt * HR * isum;
-  const double gHL = gHt * sL * isum, gHR = gHt * sR * isum;
-  double gisum = gHt * (sL * HL + sR * HR);
-  // ut_c = (sL uL_c + sR uR_c) isum
+  // Ht = (sL HL + sR HR) isum and ut_c = (sL uL_c + sR uR_c) isum: with the weights
+  // wL = sL isum, wR = sR isum, d/d sL = isum (HL, uL_c) and d/d isum = (sL + sR) (Ht, ut_c)
+  const double wL = sL * isum, wR = sR * isum;
+  const double gHL = gHt * wL, gHR = gHt * wR;
+  double guL = gHt * HL, guR = gHt * HR, gdot = gHt * Ht;
   for (int c = 0; c < 3; ++c) {
-    gsL += gut[c] * wl[1 + c] * isum;
-    gsR += gut[c] * wr[1 + c] * isum;
-    gwl[1 + c] += gut[c] * sL * isum;
-    gwr[1 + c] += gut[c] * sR * isum;
-    gisum += gut[c] * (sL * wl[1 + c] + sR * wr[1 + c]);
+    guL = fma(gut[c], wl[1 + c], guL);
+    guR = fma(gut[c], wr[1 + c], guR);
+    gdot = fma(gut[c], ut[c], gdot);
+    gwl[1 + c] = fma(gut[c], wL, gwl[1 + c]);
+    gwr[1 + c] = fma(gut[c], wR, gwr[1 + c]);
   }
+  double gsL = guL * isum, gsR = guR * isum;
+  const double gisum = gdot * (sL + sR);
   // H = (E + p) ir
   gEL += gHL * irL;
   gwl[4] += gHL * irL;
@@ -398,8 +413,8 @@ FL_HD void hllc_vjp(const double wl[5], const double wr[5], const Phys& ph, cons
 template <int D>
 FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double gd[3][4],
                          const double gb[3][4], int ndim, double mfa, const Phys& ph,
-                         const double gFd[4], double gvel[3][4], double gT[4], double ggd[3][4],
-                         double ggb[3][4]) {
+                         const double gFd[4], double gvel[3][4], double gT[4], double gGD[3],
+                         double gGB[3]) {
   const double ci[4] = {-k16th, 9.0 * k16th, 9.0 * k16th, -k16th};
   const double cn[4] = {k24th * mfa, -27.0 * k24th * mfa, 27.0 * k24th * mfa, -k24th * mfa};
   double vf[3], Gf[3][3];
@@ -450,11 +465,13 @@ FL_HD void visc_face_vjp(const double vel[3][4], const double T[4], const double
     gT[k] = gTf * ci[k] + gdT * cn[k];
     for (int c = 0; c < 3; ++c) gvel[c][k] = gvf[c] * ci[k] + gG[c][D] * cn[k];
   }
-  for (int b = 0; b < 3; ++b)
-    for (int k = 0; k < 4; ++k) {
-      ggd[b][k] = act[b] ? gG[D][b] * ci[k] : 0.0;
-      ggb[b][k] = act[b] ? gG[b][b] * ci[k] : 0.0;
-    }
+  // the tangential gradients enter only through their four-point interpolations Gf[D][b] and
+  // Gf[b][b]: their cotangents, which the stencil cells receive times the interpolation weights
+  // (-1, 9, 9, -1) / 16
+  for (int b = 0; b < 3; ++b) {
+    gGD[b] = act[b] ? gG[D][b] : 0.0;
+    gGB[b] = act[b] ? gG[b][b] : 0.0;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------

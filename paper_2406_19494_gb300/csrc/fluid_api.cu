@@ -83,7 +83,7 @@ struct fluid_solver {
   double* gW = nullptr;            // cotangent of the primitives, NW * ncell
   double* gG = nullptr;            // cotangent of the velocity gradients, NG * ncell
   double* CW = nullptr;            // per-face contributions (6 slots x 6 primitives), 36 * ncell
-  double* CG = nullptr;            // per-face gradient contributions (4 x 4), 16 * ncell
+  double* CG = nullptr;            // per-face cotangents of the four tangential face gradients, 4 * ncell
   double* S1 = nullptr;            // stage states recomputed by the step adjoint
   double* S2 = nullptr;
   double* MU = nullptr;            // scaled cotangent handed to the right-hand-side adjoint
@@ -643,7 +643,7 @@ int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
     if ((e = al.malloc((void**)&s->CW, 36 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CW");
     if (visc) {
       if ((e = al.malloc((void**)&s->gG, fl::NG * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc gG");
-      if ((e = al.malloc((void**)&s->CG, 16 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
+      if ((e = al.malloc((void**)&s->CG, 4 * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc CG");
     }
     if ((e = al.malloc((void**)&s->Wn, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wn");
     if ((e = al.malloc((void**)&s->W1, fl::NW * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc W1");

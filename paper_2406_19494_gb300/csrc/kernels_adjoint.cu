@@ -7,8 +7,10 @@
 //                     WENO5 reconstructions (weights included; the two values reconstructed in one
 //                     cell share its indicator set) and of the dissipative flux; the contributions
 //                     to the primitives of the six stencil cells (and to the four tangential-
-//                     gradient cells) go to per-face slots
+//                     gradient cells: the four cotangents of the face's interpolated tangential
+//                     gradients) go to per-face slots
 //   k_adj_gather<D>   one thread per cell: sum of the slots of the faces whose stencil contains it
+//                     (the tangential-gradient cotangents times the cell's interpolation weight)
 //   k_adj_grad        reverse of the centre velocity gradients
 //   k_adj_bc<a>       reverse of the halo passes, z then y then x; one thread owns a boundary
 //                     column (both sides, all layers), so contributions to a source cell never race
@@ -162,19 +164,19 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_face(const double* __restrict
             }
           }
           const double gFd[4] = {-gF[1], -gF[2], -gF[3], -gF[4]};
-          double gvel[3][4], gT[4], ggd[3][4], ggb[3][4];
-          visc_face_vjp<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, gFd, gvel, gT, ggd, ggb);
+          double gvel[3][4], gT[4], gGD[3], gGB[3];
+          visc_face_vjp<D>(vel, T, gd, gb, g.ndim, g.mf[D][a], ph, gFd, gvel, gT, gGD, gGB);
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             gcell[1][1 + o] += gvel[0][o];
             gcell[2][1 + o] += gvel[1][o];
             gcell[3][1 + o] += gvel[2][o];
             gcell[5][1 + o] += gT[o];
-            CG[(o * kGComp + 0) * nc + fcell] = ggd[A1][o];
-            CG[(o * kGComp + 1) * nc + fcell] = ggb[A1][o];
-            CG[(o * kGComp + 2) * nc + fcell] = ggd[A2][o];
-            CG[(o * kGComp + 3) * nc + fcell] = ggb[A2][o];
           }
+          CG[0 * nc + fcell] = gGD[A1];
+          CG[1 * nc + fcell] = gGB[A1];
+          CG[2 * nc + fcell] = gGD[A2];
+          CG[3 * nc + fcell] = gGB[A2];
         }
 #pragma unroll
         for (int k = 0; k < kSlots; ++k)
@@ -229,14 +231,17 @@ __global__ void k_adj_gather(const double* __restrict__ CW, const double* __rest
 #pragma unroll
     for (int v = 0; v < 6; ++v) gW[v * nc + cell] += acc[v];
     if (VISC) {
+      // face a's four cotangents of its interpolated tangential gradients, times the weight of
+      // this cell (stencil point k of a-1 .. a+2) in the interpolation (-1, 9, 9, -1) / 16
       double ag[kGComp] = {0, 0, 0, 0};
 #pragma unroll
       for (int k = 0; k < kGSlots; ++k) {
         const int a = x + 1 - k;
         if (a < amin || a > amax) continue;
         const int fcell = cell + (a - x) * s;
+        const double wk = (k == 0 || k == 3) ? -k16th : 9.0 * k16th;
 #pragma unroll
-        for (int m = 0; m < kGComp; ++m) ag[m] += CG[(k * kGComp + m) * nc + fcell];
+        for (int m = 0; m < kGComp; ++m) ag[m] = fma(wk, CG[m * nc + fcell], ag[m]);
       }
       // components: (D, A1), (A1, A1), (D, A2), (A2, A2) of d u_c / d x_b
       if (A1 < g.ndim) {

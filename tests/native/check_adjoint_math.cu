@@ -126,9 +126,16 @@ static double check_visc(int visc, int ndim) {
       }
     }
     const double mfa = U(5, 20);
-    double g[4], gvel[3][4], gT[4], ggd[3][4], ggb[3][4];
+    double g[4], gvel[3][4], gT[4], gGD[3], gGB[3], ggd[3][4], ggb[3][4];
     for (int k = 0; k < 4; ++k) g[k] = U(-1, 1);
-    visc_face_vjp<D>(vel, T, gd, gb, ndim, mfa, ph, g, gvel, gT, ggd, ggb);
+    visc_face_vjp<D>(vel, T, gd, gb, ndim, mfa, ph, g, gvel, gT, gGD, gGB);
+    // the stencil cells' share: the interpolation weights (-1, 9, 9, -1) / 16
+    const double wi[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 4; ++k) {
+        ggd[c][k] = gGD[c] * wi[k];
+        ggb[c][k] = gGB[c] * wi[k];
+      }
     const double h = 1e-6;
     double vp[3][4], vm[3][4], Tp[4], Tm[4], gdp[3][4], gdm[3][4], gbp[3][4], gbm[3][4];
     for (int k = 0; k < 4; ++k) {
