@@ -451,6 +451,7 @@ def run_fluid(args):
             "dtype": "f32 fluxes / f64 state",
             "error_vs_fp64": mixed_err,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items() if v[1]},
+            "roofline_step": mixed_step_roofline(mixed_ms / args.steps, ncell),
             "roofline_face": {
                 "fp64": {"achieved": m64, "peak": peak64, "unit": "TFLOP/s", "frac": m64 / peak64},
                 "fp32": {"achieved": m32, "peak": peak32, "unit": "TFLOP/s", "frac": m32 / peak32,
@@ -897,6 +898,40 @@ def face_traffic(ncell):
         return None
     per = sum(info["dram_bytes_per_launch"]) / len(info["dram_bytes_per_launch"])
     return per * ncell / info["cells"]
+
+
+def mixed_step_roofline(ms_per_step, ncell):
+    """Whole-step roofline of the mixed path from the committed ncu counters of one single-step
+    call on TGV 128^3 (profiles/mixed_step_counters.json: every launch of the step with its FP64-pipe
+    thread instructions, DRAM bytes and issued warp instructions), scaled per cell.  Three floors:
+    the FP64 pipe (152 SMs x 2 lanes per clock), instruction issue (152 SMs x 4 schedulers x one
+    warp instruction per clock), both at the maximum SM clock, and HBM at the measured copy
+    bandwidth.  None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        info = json.load(open(os.path.join(ROOT, "profiles", "mixed_step_counters.json")))
+    except (OSError, ValueError):
+        return None
+    csrc = os.path.join(ROOT, "paper_2406_19494_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                   for f in ("kernels_mixed.cu", "kernels_fp64.cu", "fluid_internal.cuh", "flux_math.cuh",
+                             "fast_math.cuh"))
+    if hashlib.sha256(src).hexdigest()[:16] != info.get("source_sha256_16"):
+        return None
+    scale = ncell / info["cells"]
+    clk = 2.07e9
+    tot = {k: sum(l[k] for l in info["launches"]) * scale
+           for k in ("fp64_thread_inst", "dram_bytes", "warp_inst")}
+    floors = {"fp64_pipe": tot["fp64_thread_inst"] / (152 * 2 * clk) * 1e3,
+              "issue": tot["warp_inst"] / (152 * 4 * clk) * 1e3,
+              "hbm": tot["dram_bytes"] / (measured_hbm_gbs() * 1e9) * 1e3}
+    bound = max(floors, key=floors.get)
+    return {"bound": bound, "floor_ms": floors[bound], "ms_per_step": ms_per_step,
+            "frac": floors[bound] / ms_per_step, "floors_ms": floors,
+            "per_cell_update": {"fp64_thread_inst": tot["fp64_thread_inst"] / ncell,
+                                "dram_bytes": tot["dram_bytes"] / ncell,
+                                "thread_inst": tot["warp_inst"] * 32 / ncell},
+            "basis": "ncu counters of every launch of one single-step call (profiles/mixed_step_counters.json)"}
 
 
 def ctypes_peak(s, kind):
