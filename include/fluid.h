@@ -283,7 +283,10 @@ int fluid_check(fluid_solver* s, void* stream);
  * and cells per thread segment along the face axis (0 = automatic: the longest of 64/32/16/8/4
  * that still fills the GPU), for every axis (fluid_autotune_faces picks one per axis).  For FLUID_PREC_MIXED the y and z face kernels are shared-memory
  * tiles of 2 warps (block 64) or 4 warps (otherwise) by default; seg < 0 selects the register-window
- * marching kernels with |seg| cells per segment and `block` threads instead.  With the tiles,
+ * marching kernels with |seg| cells per segment and `block` threads instead; seg = 1 selects the
+ * 4-warp tiles whose (hi, lo) rows are staged into shared memory by bulk copies (cp.async.bulk on an
+ * mbarrier; a copy that does not complete within its bounded wait makes fluid_check return
+ * FLUID_ECUDA).  With the tiles,
  * fluid_step folds each RK3 stage (and the primitives of its result) into the last axis's tile
  * kernel, with the same arithmetic as the separate stage kernel.  FP64 results and those of the two
  * mixed tiles are bitwise the same for every shape; the mixed register-window kernels agree with

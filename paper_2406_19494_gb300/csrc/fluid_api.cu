@@ -307,7 +307,7 @@ int grad_faces(fluid_solver* s, double* R, cudaStream_t st) {
     for (int d = 0; d < g.ndim; ++d)
       FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
                fl::launch_face_mixed(d, s->W, s->W32, s->G32, R, g, s->ph, d > 0, s->face_block,
-                                     s->face_seg, st));
+                                     s->face_seg, st, &s->ctl->flags));
     return FLUID_OK;
   }
   if (s->ph.visc != FLUID_VISC_NONE)
@@ -366,10 +366,11 @@ int stage_fused_into(fluid_solver* s, int stage, const double* Un, const double*
   for (int d = 0; d + 1 < g.ndim; ++d)
     FL_TIMED(s, FLUID_KERNEL_FACE_X + d, st,
              fl::launch_face_mixed(d, s->W, s->W32, s->G32, s->R, g, s->ph, d > 0, s->face_block,
-                                   s->face_seg, st));
+                                   s->face_seg, st, &s->ctl->flags));
   const fl::StageOut so{stage, prims ? 1 : 0, Un, Us, Ud, s->Wb, s->W32b, s->ctl, t_end};
   FL_TIMED(s, FLUID_KERNEL_FACE_X + g.ndim - 1, st,
-           fl::launch_face_mixed_stage(s->W, s->W32, s->G32, s->R, g, s->ph, s->face_block, so, st));
+           fl::launch_face_mixed_stage(s->W, s->W32, s->G32, s->R, g, s->ph, s->face_block, s->face_seg,
+                                       so, st));
   if (prims) {
     FL_TIMED(s, FLUID_KERNEL_STAGE, st, fl::launch_halo_prim(s->Wb, s->W32b, g, s->ph, s->bc, s->ctl, st));
     std::swap(s->W, s->Wb);
@@ -538,9 +539,10 @@ int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
   if ((e = al.malloc((void**)&s->W, (fl::NW + (s->mixed ? 1 : 0)) * nc * sizeof(double))) != cudaSuccess)
     return bail(e, "cudaMalloc W");
   if (s->mixed) {
-    if ((e = al.malloc((void**)&s->W32, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
+    // W32 buffers: 64 floats of slack past the end for the aligned tails of bulk-staged rows
+    if ((e = al.malloc((void**)&s->W32, (2 * fl::NW * nc + 64) * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
     if ((e = al.malloc((void**)&s->Wb, (fl::NW + 1) * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wb");
-    if ((e = al.malloc((void**)&s->W32b, 2 * fl::NW * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32b");
+    if ((e = al.malloc((void**)&s->W32b, (2 * fl::NW * nc + 64) * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32b");
     if ((e = al.malloc((void**)&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
     if (c.visc_law != FLUID_VISC_NONE)
       if ((e = al.malloc((void**)&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
@@ -1020,6 +1022,8 @@ int fluid_check(fluid_solver* s, void* stream) {
   if (flags) {
     const unsigned zero = 0;
     FL_CUDA(s, cudaMemcpy(&s->ctl->flags, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
+    if (flags & fl::FLAG_STAGING)
+      return fail(s, FLUID_ECUDA, "a bulk copy into shared memory did not complete within its wait limit");
     return fail(s, FLUID_ENONFINITE,
                 (flags & fl::FLAG_GHOST_T) ? "non-positive ghost temperature at an isothermal wall"
                                            : "non-finite value in the state");

@@ -18,6 +18,7 @@ constexpr int NG = 9;   // velocity-gradient scratch, component c * 3 + b = d u_
 // flag bits of Ctl::flags
 constexpr unsigned FLAG_NONFINITE = 1u;
 constexpr unsigned FLAG_GHOST_T = 2u;
+constexpr unsigned FLAG_STAGING = 4u;   // a shared-memory staging copy did not complete in time
 
 // Grid geometry: padded sizes, strides and per-axis 1-D metric arrays (device, length p[a]).
 struct Geo {
@@ -184,9 +185,11 @@ cudaError_t launch_face_teno(int D, const double* W, const double* G, double* R,
                              const Phys& ph, int accumulate, int block, int seg, SeamBuf fb,
                              cudaStream_t st);
 // ---- mixed-precision launchers implemented in kernels_mixed.cu --------------------------------
+// seg 1 on the y / z tiles stages their rows by bulk copies; a copy that does not complete within
+// its bounded wait sets FLAG_STAGING in *flags (when given) and leaves its tile undone
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,
-                              cudaStream_t st);
+                              cudaStream_t st, unsigned* flags = nullptr);
 // Stage output of the last axis's face kernel when the stage is fused into it: Ud = stage `stage`
 // of RK3 from Un, Us and the completed right-hand side, and the primitives of Ud (W: NW rows and
 // the H row; W32: the split) written to a second buffer pair, since the kernel still reads the
@@ -208,7 +211,7 @@ bool mixed_stage_fusable(const Geo& g, int seg);
 // fused with the stage combination and the primitives of its result (interior cells; the halo
 // cells of the new buffer follow with launch_halo_prim)
 cudaError_t launch_face_mixed_stage(const double* W, const float* W32, const float* G32,
-                                    const double* R, const Geo& g, const Phys& ph, int block,
+                                    const double* R, const Geo& g, const Phys& ph, int block, int seg,
                                     const StageOut& so, cudaStream_t st);
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st);
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,

@@ -48,6 +48,39 @@ __device__ __forceinline__ float rsqrtf_a(float y) {
   float r; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y)); return r;
 }
 
+// ---- bulk-copy staging: cp.async.bulk (the TMA unit's untiled copy) completing on an mbarrier ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one arrival that also raises the phase's expected transaction count by `bytes`
+__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned), counted on bar
+__device__ __forceinline__ void bulk_to_smem(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase of the given parity: non-blocking tests with a short sleep between
+// them, 2^17 of them at most (of the order of 10 ms); false if the phase did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 17); ++it) {
+    if (mbar_test(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 int grid_for(long long work, int block) {
   long long b = (work + block - 1) / block;
   if (b < 1) b = 1;
@@ -464,10 +497,22 @@ constexpr size_t t_smem() {
   return sizeof(float) * 6 * (FPW * NWARP + 4) * 32 + sizeof(double) * NWARP * 5 * 32;
 }
 
-template <int D, int SCHEME, bool VISC, int NWARP, int FPW, bool STAGE = false>
+// Bulk-staged tiles: the (hi, lo) rows a tile's cell differences need, staged into shared memory
+// by cp.async.bulk.  Per row 36 floats: the 32 columns of the tile from the 16-byte boundary at or
+// below the first, so that both addresses of the copy are aligned (the rows' own alignment varies
+// with the row); the W32 buffers carry 64 floats of slack past their end for the last rows' tails.
+constexpr int kBulkRow = 36;
+
+template <int NWARP, int FPW, int NVW>
+constexpr size_t t_smem_bulk() {
+  return sizeof(float) * 2 * NVW * (FPW * NWARP + 5) * kBulkRow + t_smem<NWARP, FPW>();
+}
+
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW, bool STAGE = false, bool BULK = false>
 __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restrict__ R,
                                                                        Geo g, PhysF pf, int accumulate,
-    uint3 bid, uint3 gdim, const StageOut* sop = nullptr, const Phys* php = nullptr) {
+    uint3 bid, uint3 gdim, const StageOut* sop = nullptr, const Phys* php = nullptr,
+    unsigned* flags = nullptr) {
   static_assert(D == 1 || D == 2, "tiles along y or z");
   constexpr int kTFaces = FPW;
   constexpr int kTCells = kTFaces * NWARP - 1;
@@ -475,10 +520,14 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
   constexpr int NVW = VISC ? 6 : 5;
   constexpr int ND = kTCells + 5;
   constexpr int OTHER = D == 1 ? 2 : 1;                     // the axis that is neither x nor D
-  extern __shared__ unsigned char smem_raw[];
-  float (*sD)[ND][32] = reinterpret_cast<float (*)[ND][32]>(smem_raw);                  // [6][ND][32]
+  constexpr int NA = 2 * NVW;                               // staged arrays: hi and lo of each primitive
+  constexpr int NR = ND + 1;                                // staged rows: cells d0 - 3 .. d0 + kTCells + 2
+  constexpr size_t kRawBytes = BULK ? sizeof(float) * NA * NR * kBulkRow : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* raw = reinterpret_cast<float*>(smem_raw);                                      // [NA][NR][36]
+  float (*sD)[ND][32] = reinterpret_cast<float (*)[ND][32]>(smem_raw + kRawBytes);      // [6][ND][32]
   double (*sF)[5][32] =
-      reinterpret_cast<double (*)[5][32]>(smem_raw + sizeof(float) * 6 * ND * 32);      // [NWARP][5][32]
+      reinterpret_cast<double (*)[5][32]>(smem_raw + kRawBytes + sizeof(float) * 6 * ND * 32);  // [NWARP][5][32]
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int x = g.h[0] + bid.x * 32 + lane;
   const bool xok = x < g.h[0] + g.n[0];
@@ -500,12 +549,57 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
       sop->ctl->t = (sop->t_end > 0.0 && !(tn < sop->t_end)) ? sop->t_end : tn;
     }
   }
-  for (int k = warp; k < ND; k += kTWarps) {
-    const int j = d0 - 3 + k;
-    const bool ok = xok && j + 1 <= dend + 2;
+  if (BULK) {
+    // stage the rows: warp 0 issues one bulk copy per (array, row) inside the padded grid, all
+    // counted on one mbarrier; every thread then waits for the phase (bounded)
+    __shared__ __align__(8) unsigned long long s_bar;
+    const unsigned bar = smem_u32(&s_bar);
+    const int nvalid = min(NR, g.p[D] - (d0 - 3));
+    const int colbase0 = g.h[0] + bid.x * 32 + o * so;      // column of lane 0
+    if (lane == 0 && warp == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (warp == 0) {
+      if (lane == 0) mbar_arrive_expect(bar, (unsigned)(NA * nvalid * kBulkRow * sizeof(float)));
+      __syncwarp();
+      for (int q = lane; q < NA * nvalid; q += 32) {
+        const int ar = q / nvalid, k = q - ar * nvalid;
+        const float* src = (ar < NVW ? in.hi + (size_t)ar * nc : in.lo + (size_t)(ar - NVW) * nc) +
+                           colbase0 + (d0 - 3 + k) * s;
+        const uintptr_t a16 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+        bulk_to_smem(smem_u32(raw + (ar * NR + k) * kBulkRow), reinterpret_cast<const void*>(a16),
+                     kBulkRow * sizeof(float), bar);
+      }
+    }
+    const bool late = !mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(late)) {
+      // the copies did not complete in time: report it, give copies still in flight into this
+      // block's shared memory one more bounded wait, and leave the tile undone
+      if (lane == 0 && warp == 0 && flags) atomicOr(flags, FLAG_STAGING);
+      if (late) mbar_wait_bounded(bar, 0);
+      return;
+    }
+    // cell differences from the staged rows, in the order diff32 forms them
+    auto at = [&](int ar, int k) {
+      const float* src = (ar < NVW ? in.hi + (size_t)ar * nc : in.lo + (size_t)(ar - NVW) * nc) +
+                         colbase0 + (d0 - 3 + k) * s;
+      const int sh = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+      return raw[(ar * NR + k) * kBulkRow + sh + lane];
+    };
+    for (int k = warp; k < ND; k += kTWarps) {
+      const int j = d0 - 3 + k;
+      const bool ok = xok && j + 1 <= dend + 2;
 #pragma unroll
-    for (int v = 0; v < NVW; ++v)
-      sD[v][k][lane] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, colbase + j * s, s) : 0.0f;
+      for (int v = 0; v < NVW; ++v)
+        sD[v][k][lane] = ok ? (at(v, k + 1) - at(v, k)) + (at(NVW + v, k + 1) - at(NVW + v, k)) : 0.0f;
+    }
+  } else {
+    for (int k = warp; k < ND; k += kTWarps) {
+      const int j = d0 - 3 + k;
+      const bool ok = xok && j + 1 <= dend + 2;
+#pragma unroll
+      for (int v = 0; v < NVW; ++v)
+        sD[v][k][lane] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, colbase + j * s, s) : 0.0f;
+    }
   }
   __syncthreads();
   const int f0 = warp * kTFaces;                            // face a + 1/2, a = d0 - 1 + f
@@ -550,12 +644,20 @@ __global__ void __launch_bounds__(32 * NWARP, 32 / NWARP) k_face_mixed_t(MixedIn
   k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW>(in, R, g, pf, accumulate, blockIdx, gridDim);
 }
 
+// bulk-staged tile (4 warps x 4 faces): the y / z face kernel with its rows staged by cp.async.bulk
+template <int D, int SCHEME, bool VISC>
+__global__ void __launch_bounds__(128, 4) k_face_mixed_tb(MixedIn in, double* __restrict__ R, Geo g,
+                                                          PhysF pf, int accumulate, unsigned* flags) {
+  k_face_mixed_t_body<D, SCHEME, VISC, 4, 4, false, true>(in, R, g, pf, accumulate, blockIdx, gridDim,
+                                                          nullptr, nullptr, flags);
+}
+
 // the last axis's tile kernel with the stage fused (StageOut): R is read, not written
-template <int D, int SCHEME, bool VISC, int NWARP, int FPW, int MINB>
+template <int D, int SCHEME, bool VISC, int NWARP, int FPW, int MINB, bool BULK = false>
 __global__ void __launch_bounds__(32 * NWARP, MINB) k_face_mixed_ts(MixedIn in, const double* __restrict__ R,
                                                                     Geo g, PhysF pf, StageOut so, Phys ph) {
-  k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW, true>(in, const_cast<double*>(R), g, pf, 1, blockIdx,
-                                                         gridDim, &so, &ph);
+  k_face_mixed_t_body<D, SCHEME, VISC, NWARP, FPW, true, BULK>(in, const_cast<double*>(R), g, pf, 1, blockIdx,
+                                                               gridDim, &so, &ph, &so.ctl->flags);
 }
 
 
@@ -757,8 +859,28 @@ cudaError_t launch_tile(int D, const MixedIn& in, double* R, const Geo& g, const
 }
 
 template <int SCHEME, bool VISC>
+cudaError_t launch_tile_bulk(int D, const MixedIn& in, double* R, const Geo& g, const PhysF& pf,
+                             int accumulate, unsigned* flags, cudaStream_t st) {
+  constexpr size_t smem = t_smem_bulk<4, 4, VISC ? 6 : 5>();
+  const int other = D == 1 ? 2 : 1;
+  const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + 14) / 15, g.n[other]);
+  if (D == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_tb<1, SCHEME, VISC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (k_face_mixed_tb<1, SCHEME, VISC><<<grid, dim3(32, 4), smem, st>>>(in, R, g, pf, accumulate, flags), ++t_launches);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_tb<2, SCHEME, VISC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (k_face_mixed_tb<2, SCHEME, VISC><<<grid, dim3(32, 4), smem, st>>>(in, R, g, pf, accumulate, flags), ++t_launches);
+  }
+  return cudaGetLastError();
+}
+
+template <int SCHEME, bool VISC>
 cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const PhysF& pf,
-                      int accumulate, int block, int seg, cudaStream_t st) {
+                      int accumulate, int block, int seg, unsigned* flags, cudaStream_t st) {
   if (D == 0) {
     const long long lines = (long long)g.n[1] * g.n[2];
     const dim3 grid((g.n[0] + kXCells - 1) / kXCells, (unsigned)((lines + kXRows - 1) / kXRows));
@@ -771,37 +893,40 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
     if (D == 1) return launch_t<1, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
     return launch_t<2, SCHEME, VISC>(in, R, g, pf, accumulate, block, sg, st);
   }
+  // seg 1: the 4 x 4 tile with its rows staged by bulk copies
+  if (seg == 1) return launch_tile_bulk<SCHEME, VISC>(D, in, R, g, pf, accumulate, flags, st);
   // tile shape (warps x faces per warp): block 64 -> 2 x 4, otherwise 4 x 4 (on TGV 128^3 the
   // 4 x 4 tile was the fastest of 16 x 1, 8 x 2, 4 x 4 and 2 x 4)
   if (block == 64) return launch_tile<SCHEME, VISC, 2, 4>(D, in, R, g, pf, accumulate, st);
   return launch_tile<SCHEME, VISC, 4, 4>(D, in, R, g, pf, accumulate, st);
 }
 
-template <int SCHEME, bool VISC, int NWARP, int FPW, int MINB>
+template <int SCHEME, bool VISC, int NWARP, int FPW, int MINB, bool BULK = false>
 cudaError_t launch_tile_stage(int D, const MixedIn& in, const double* R, const Geo& g, const PhysF& pf,
                               const Phys& ph, const StageOut& so, cudaStream_t st) {
   constexpr int cells = FPW * NWARP - 1;
-  constexpr size_t smem = t_smem<NWARP, FPW>();
+  constexpr size_t smem = BULK ? t_smem_bulk<NWARP, FPW, VISC ? 6 : 5>() : t_smem<NWARP, FPW>();
   const int other = D == 1 ? 2 : 1;
   const dim3 grid((g.n[0] + 31) / 32, (g.n[D] + cells - 1) / cells, g.n[other]);
   if (D == 1) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB, BULK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    (k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
+    (k_face_mixed_ts<1, SCHEME, VISC, NWARP, FPW, MINB, BULK><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB, BULK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    (k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
+    (k_face_mixed_ts<2, SCHEME, VISC, NWARP, FPW, MINB, BULK><<<grid, dim3(32, NWARP), smem, st>>>(in, R, g, pf, so, ph), ++t_launches);
   }
   return cudaGetLastError();
 }
 
 template <int SCHEME, bool VISC>
 cudaError_t launch_stage_sv(const MixedIn& in, const double* R, const Geo& g, const PhysF& pf, const Phys& ph,
-                            int block, const StageOut& so, cudaStream_t st) {
+                            int block, int seg, const StageOut& so, cudaStream_t st) {
   const int D = g.ndim - 1;
+  if (seg == 1) return launch_tile_stage<SCHEME, VISC, 4, 4, 4, true>(D, in, R, g, pf, ph, so, st);
   if (block == 64) return launch_tile_stage<SCHEME, VISC, 2, 4, 12>(D, in, R, g, pf, ph, so, st);
   return launch_tile_stage<SCHEME, VISC, 4, 4, 6>(D, in, R, g, pf, ph, so, st);
 }
@@ -815,29 +940,29 @@ bool mixed_stage_fusable(const Geo& g, int seg) {
 }
 
 cudaError_t launch_face_mixed_stage(const double* W, const float* W32, const float* G32,
-                                    const double* R, const Geo& g, const Phys& ph, int block,
+                                    const double* R, const Geo& g, const Phys& ph, int block, int seg,
                                     const StageOut& so, cudaStream_t st) {
   const bool visc = ph.visc != FLUID_VISC_NONE;
   const MixedIn in{W, W32, W32 + (size_t)NW * g.ncell, G32};
   const PhysF pf = phys_f(ph);
   if (ph.weno == FLUID_WENO_JS)
-    return visc ? launch_stage_sv<FLUID_WENO_JS, true>(in, R, g, pf, ph, block, so, st)
-                : launch_stage_sv<FLUID_WENO_JS, false>(in, R, g, pf, ph, block, so, st);
-  return visc ? launch_stage_sv<FLUID_WENO_Z, true>(in, R, g, pf, ph, block, so, st)
-              : launch_stage_sv<FLUID_WENO_Z, false>(in, R, g, pf, ph, block, so, st);
+    return visc ? launch_stage_sv<FLUID_WENO_JS, true>(in, R, g, pf, ph, block, seg, so, st)
+                : launch_stage_sv<FLUID_WENO_JS, false>(in, R, g, pf, ph, block, seg, so, st);
+  return visc ? launch_stage_sv<FLUID_WENO_Z, true>(in, R, g, pf, ph, block, seg, so, st)
+              : launch_stage_sv<FLUID_WENO_Z, false>(in, R, g, pf, ph, block, seg, so, st);
 }
 
 cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const float* G32, double* R,
                               const Geo& g, const Phys& ph, int accumulate, int block, int seg,
-                              cudaStream_t st) {
+                              cudaStream_t st, unsigned* flags) {
   const bool visc = ph.visc != FLUID_VISC_NONE;
   const MixedIn in{W, W32, W32 + (size_t)NW * g.ncell, G32};
   const PhysF pf = phys_f(ph);
   if (ph.weno == FLUID_WENO_JS)
-    return visc ? launch_sv<FLUID_WENO_JS, true>(D, in, R, g, pf, accumulate, block, seg, st)
-                : launch_sv<FLUID_WENO_JS, false>(D, in, R, g, pf, accumulate, block, seg, st);
-  return visc ? launch_sv<FLUID_WENO_Z, true>(D, in, R, g, pf, accumulate, block, seg, st)
-              : launch_sv<FLUID_WENO_Z, false>(D, in, R, g, pf, accumulate, block, seg, st);
+    return visc ? launch_sv<FLUID_WENO_JS, true>(D, in, R, g, pf, accumulate, block, seg, flags, st)
+                : launch_sv<FLUID_WENO_JS, false>(D, in, R, g, pf, accumulate, block, seg, flags, st);
+  return visc ? launch_sv<FLUID_WENO_Z, true>(D, in, R, g, pf, accumulate, block, seg, flags, st)
+              : launch_sv<FLUID_WENO_Z, false>(D, in, R, g, pf, accumulate, block, seg, flags, st);
 }
 
 cudaError_t launch_batch_mixed(const BatchTable* dev, int kind, int D, int step, cudaStream_t st) {

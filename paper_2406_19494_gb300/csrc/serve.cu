@@ -112,6 +112,7 @@ size_t footprint(const fluid_config& c) {
   if (c.precision == FLUID_PREC_MIXED) {
     b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
     b += 8 * nc * (fl::NW + 1) + 4 * nc * 2 * fl::NW;
+    b += 2 * 64 * 4;                                    // the W32 buffers' slack for staged rows
   } else {
     if (visc) b += 8 * nc * fl::NG;
     // seam buffer of the face kernels: 10 doubles per segment of kSeamMinSeg cells, on the axis
