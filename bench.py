@@ -214,6 +214,37 @@ def one_call_ms(s, U, steps, flush, stream):
     return a.elapsed_time(b) / steps
 
 
+def graph_step_ms(s, U, reps, stream):
+    """Median ms of one RK3 step replayed from a CUDA graph that captured one single-step
+    fluid_step call, over `reps` timed replays after ten untimed ones.  No L2 flush between
+    replays: the arrays a step touches (state, stage state, right-hand side, primitives,
+    gradients; about 0.5 GB on TGV 128^3) exceed the 126 MB L2."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        s.step(U, 1)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        s.step(U, 1)
+    for _ in range(10):
+        g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    s.check()
+    del g
+    return statistics.median(ts)
+
+
 def slab_case(base, ws):
     """The workload extended ws times along z (its z-periodic state repeats), to be split into ws
     z-slabs of the workload's own size."""
@@ -362,6 +393,13 @@ def run_fluid(args):
         one_call["mixed_ms_per_step"] = one_call_ms(sm, Uc, args.steps, flush, stream)
         one_call["note"] = ("K steps in one fluid_step call after a warm-up call of K; L2 flushed "
                             "once before the call, the working set of a step (~0.5 GB) exceeds L2")
+        Uc.copy_(U0)
+        graph = {"fp64_ms_per_step": graph_step_ms(s, Uc, 50, stream)}
+        Uc.copy_(U0)
+        graph["mixed_ms_per_step"] = graph_step_ms(sm, Uc, 50, stream)
+        graph["note"] = ("median of 50 replays of a CUDA graph holding one single-step fluid_step call, "
+                         "after 10 untimed replays; inputs larger than L2, no flush")
+        one_call["graph"] = graph
         del Uc
 
     # ---- the paper's channel scheme (TENO6-A + sixth-order central, FP64) ------------------------
