@@ -551,7 +551,7 @@ int fluid_serve_create(const fluid_serve_config* cfg, fluid_server** out) {
   s->device = cfg->device;
   s->t0 = Clock::now();
   // the solves' stream-ordered memory returns to the device's pool and is reused without
-  // returning it to the driver in between (the HBM budget bounds what the server holds)
+  // returning it to the CUDA driver in between (the HBM budget bounds what the server holds)
   cudaMemPool_t pool;
   if (cudaSetDevice(cfg->device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
     uint64_t keep = cfg->hbm_budget_bytes;
