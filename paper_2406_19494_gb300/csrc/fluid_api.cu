@@ -55,7 +55,7 @@ struct fluid_solver {
   float* W32 = nullptr;            // FP32 (hi, lo) primitives, 2 NW * ncell (mixed)
   double* Wb = nullptr;            // mixed: the second pair of primitive buffers (W with its H row,
   float* W32b = nullptr;           // W32), written by a stage fused into the last face kernel
-  float* mf32 = nullptr;           // FP32 face metrics of the three axes (mixed)
+  float* mf32 = nullptr;           // FP32 face metrics, centre metrics and inverse widths of the three axes (mixed)
   float* G32 = nullptr;            // FP32 velocity gradients (mixed, viscous)
   double* A = nullptr;             // RK stage state, NV * ncell
   double* R = nullptr;             // right-hand side accumulator, NV * ncell
@@ -543,7 +543,7 @@ int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
     if ((e = al.malloc((void**)&s->W32, (2 * fl::NW * nc + 64) * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32");
     if ((e = al.malloc((void**)&s->Wb, (fl::NW + 1) * nc * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc Wb");
     if ((e = al.malloc((void**)&s->W32b, (2 * fl::NW * nc + 64) * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc W32b");
-    if ((e = al.malloc((void**)&s->mf32, nmetric / 5 * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
+    if ((e = al.malloc((void**)&s->mf32, 3 * (nmetric / 5) * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc mf32");
     if (c.visc_law != FLUID_VISC_NONE)
       if ((e = al.malloc((void**)&s->G32, fl::NG * nc * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc G32");
   } else if (c.visc_law != FLUID_VISC_NONE) {
@@ -577,15 +577,23 @@ int create_impl(const fluid_config* cfg, fluid_solver** out, SolverAlloc al) {
   if ((e = al.h2d(s->metric, all.data(), all.size() * sizeof(double))) != cudaSuccess)
     return bail(e, "metric upload");
   if (s->mixed) {
-    std::vector<float> mf32;
-    size_t off32[3];
-    for (int a = 0; a < 3; ++a) {
-      off32[a] = mf32.size();
-      for (int k = 0; k < g.p[a]; ++k) mf32.push_back((float)all[off[a][4] + k]);
-    }
-    if ((e = al.h2d(s->mf32, mf32.data(), mf32.size() * sizeof(float))) != cudaSuccess)
+    // FP32 copies (rounded to nearest, as the device conversion rounds) of the face metrics, the
+    // centre metrics and the inverse widths, so that the FP32 kernels convert nothing per cell
+    std::vector<float> m32;
+    size_t off32[3][3];
+    const int src[3] = {4, 3, 2};            // mf, mc, idx
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 3; ++a) {
+        off32[q][a] = m32.size();
+        for (int k = 0; k < g.p[a]; ++k) m32.push_back((float)all[off[a][src[q]] + k]);
+      }
+    if ((e = al.h2d(s->mf32, m32.data(), m32.size() * sizeof(float))) != cudaSuccess)
       return bail(e, "metric upload");
-    for (int a = 0; a < 3; ++a) g.mf32[a] = s->mf32 + off32[a];
+    for (int a = 0; a < 3; ++a) {
+      g.mf32[a] = s->mf32 + off32[0][a];
+      g.mc32[a] = s->mf32 + off32[1][a];
+      g.idx32[a] = s->mf32 + off32[2][a];
+    }
   }
   for (int a = 0; a < 3; ++a) {
     g.xc[a] = s->metric + off[a][0];

@@ -32,6 +32,8 @@ struct Geo {
   const double* mc[3];   // d(index)/dx at centres
   const double* mf[3];   // d(index)/dx at face a+1/2
   const float* mf32[3];  // FP32 copy of mf (mixed path only, else null)
+  const float* mc32[3];  // FP32 copy of mc (mixed path only, else null)
+  const float* idx32[3]; // FP32 copy of idx (mixed path only, else null)
 };
 
 struct Phys {

@@ -681,7 +681,7 @@ __device__ __forceinline__ void k_grad32_body(const float* __restrict__ W32, flo
     for (int b = 0; b < 3; ++b) {
       const bool inb = b < g.ndim && c[b] >= g.h[b] && c[b] < g.h[b] + g.n[b];
       const int s = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
-      const float m = inb ? (float)g.mc[b][c[b]] : 0.0f;
+      const float m = inb ? g.mc32[b][c[b]] : 0.0f;
       for (int comp = 0; comp < 3; ++comp) {
         float d = 0.0f;
         if (inb) {
@@ -722,7 +722,7 @@ __device__ __forceinline__ void k_dt_partial32_body(const float* __restrict__ W3
     float knu = 0.0f;
     if (pf.visc != FLUID_VISC_NONE) knu = k * viscosity_f(W32[5 * nc + c], pf) * irho;
     for (int d = 0; d < g.ndim; ++d) {
-      const float id = (float)g.idx[d][ci[d]];
+      const float id = g.idx32[d][ci[d]];
       best = fmaxf(best, (fabsf(W32[(1 + d) * nc + c]) + cs) * id);
       if (pf.visc != FLUID_VISC_NONE) best = fmaxf(best, knu * id * id);
     }

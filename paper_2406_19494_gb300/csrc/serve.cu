@@ -107,10 +107,10 @@ size_t footprint(const fluid_config& c) {
   }
   const bool visc = c.visc_law != FLUID_VISC_NONE;
   size_t b = 8 * (nc * (fl::NW + 3 * fl::NV) + metric + 4096);   // W, A, R, the state U, metrics
-  // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients and face metrics, and the
+  // mixed: the H row of W, the (hi, lo) FP32 primitives, FP32 gradients, the FP32 metric copies, and the
   // second pair of primitive buffers (W with its H row, W32)
   if (c.precision == FLUID_PREC_MIXED) {
-    b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + metric / 5);
+    b += 8 * nc + 4 * (nc * (2 * fl::NW + (visc ? fl::NG : 0)) + 3 * (metric / 5));
     b += 8 * nc * (fl::NW + 1) + 4 * nc * 2 * fl::NW;
     b += 2 * 64 * 4;                                    // the W32 buffers' slack for staged rows
   } else {
