@@ -355,6 +355,16 @@ int fluid_check_pow(const double* x_dev, double* fast_dev, double* lib_dev, int 
 int fluid_check_widen(const float* x_dev, double* bits_dev, double* cvt_dev, int n, void* stream);
 
 
+/* Check of the bulk-copy staging the mixed y / z tiles can use (fluid_tune_faces seg = 1): one warp
+ * stages nrows (1..8) rows of 36 floats from src_dev (16-byte aligned, device) into shared memory
+ * with cp.async.bulk on an mbarrier expecting the rows' bytes plus extra_bytes, waits with the
+ * tiles' bounded wait and writes the rows to dst_dev.  extra_bytes > 0 makes the wait run out
+ * (every copy lands, the expected count is never reached): FLAG_STAGING (4) is then ORed into
+ * *flags_dev (device) and dst_dev is not written.  Enqueued on `stream`.  For tests. */
+int fluid_check_bulk_staging(const float* src_dev, float* dst_dev, int nrows, int extra_bytes,
+                             unsigned* flags_dev, void* stream);
+
+
 /* fluid_rhs without a solver object and without allocating: the same right-hand side as
  * fluid_rhs, for callers that cannot call cudaMalloc -- for example a host whose device memory is
  * owned by its own pool or arena and which forbids allocations behind its back, or a

@@ -216,6 +216,9 @@ cudaError_t launch_face_mixed_stage(const double* W, const float* W32, const flo
                                     const double* R, const Geo& g, const Phys& ph, int block, int seg,
                                     const StageOut& so, cudaStream_t st);
 cudaError_t launch_grad32(const float* W32, float* G32, const Geo& g, cudaStream_t st);
+// check of the bulk-staging helpers (fluid_check_bulk_staging)
+cudaError_t launch_bulk_probe(const float* src, float* dst, int nrows, unsigned extra_tx,
+                              unsigned* flags, cudaStream_t st);
 cudaError_t launch_dt_partial32(const float* W32, const Geo& g, const Phys& ph, double* partial,
                                 int nparts, cudaStream_t st);
 

@@ -967,6 +967,43 @@ cudaError_t launch_face_mixed(int D, const double* W, const float* W32, const fl
               : launch_sv<FLUID_WENO_Z, false>(D, in, R, g, pf, accumulate, block, seg, flags, st);
 }
 
+namespace {
+// Check of the bulk-staging helpers: one warp stages nrows rows of 36 floats (16-byte aligned) from
+// src into shared memory on one mbarrier whose expected transaction count is the rows' bytes plus
+// extra_tx, waits with the tiles' bounded wait and copies the rows to dst.  With extra_tx > 0 the
+// phase cannot complete (every copy lands, the count stays short), so the wait runs out: the block
+// sets FLAG_STAGING in *flags, waits once more and returns without writing dst.
+constexpr int kProbeRows = 8;
+__global__ void k_bulk_probe(const float* __restrict__ src, float* __restrict__ dst, int nrows,
+                             unsigned extra_tx, unsigned* flags) {
+  __shared__ __align__(16) float rows[kProbeRows * kBulkRow];
+  __shared__ __align__(8) unsigned long long s_bar;
+  const unsigned bar = smem_u32(&s_bar);
+  const int lane = threadIdx.x;
+  if (lane == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (lane == 0) mbar_arrive_expect(bar, (unsigned)(nrows * kBulkRow * sizeof(float)) + extra_tx);
+  __syncwarp();
+  if (lane < nrows)
+    bulk_to_smem(smem_u32(rows + lane * kBulkRow), src + lane * kBulkRow, kBulkRow * sizeof(float), bar);
+  const bool late = !mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(late)) {
+    if (lane == 0) atomicOr(flags, FLAG_STAGING);
+    if (late) mbar_wait_bounded(bar, 0);
+    return;
+  }
+  for (int i = lane; i < nrows * kBulkRow; i += 32) dst[i] = rows[i];
+}
+}  // namespace
+
+cudaError_t launch_bulk_probe(const float* src, float* dst, int nrows, unsigned extra_tx,
+                              unsigned* flags, cudaStream_t st) {
+  if (nrows < 1 || nrows > kProbeRows || (reinterpret_cast<uintptr_t>(src) & 15) != 0)
+    return cudaErrorInvalidValue;
+  (k_bulk_probe<<<1, 32, 0, st>>>(src, dst, nrows, extra_tx, flags), ++t_launches);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_mixed(const BatchTable* dev, int kind, int D, int step, cudaStream_t st) {
   static const int gg = batch_grid_m(kbm_grad, 256);
   static const int gd = batch_grid_m(kbm_dtp, kDtBlock);

@@ -123,6 +123,15 @@ extern "C" int fluid_check_widen(const float* x_dev, double* bits_dev, double* c
   return cudaGetLastError() == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
 }
 
+extern "C" int fluid_check_bulk_staging(const float* src_dev, float* dst_dev, int nrows, int extra_bytes,
+                                        unsigned* flags_dev, void* stream) {
+  if (!src_dev || !dst_dev || !flags_dev || nrows < 1 || nrows > 8 || extra_bytes < 0 ||
+      (reinterpret_cast<uintptr_t>(src_dev) & 15) != 0)
+    return FLUID_EINVAL;
+  return fl::launch_bulk_probe(src_dev, dst_dev, nrows, (unsigned)extra_bytes, flags_dev,
+                               reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? FLUID_OK : FLUID_ECUDA;
+}
+
 extern "C" int fluid_check_rcp(const double* y_dev, double* fast_dev, double* ieee_dev, int n,
                                void* stream) {
   if (!y_dev || !fast_dev || !ieee_dev || n < 0) return FLUID_EINVAL;

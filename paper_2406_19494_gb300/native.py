@@ -57,6 +57,7 @@ SIGNATURES = {
     "fluid_rhs_noalloc": (_i, [_vp, _vp, _vp, _vp, ctypes.c_char_p, _sz]),
     "fluid_check_rcp": (_i, [_vp, _vp, _vp, _i, _vp]),
     "fluid_check_widen": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "fluid_check_bulk_staging": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "fluid_check_sqrt": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "fluid_check_pow": (_i, [_vp, _vp, _vp, _i, _d, _vp]),
     "fluid_serve_create": (_i, [_vp, ctypes.POINTER(_vp)]),

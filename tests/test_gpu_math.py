@@ -132,8 +132,58 @@ def test_integer_widening_equals_the_conversion_instruction():
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0
     b, c = bits.cpu().numpy(), cvt.cpu().numpy()
-    ref = x.astype(np.float64)
+    with np.errstate(invalid="ignore"):
+        ref = x.astype(np.float64)
     nan = np.isnan(ref)
     assert np.all(np.isnan(b[nan])) and np.all(np.isnan(c[nan]))
     assert np.array_equal(b[~nan].view(np.uint64), ref[~nan].view(np.uint64))
     assert np.array_equal(c[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+
+
+def test_bulk_staging_copies_and_its_bounded_wait():
+    """The bulk-copy staging helpers of the mixed tiles: with the exact expected byte count the
+    rows arrive in shared memory and come back unchanged, no flag; with the expected count raised
+    above what the copies deliver the phase cannot complete, the bounded wait runs out, the block
+    reports FLAG_STAGING and returns, and the context stays usable (a following staging call and a
+    solver step still work)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_19494_gb300 import build, native
+    build.build()
+    lib = native.lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    src = torch.arange(8 * 36, dtype=torch.float32, device="cuda") * 0.5 - 7.0
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def run(nrows, extra):
+        dst = torch.full((8 * 36,), -1.0, dtype=torch.float32, device="cuda")
+        flags.zero_()
+        r = lib.fluid_check_bulk_staging(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                         nrows, extra, ctypes.c_void_p(flags.data_ptr()), st)
+        assert r == 0
+        torch.cuda.synchronize()
+        return dst, int(flags.item())
+
+    dst, fl = run(8, 0)
+    assert fl == 0 and torch.equal(dst, src)
+    dst, fl = run(3, 0)
+    assert fl == 0 and torch.equal(dst[:3 * 36], src[:3 * 36]) and bool((dst[3 * 36:] == -1.0).all())
+    dst, fl = run(5, 16)
+    assert fl == 4 and bool((dst == -1.0).all())
+    dst, fl = run(8, 0)
+    assert fl == 0 and torch.equal(dst, src)
+    # argument checks on the host: row count, alignment
+    bad = lib.fluid_check_bulk_staging(ctypes.c_void_p(src.data_ptr() + 4), ctypes.c_void_p(src.data_ptr()),
+                                       2, 0, ctypes.c_void_p(flags.data_ptr()), st)
+    assert bad == native.FLUID_EINVAL
+    assert lib.fluid_check_bulk_staging(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(src.data_ptr()),
+                                        9, 0, ctypes.c_void_p(flags.data_ptr()), st) == native.FLUID_EINVAL
+    from paper_2406_19494_gb300 import workloads as wl
+    from paper_2406_19494_gb300.solver import Solver
+    s = Solver(wl.tgv_case(16), precision="mixed")
+    cen = [s.grid(a)[0][3:-3] for a in range(3)]
+    W = np.pad(wl.tgv_prims(wl.tgv_case(16), *cen), [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U = s.prim_to_cons(torch.from_numpy(W).cuda())
+    s.tune_faces(0, 1)
+    s.step(U, 2)
+    s.check()
