@@ -77,7 +77,9 @@ enum { FLUID_PREC_FP64 = 0, FLUID_PREC_MIXED = 1 };
 /*
  * Configuration of one solve.  Versioned by struct_size (set it to sizeof(fluid_config)).
  *   ndim           1, 2 or 3; axes a >= ndim are inactive (n[a] == 1)
- *   n[a]           interior cells per axis (active axes: 3 .. 2^20, product of padded sizes < 2^31)
+ *   n[a]           interior cells per axis (active axes: 3 .. 2^20); the product of the padded
+ *                  sizes must stay below 2^31 / 9 (FP64), 2^31 / 12 (mixed) and 2^31 / 36 (adjoint)
+ *                  so that the kernels' 32-bit row * cells + cell indices cannot overflow
  *   lo, hi         domain extent per axis (face coordinates of the boundaries), hi > lo
  *   stretch, beta  grid mapping per axis (beta > 0 for the tanh mappings)
  *   bc[a][side]    boundary kind for side 0 (low) and 1 (high); periodic must pair with periodic

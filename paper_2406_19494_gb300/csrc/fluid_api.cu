@@ -218,7 +218,14 @@ const char* validate(const fluid_config* c) {
         return "the block (offset, n) must lie inside the global grid";
     }
   }
+  // the kernels index arrays of R rows of padded cells with 32-bit row * ncell + cell: 9 rows on
+  // the FP64 path (the velocity gradients), 12 on the mixed one (the FP32 split of the
+  // primitives), 36 for the adjoint (its per-face slots)
   if (cells >= (1LL << 31) / 9) return "grid too large for 32-bit cell indexing";
+  if (c->precision == FLUID_PREC_MIXED && cells >= (1LL << 31) / 12)
+    return "grid too large for 32-bit cell indexing of the mixed path (12 FP32 rows per cell)";
+  if (c->adjoint && cells >= (1LL << 31) / 36)
+    return "grid too large for 32-bit cell indexing of the adjoint (36 per-face slots per cell)";
   if (!(c->gamma > 1.0) || !(c->gas_R > 0) || !(c->prandtl > 0)) return "need gamma > 1, R > 0, Pr > 0";
   if (c->visc_law < 0 || c->visc_law > 3) return "unknown viscosity law";
   if (c->visc_law != FLUID_VISC_NONE && !(c->mu_ref > 0)) return "viscous runs need mu_ref > 0";

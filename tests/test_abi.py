@@ -61,6 +61,8 @@ def _create(lib, cfg):
     (lambda c: (setattr(c, "cfl", 0.0), setattr(c, "dt_fixed", 0.0)), "cfl"),
     (lambda c: c.n.__setitem__(0, (1 << 20) + 1), "3 <= n"),
     (lambda c: (c.n.__setitem__(0, 20000), c.n.__setitem__(1, 20000)), "32-bit"),
+    (lambda c: (c.n.__setitem__(0, 14000), c.n.__setitem__(1, 14000), setattr(c, "precision", 1)), "mixed path"),
+    (lambda c: (c.n.__setitem__(0, 8000), c.n.__setitem__(1, 8000), setattr(c, "adjoint", 1)), "adjoint (36"),
     (lambda c: c.global_n.__setitem__(0, 4), "inside the global grid"),
     (lambda c: (c.global_n.__setitem__(0, 20), c.offset.__setitem__(0, 13)), "inside the global grid"),
     (lambda c: c.offset.__setitem__(1, 2), "offset needs global_n"),
