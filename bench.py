@@ -393,6 +393,8 @@ def run_fluid(args):
 
     # ---- the mixed FP32-flux / FP64-state path on the same workload ------------------------------
     sm = Solver(case, precision="mixed")
+    if args.mixed_tiles == "bulk":
+        sm.tune_faces(0, 1)
     Um = U0.clone()
     mixed_ms, mprof, _ = timed_steps(sm, Um, args.steps, args.warmup, flush, stream)
     mixed_ms = max_over_ranks(mixed_ms, "cuda")
@@ -500,7 +502,7 @@ def run_fluid(args):
         "mixed": {
             "value": whole_job_rate(ncell, args.steps, ws, mixed_ms), "unit": UNIT,
             "ms_per_step": mixed_ms / args.steps, "speedup_vs_fp64": total_ms / mixed_ms,
-            "dtype": "f32 fluxes / f64 state",
+            "dtype": "f32 fluxes / f64 state", "tiles": args.mixed_tiles,
             "error_vs_fp64": mixed_err,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in mprof.items() if v[1]},
             "roofline_step": mixed_step_roofline(mixed_ms / args.steps, ncell),
@@ -1123,6 +1125,8 @@ def main():
     ap.add_argument("--no-teno", action="store_true", help="skip the TENO6-A channel-scheme measurement")
     ap.add_argument("--no-mixed-errors", action="store_true",
                     help="skip the mixed-vs-FP64 errors on the stated workloads (TGV 1000 steps, walls)")
+    ap.add_argument("--mixed-tiles", default="plain", choices=("plain", "bulk"),
+                    help="the mixed path's y / z face tiles: plain loads (default) or rows staged by bulk copies")
     ap.add_argument("--e2", action="store_true",
                     help="also run the Ma 2.25 boundary-layer validation to steady state (about 3 minutes)")
     args = ap.parse_args()
