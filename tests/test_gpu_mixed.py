@@ -203,3 +203,32 @@ def test_mixed_porous_bl_wall_heat_flux():
     J = {p: nf.wall_heat_loss(U, case, grid, 1, 0, phi, {(0, 0): prof}) for p, U in out.items()}
     rel = abs(J["mixed"] - J["fp64"]) / abs(J["fp64"])
     assert rel <= TOL_DERIVED, (J, rel)
+
+
+@pytest.mark.slow
+def test_mixed_tgv_128_full_size_step_sampled():
+    """One mixed RK3 step of the full-size TGV 128^3 (seeded 5 % perturbation, so that every
+    variable moves) in the benchmark's launch configuration -- the y / z tiles with the stage
+    folded into the z tile -- at sampled cells, each evaluated by the oracle from its periodic
+    radius-9 neighbourhood: within the stated 1e-5 of the step's increment per variable."""
+    from test_gpu_parity import _patch_step, _perturbed, _tgv_full
+    c, case, grid, W = _tgv_full()
+    W = _perturbed(W, seed=10)
+    Wp = np.pad(W, [(0, 0)] + [(3, 3)] * 3, mode="edge")
+    U = nf.prim_to_cons(Wp, case)
+    dt = nf.cfl_dt(U, case, grid)
+    s = Solver(dict(c, dt_fixed=dt), "mixed")
+    Ud = torch.from_numpy(U).cuda()
+    s.step(Ud, 1)
+    s.check()
+    got = Ud.cpu().numpy()
+    Uint = U[(slice(None),) + case.interior()]
+    rng = np.random.default_rng(11)
+    cells = [tuple(int(rng.integers(0, 128)) for _ in range(3)) for _ in range(20)] + [(0, 0, 0), (127, 0, 64)]
+    ref = np.array([_patch_step(Uint, case, grid, cl, dt) for cl in cells])
+    u0 = np.array([Uint[:, cl[2], cl[1], cl[0]] for cl in cells])
+    gv = np.array([got[:, cl[2] + 3, cl[1] + 3, cl[0] + 3] for cl in cells])
+    inc = np.max(np.abs(ref - u0), axis=0)
+    assert np.all(inc > 0)
+    err = np.max(np.abs(gv - ref), axis=0)
+    assert np.all(err <= TOL_STEP * inc), err / inc
