@@ -54,6 +54,8 @@ CASES = {
     # several x tiles (31 cells) and ragged y / z tiles (15 cells): 40 = 31 + 9, 33 = 2 x 15 + 3
     "ragged3d_tiles": lambda: wl.random_box(3, (40, 33, 17), visc="sutherland"),
     "euler3d_minimal_n3": lambda: wl.random_box(3, (3, 3, 3), visc="none"),
+    "visc3d_minimal_n3_walls": lambda: wl.random_box(3, (3, 3, 3), bc=(P, ("wall", "wall"), P),
+                                                     t_wall=((1, 1), (1.4, 1.1), (1, 1))),
     "ragged2d_xwall": lambda: wl.random_box(2, (37, 5, 1), bc=(("wall", "wall"), P, P),
                                             t_wall=((2.5, 2.6), (1, 1), (1, 1))),
 }

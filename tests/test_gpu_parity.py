@@ -83,6 +83,8 @@ CASES = {
                                                   porous=dict(axis=1, side=0, begin=4, count=12, A=0.05,
                                                               kappa=3.0, phi0=0.1)),
     "euler3d_minimal_n3": lambda: wl.random_box(3, (3, 3, 3), visc="none"),
+    "visc3d_minimal_n3_walls": lambda: wl.random_box(3, (3, 3, 3), bc=(P, ("wall", "wall"), P),
+                                                     t_wall=((1, 1), (1.4, 1.1), (1, 1))),
     "ragged2d_xwall": lambda: wl.random_box(2, (37, 5, 1), bc=(WALL, P, P), t_wall=((2.5, 2.6), (1, 1), (1, 1))),
 }
 
@@ -476,3 +478,19 @@ def test_wall_fluxes_parity(name):
         assert got_q.shape == q_ref.shape
         assert np.max(np.abs(got_q - q_ref)) <= TOL * np.max(np.abs(q_ref)), (a, sd)
         assert np.max(np.abs(got_t - t_ref)) <= TOL * np.max(np.abs(t_ref)), (a, sd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_zero_steps_change_nothing(precision):
+    """fluid_step with nsteps = 0 launches nothing: the state and the solver's clock stay as they
+    are, bit for bit."""
+    c = CASES["ragged2d_xwall"]()
+    case, grid, U = padded_state(c, seed=4)
+    from paper_2406_19494_gb300.solver import Solver as S
+    s = S(c, precision=precision)
+    s.set_time(0.25)
+    Ud = torch.from_numpy(U).cuda()
+    s.step(Ud, 0)
+    s.check()
+    assert np.array_equal(Ud.cpu().numpy(), U)
+    assert s.time()[0] == 0.25
