@@ -926,10 +926,11 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
   }
   // seg 1: the 4 x 4 tile with its rows staged by bulk copies
   if (seg == 1) return launch_tile_bulk<SCHEME, VISC>(D, in, R, g, pf, accumulate, flags, st);
-  // tile shape (warps x faces per warp): block 64 -> 2 x 4, otherwise 4 x 4 (on TGV 128^3 the
-  // 4 x 4 tile was the fastest of 16 x 1, 8 x 2, 4 x 4 and 2 x 4)
+  // tile shape (warps x faces per warp): block 64 -> 2 x 4, otherwise 4 x 3 (on TGV 128^3 the
+  // 4 x 4 tile was the fastest of 16 x 1, 8 x 2, 4 x 4 and 2 x 4, and 4 x 3 beat 4 x 4, 4 x 5 and
+  // 4 x 2 by 2.5 % or more over the step)
   if (block == 64) return launch_tile<SCHEME, VISC, 2, 4>(D, in, R, g, pf, accumulate, st);
-  return launch_tile<SCHEME, VISC, 4, 4>(D, in, R, g, pf, accumulate, st);
+  return launch_tile<SCHEME, VISC, 4, 3>(D, in, R, g, pf, accumulate, st);
 }
 
 template <int SCHEME, bool VISC, int NWARP, int FPW, int MINB, bool BULK = false>
@@ -959,9 +960,10 @@ cudaError_t launch_stage_sv(const MixedIn& in, const double* R, const Geo& g, co
   const int D = g.ndim - 1;
   if (seg == 1) return launch_tile_stage<SCHEME, VISC, 4, 4, 4, true>(D, in, R, g, pf, ph, so, st);
   if (block == 64) return launch_tile_stage<SCHEME, VISC, 2, 4, 12>(D, in, R, g, pf, ph, so, st);
-  // 64 registers (a few bytes spilled) so that 8 tiles fit an SM: on TGV 128^3 6 % faster than
-  // 72 registers without spills (7 tiles) and 11 % faster than 80 (6 tiles)
-  return launch_tile_stage<SCHEME, VISC, 4, 4, 8>(D, in, R, g, pf, ph, so, st);
+  // 4 warps x 3 faces, as the unfused tile; 64 registers (a few bytes spilled) so that 8 tiles
+  // fit an SM: on TGV 128^3 6 % faster than 72 registers without spills (7 tiles) and 11 % faster
+  // than 80 (6 tiles)
+  return launch_tile_stage<SCHEME, VISC, 4, 3, 8>(D, in, R, g, pf, ph, so, st);
 }
 
 }  // namespace
