@@ -19,6 +19,9 @@ constexpr int NG = 9;   // velocity-gradient scratch, component c * 3 + b = d u_
 constexpr unsigned FLAG_NONFINITE = 1u;
 constexpr unsigned FLAG_GHOST_T = 2u;
 constexpr unsigned FLAG_STAGING = 4u;   // a shared-memory staging copy did not complete in time
+// the mixed path's y / z face tiles: 4 warps of 3 faces, 11 cells along the face axis
+constexpr int kMixedTileWarps = 4, kMixedTileFaces = 3;
+constexpr int kMixedTileCells = kMixedTileWarps * kMixedTileFaces - 1;
 
 // Grid geometry: padded sizes, strides and per-axis 1-D metric arrays (device, length p[a]).
 struct Geo {

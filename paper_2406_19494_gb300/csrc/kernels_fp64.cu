@@ -964,7 +964,7 @@ void batch_plan(BatchTable& t, bool mixed) {
       }
       if (mixed) {
         if (D == 0) set(BK_FACE0, ceil_div(g.n[0], 31), ceil_div(lines, 4));
-        else set(BK_FACE0 + D, ceil_div(g.n[0], 32), ceil_div(g.n[D], 15), g.n[D == 1 ? 2 : 1]);
+        else set(BK_FACE0 + D, ceil_div(g.n[0], 32), ceil_div(g.n[D], kMixedTileCells), g.n[D == 1 ? 2 : 1]);
         set(BK_SEAM0 + D, 0);
       } else {
         const long long nseg = ceil_div(g.n[D], S.seg[D]);

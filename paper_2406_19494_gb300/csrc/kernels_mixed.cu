@@ -801,7 +801,8 @@ template <int D, int SCHEME, bool VISC>
 __global__ void __launch_bounds__(128, 8) kbm_face_t(const BatchTable* __restrict__ t, int step) {
   FL_BATCH_LOOP(BK_FACE0 + D)
   if (step < S.steps)
-    k_face_mixed_t_body<D, SCHEME, VISC, 4, 4>(batch_in(S), S.R, S.g, phys_f(S.ph), 1, bid, gdim);
+    k_face_mixed_t_body<D, SCHEME, VISC, kMixedTileWarps, kMixedTileFaces>(batch_in(S), S.R, S.g, phys_f(S.ph), 1,
+                                                                          bid, gdim);
   FL_BATCH_END
 }
 
@@ -829,7 +830,7 @@ int batch_grid_m(K kernel, int block, size_t smem = 0) {
 
 template <int SCHEME, bool VISC>
 cudaError_t batch_face_m(const BatchTable* dev, int D, int step, cudaStream_t st) {
-  constexpr size_t smem = t_smem<4, 4>();
+  constexpr size_t smem = t_smem<kMixedTileWarps, kMixedTileFaces>();
   if (D == 0) {
     static const int gx = batch_grid_m(kbm_face_x<SCHEME, VISC>, 32 * kXRows);
     (kbm_face_x<SCHEME, VISC><<<gx, dim3(32, kXRows), 0, st>>>(dev, step), ++t_launches);
@@ -846,8 +847,8 @@ cudaError_t batch_face_m(const BatchTable* dev, int D, int step, cudaStream_t st
     g2 = batch_grid_m(kbm_face_t<2, SCHEME, VISC>, 128, smem);
     init = true;
   }
-  if (D == 1) (kbm_face_t<1, SCHEME, VISC><<<g1, dim3(32, 4), smem, st>>>(dev, step), ++t_launches);
-  else (kbm_face_t<2, SCHEME, VISC><<<g2, dim3(32, 4), smem, st>>>(dev, step), ++t_launches);
+  if (D == 1) (kbm_face_t<1, SCHEME, VISC><<<g1, dim3(32, kMixedTileWarps), smem, st>>>(dev, step), ++t_launches);
+  else (kbm_face_t<2, SCHEME, VISC><<<g2, dim3(32, kMixedTileWarps), smem, st>>>(dev, step), ++t_launches);
   return cudaGetLastError();
 }
 
@@ -930,7 +931,7 @@ cudaError_t launch_sv(int D, const MixedIn& in, double* R, const Geo& g, const P
   // 4 x 4 tile was the fastest of 16 x 1, 8 x 2, 4 x 4 and 2 x 4, and 4 x 3 beat 4 x 4, 4 x 5 and
   // 4 x 2 by 2.5 % or more over the step)
   if (block == 64) return launch_tile<SCHEME, VISC, 2, 4>(D, in, R, g, pf, accumulate, st);
-  return launch_tile<SCHEME, VISC, 4, 3>(D, in, R, g, pf, accumulate, st);
+  return launch_tile<SCHEME, VISC, kMixedTileWarps, kMixedTileFaces>(D, in, R, g, pf, accumulate, st);
 }
 
 template <int SCHEME, bool VISC, int NWARP, int FPW, int MINB, bool BULK = false>
@@ -963,7 +964,7 @@ cudaError_t launch_stage_sv(const MixedIn& in, const double* R, const Geo& g, co
   // 4 warps x 3 faces, as the unfused tile; 64 registers (a few bytes spilled) so that 8 tiles
   // fit an SM: on TGV 128^3 6 % faster than 72 registers without spills (7 tiles) and 11 % faster
   // than 80 (6 tiles)
-  return launch_tile_stage<SCHEME, VISC, 4, 3, 8>(D, in, R, g, pf, ph, so, st);
+  return launch_tile_stage<SCHEME, VISC, kMixedTileWarps, kMixedTileFaces, 8>(D, in, R, g, pf, ph, so, st);
 }
 
 }  // namespace
