@@ -456,7 +456,8 @@ __device__ __forceinline__ void k_face_mixed_x_body(MixedIn in, double* __restri
         sD[row][v][k] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, rowbase + j, 1) : 0.0f;
     }
   }
-  __syncthreads();
+  // each warp reads only the shared rows it wrote: a warp barrier suffices
+  __syncwarp();
   const int a = x0 - 1 + lane;                   // this lane's face is a + 1/2
   if (live && a < xend) {
     float Dw[6][5];
@@ -469,7 +470,7 @@ __device__ __forceinline__ void k_face_mixed_x_body(MixedIn in, double* __restri
 #pragma unroll
     for (int v = 0; v < 5; ++v) sF[row][v][lane] = F[v];
   }
-  __syncthreads();
+  __syncwarp();
   const int cx = x0 + lane;                      // cell of the divergence
   if (live && lane < kXCells && cx < xend) {
     double F[5], Fp[5];
