@@ -184,26 +184,42 @@ class TorchComm:
     """Point-to-point swaps over a torch.distributed process group.  NCCL moves device tensors;
     gloo (CPU) stages them through host memory.  Buffers may be torch tensors of any device."""
 
-    def __init__(self, group=None):
+    def __init__(self, group=None, grouped=None):
+        """grouped: post each swap as one batch_isend_irecv group (default: with NCCL only)."""
         import torch.distributed as dist
         self.dist = dist
         self.group = group
         self.backend = dist.get_backend(group)
+        self.grouped = (self.backend == "nccl") if grouped is None else bool(grouped)
 
     def swap(self, ops):
+        """Post every send and receive of one axis, then wait for all.  With NCCL they go as one
+        group (batch_isend_irecv): a rank's sends and receives then progress together, where
+        separately enqueued NCCL sends would each wait for a receive that the peer has queued
+        behind its own send (every rank sends to its high neighbour first); NCCL ignores tags and
+        matches a peer pair's messages in posting order, which plan_axis's order pairs up."""
         import torch
         dist = self.dist
         host = self.backend != "nccl"
-        reqs, recvs, like = [], [], None
+        reqs, recvs, like, p2p = [], [], None, []
         for kind, peer, tag, x in ops:
             if kind == "send":
                 like = x
-                reqs.append(dist.isend(x.cpu() if host else x, peer, group=self.group, tag=tag))
+                t = x.cpu() if host else x.contiguous()
+                if self.grouped:
+                    p2p.append(dist.P2POp(dist.isend, t, peer, group=self.group, tag=tag))
+                else:
+                    reqs.append(dist.isend(t, peer, group=self.group, tag=tag))
             else:
                 dev = "cpu" if host else x_device(ops)
                 r = torch.empty(x, dtype=torch.float64, device=dev)
-                reqs.append(dist.irecv(r, peer, group=self.group, tag=tag))
+                if self.grouped:
+                    p2p.append(dist.P2POp(dist.irecv, r, peer, group=self.group, tag=tag))
+                else:
+                    reqs.append(dist.irecv(r, peer, group=self.group, tag=tag))
                 recvs.append(r)
+        if p2p:
+            reqs.extend(dist.batch_isend_irecv(p2p))
         for q in reqs:
             q.wait()
         if host and like is not None and like.device.type != "cpu":

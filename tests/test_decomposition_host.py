@@ -117,7 +117,7 @@ def _global_value(case, idx):
     return v * 1e6 + (k % n[2]) * 1e4 + (j % n[1]) * 1e2 + (i % n[0])
 
 
-def _rank(rank, world, port, splits, which):
+def _rank(rank, world, port, splits, which, grouped=False):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -132,7 +132,7 @@ def _rank(rank, world, port, splits, which):
         field = torch.tensor(_global_value(c, (vv, gk, gj, gi)))
         inner = (slice(None),) + lay.interior()
         U[inner] = field[inner]
-        decomp.exchange(U, lay, _pack(lay), _unpack(lay), decomp.TorchComm())
+        decomp.exchange(U, lay, _pack(lay), _unpack(lay), decomp.TorchComm(grouped=grouped))
         # cells interior or in an exchange halo along every axis hold the global value
         ok = np.ones(shp[1:], dtype=bool)
         for a, g in ((2, kk[0]), (1, jj[0]), (0, ii[0])):
@@ -169,3 +169,14 @@ def test_exchange_fills_every_exchange_halo_over_gloo(which, splits):
     import torch.multiprocessing as mp
     world = splits[0] * splits[1] * splits[2]
     mp.spawn(_rank, args=(world, _port(), splits, which), nprocs=world, join=True)
+
+
+@pytest.mark.parametrize("which,splits", [("blocks", (2, 2, 1)), ("slabs", (1, 1, 2))])
+def test_grouped_exchange_over_gloo(which, splits):
+    """The same exchange with each axis's sends and receives posted as one batch_isend_irecv group
+    (what TorchComm does over NCCL, where separately enqueued sends would wait on each other):
+    every exchange halo holds the global value, including two blocks on a periodic axis, where both
+    faces swap with the same peer."""
+    import torch.multiprocessing as mp
+    world = splits[0] * splits[1] * splits[2]
+    mp.spawn(_rank, args=(world, _port(), splits, which, True), nprocs=world, join=True)
