@@ -593,20 +593,11 @@ __device__ __forceinline__ void k_face_mixed_t_body(MixedIn in, double* __restri
       for (int v = 0; v < NVW; ++v)
         sD[v][k][lane] = ok ? (at(v, k + 1) - at(v, k)) + (at(NVW + v, k + 1) - at(NVW + v, k)) : 0.0f;
     }
-  } else if (STAGE) {
-    // (the fused stage leaves no registers for the row carry below: measured 1 % slower with it)
-    for (int k = warp; k < ND; k += kTWarps) {
-      const int j = d0 - 3 + k;
-      const bool ok = xok && j + 1 <= dend + 2;
-#pragma unroll
-      for (int v = 0; v < NVW; ++v)
-        sD[v][k][lane] = ok ? diff32(in.hi + v * nc, in.lo + v * nc, colbase + j * s, s) : 0.0f;
-    }
   } else {
     // each warp takes a run of consecutive rows and keeps the previous row's (hi, lo) in
     // registers, so every value is loaded once (the differences are those diff32 forms; the
     // rows' second loads missed L1, which holds about 11 KB per tile beside the shared memory:
-    // 4.5 % faster on TGV 128^3)
+    // on TGV 128^3 the y tile 4.5 % faster, the z tile with the stage 1.3 %)
     constexpr int KPW = (ND + kTWarps - 1) / kTWarps;
     const int k0 = warp * KPW, k1 = min(ND, k0 + KPW);
     const int jmax = dend + 2;                              // last padded index along D
